@@ -1,0 +1,600 @@
+/*
+ * orc.c -- plain FP64 CPU oracle (test infrastructure; see orc.h).
+ *
+ * Each function cites the passage of Killedar et al. (2011) it follows.
+ * Readings where the paper is silent or garbled are marked READING and are
+ * listed in the design notes of the repository.
+ */
+#include "orc.h"
+
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+
+/* ------------------------------------------------------------------------ */
+/* constants: IAU nominal G Msun, SI c, IAU parsec-based Mpc                 */
+/* ------------------------------------------------------------------------ */
+static const double GM_SUN_SI = 1.32712440018e20;   /* m^3 s^-2 */
+static const double C_SI = 299792458.0;             /* m s^-1 */
+static const double MPC_SI = 3.0856775814913673e22; /* m */
+static const double C_KMS = 299792.458;             /* km s^-1 */
+
+double orc_mu_G(void) { return GM_SUN_SI / (C_SI * C_SI) / MPC_SI; }
+double orc_H0(const orc_cosmo *c) { return 100.0 * c->h / C_KMS; }
+
+/* H(z)/H0 for a flat, radiation-free Lemaitre model (Sec. 3.5). */
+double orc_E(const orc_cosmo *c, double z)
+{
+    double zp = 1.0 + z;
+    return sqrt(c->omega_m * zp * zp * zp + c->omega_l);
+}
+
+/* ------------------------------------------------------------------------ */
+/* composite 8-point Gauss-Legendre quadrature (library-grade primitive)    */
+/* ------------------------------------------------------------------------ */
+static const double GLX[4] = {0.1834346424956498, 0.5255324099163290,
+                              0.7966664774136267, 0.9602898564975363};
+static const double GLW[4] = {0.3626837833783620, 0.3137066458778873,
+                              0.2223810344533745, 0.1012285362903763};
+
+typedef double (*orc_fn)(const void *ctx, double x);
+
+static double gl8(orc_fn f, const void *ctx, double a, double b, int panels)
+{
+    double h = (b - a) / panels, s = 0.0;
+    for (int p = 0; p < panels; ++p) {
+        double m = a + (p + 0.5) * h, r = 0.5 * h, ps = 0.0;
+        for (int i = 0; i < 4; ++i)
+            ps += GLW[i] * (f(ctx, m - r * GLX[i]) + f(ctx, m + r * GLX[i]));
+        s += ps * r;
+    }
+    return s;
+}
+
+static double inv_E(const void *ctx, double z) { return 1.0 / orc_E((const orc_cosmo *)ctx, z); }
+static double inv_E_zp2(const void *ctx, double z)
+{
+    double zp = 1.0 + z;
+    return 1.0 / (zp * zp * orc_E((const orc_cosmo *)ctx, z));
+}
+static int panels_for(double z) { int p = (int)ceil(fabs(z) / 0.05); return p < 1 ? 1 : p; }
+
+/* Eq. raytracedistance: D_C = c int_0^z dz / H(z). */
+double orc_chi(const orc_cosmo *c, double z)
+{
+    if (z == 0.0) return 0.0;
+    return gl8(inv_E, c, 0.0, z, panels_for(z)) / orc_H0(c);
+}
+
+/* inverse of orc_chi by Newton-Raphson, d chi/dz = 1/(H0 E). */
+double orc_z_of_chi(const orc_cosmo *c, double chi)
+{
+    if (chi == 0.0) return 0.0;
+    double H0 = orc_H0(c), z = chi * H0;
+    for (int it = 0; it < 60; ++it) {
+        double dz = (orc_chi(c, z) - chi) * H0 * orc_E(c, z);
+        z -= dz;
+        if (fabs(dz) <= 1e-16 * (1.0 + fabs(z))) break;
+    }
+    return z;
+}
+
+/* Eq. lookbacksingularity.  READING: the printed argument of sinh^-1 is
+ * Omega_L/Omega_M, which gives a(0) != 1; the square root of that ratio
+ * makes a(0) = 1 as Eq. scalefac defines, and is used here. */
+double orc_t0(const orc_cosmo *c)
+{
+    return 2.0 / (3.0 * orc_H0(c) * sqrt(c->omega_l)) * asinh(sqrt(c->omega_l / c->omega_m));
+}
+
+/* Eq. scalefac2 with t the lookback time. */
+double orc_a_of_t(const orc_cosmo *c, double t)
+{
+    double s = sinh(1.5 * sqrt(c->omega_l) * orc_H0(c) * (orc_t0(c) - t));
+    return cbrt(c->omega_m / c->omega_l * s * s);
+}
+
+/* d a / d t for t the lookback time: the derivative of Eq. scalefac2,
+ * written as -a H(a) (the Friedmann equation of the same model). */
+double orc_adot_of_t(const orc_cosmo *c, double t)
+{
+    double a = orc_a_of_t(c, t);
+    return -a * orc_H0(c) * sqrt(c->omega_m / (a * a * a) + c->omega_l);
+}
+
+/* Eq. angularDD12 (full beam = FLRW angular diameter distance). */
+double orc_D_fb(const orc_cosmo *c, double z) { return orc_chi(c, z) / (1.0 + z); }
+
+/* Eq. DRempty (empty beam, Dyer-Roeder alpha = 0). */
+double orc_D_eb(const orc_cosmo *c, double z)
+{
+    if (z == 0.0) return 0.0;
+    return gl8(inv_E_zp2, c, 0.0, z, panels_for(z)) / orc_H0(c);
+}
+
+/* ------------------------------------------------------------------------ */
+/* step schedule (Eq. RKstepsize; READING: node table instead of grid size) */
+/* ------------------------------------------------------------------------ */
+typedef struct { const orc_cosmo *c; } a2_ctx;
+static double a2_of_chi(const void *ctx, double chi)
+{
+    const orc_cosmo *c = ((const a2_ctx *)ctx)->c;
+    double a = 1.0 / (1.0 + orc_z_of_chi(c, chi));
+    return a * a;
+}
+
+int orc_schedule(const orc_cosmo *c, double chi_s, int kind, int n, double chi_l,
+                 double s, double *dlam, double *nodes)
+{
+    if (n < 1 || !(chi_s > 0.0)) return -1;
+    if (kind == 1 && !(s > 0.0)) return -1;
+    double *x = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    if (!x) return -2;
+    if (kind == 0) {
+        for (int k = 0; k <= n; ++k) x[k] = chi_s * (double)k / (double)n;
+    } else {
+        double u0 = asinh((0.0 - chi_l) / s), u1 = asinh((chi_s - chi_l) / s);
+        for (int k = 0; k <= n; ++k) x[k] = chi_l + s * sinh(u0 + (u1 - u0) * (double)k / (double)n);
+    }
+    x[0] = 0.0;
+    x[n] = chi_s;
+    a2_ctx ctx = {c};
+    /* unperturbed ray with dx3/dlambda = 1 at the observer: dlambda = a^2 dx3 */
+    for (int k = 0; k < n; ++k) dlam[k] = gl8(a2_of_chi, &ctx, x[k], x[k + 1], 1);
+    if (nodes) memcpy(nodes, x, sizeof(double) * (size_t)(n + 1));
+    free(x);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Neumaier compensated summation                                           */
+/* ------------------------------------------------------------------------ */
+typedef struct { double s, c; } nsum;
+static inline void nadd(nsum *a, double x)
+{
+    double t = a->s + x;
+    if (fabs(a->s) >= fabs(x)) a->c += (a->s - t) + x;
+    else a->c += (x - t) + a->s;
+    a->s = t;
+}
+static inline double nval(nsum a) { return a.s + a.c; }
+
+/* ------------------------------------------------------------------------ */
+/* uniform prism: I(r) = int dV / |r - r'|  (Newtonian potential integral)   */
+/* F is an antiderivative with d^3F/dx dy dz = 1/r; Hx = dF/dx.             */
+/* ------------------------------------------------------------------------ */
+/* log(a + r) where b2 = r^2 - a^2 > 0; the second form avoids cancellation */
+static double log_a_plus_r(double a, double r, double b2)
+{
+    return a >= 0.0 ? log(a + r) : log(b2 / (r - a));
+}
+
+static double prism_F(double x, double y, double z)
+{
+    double x2 = x * x, y2 = y * y, z2 = z * z, r = sqrt(x2 + y2 + z2);
+    double v = 0.0;
+    if (x != 0.0 && y != 0.0) v += x * y * log_a_plus_r(z, r, x2 + y2);
+    if (y != 0.0 && z != 0.0) v += y * z * log_a_plus_r(x, r, y2 + z2);
+    if (z != 0.0 && x != 0.0) v += z * x * log_a_plus_r(y, r, z2 + x2);
+    if (x != 0.0) v -= 0.5 * x2 * atan(y * z / (x * r));
+    if (y != 0.0) v -= 0.5 * y2 * atan(z * x / (y * r));
+    if (z != 0.0) v -= 0.5 * z2 * atan(x * y / (z * r));
+    return v;
+}
+
+/* dF/dx (first argument); the other two follow by cyclic permutation */
+static double prism_H(double x, double y, double z)
+{
+    double x2 = x * x, y2 = y * y, z2 = z * z, r = sqrt(x2 + y2 + z2);
+    double v = 0.0;
+    if (y != 0.0) v += y * log_a_plus_r(z, r, x2 + y2);
+    if (z != 0.0) v += z * log_a_plus_r(y, r, x2 + z2);
+    if (x != 0.0) v -= x * atan(y * z / (x * r));
+    return v;
+}
+
+void orc_prism(const double lo[3], const double hi[3], const double r[3], double out[4])
+{
+    double X[2] = {lo[0] - r[0], hi[0] - r[0]};
+    double Y[2] = {lo[1] - r[1], hi[1] - r[1]};
+    double Z[2] = {lo[2] - r[2], hi[2] - r[2]};
+    double I = 0, gx = 0, gy = 0, gz = 0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int d = 0; d < 2; ++d) {
+                /* sign = s_a s_b s_d with s = +1 at the upper limit, -1 at the lower */
+                double sgn = (a ? 1.0 : -1.0) * (b ? 1.0 : -1.0) * (d ? 1.0 : -1.0);
+                I += sgn * prism_F(X[a], Y[b], Z[d]);
+                /* X = corner - r, so d/dr = -d/dX */
+                gx -= sgn * prism_H(X[a], Y[b], Z[d]);
+                gy -= sgn * prism_H(Y[b], Z[d], X[a]);
+                gz -= sgn * prism_H(Z[d], X[a], Y[b]);
+            }
+    out[0] = I;
+    out[1] = gx;
+    out[2] = gy;
+    out[3] = gz;
+}
+
+/* ------------------------------------------------------------------------ */
+/* mass distribution: world positions of a replica (Sec. 5.2)               */
+/* READING: replica j is the box rotated about its centre by a proper 90-   */
+/* degree rotation, shifted periodically, centred transversely on the       */
+/* optical axis and placed at x3 in [jL, (j+1)L).                            */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int64_t n;
+    int nrep;          /* replicas held (1 for isolated fields) */
+    double **w;        /* nrep arrays of n*3 world positions */
+    double *m;         /* n */
+    double *eps2;      /* n */
+    double rho_bar;    /* particle mean density of the box (Msun/Mpc^3) */
+} prep_field;
+
+static void replica_world(const orc_field *f, int j, double *w)
+{
+    double L = f->L, c = 0.5 * L;
+    const int32_t *R = f->rot + 9 * j;
+    const double *s = f->shift + 3 * j;
+    for (int64_t i = 0; i < f->n; ++i) {
+        const double *p = f->pos + 3 * i;
+        double q[3];
+        for (int r = 0; r < 3; ++r) {
+            double v = 0.0;
+            for (int k = 0; k < 3; ++k) v += (double)R[3 * r + k] * (p[k] - c);
+            v = v + c + s[r];
+            while (v >= L) v -= L;
+            while (v < 0.0) v += L;
+            q[r] = v;
+        }
+        w[3 * i + 0] = q[0] - c;
+        w[3 * i + 1] = q[1] - c;
+        w[3 * i + 2] = q[2] + (double)j * L;
+    }
+}
+
+static int prep_make(const orc_field *f, prep_field *pf)
+{
+    memset(pf, 0, sizeof(*pf));
+    pf->n = f->n;
+    pf->nrep = f->replicated ? f->n_rep : 1;
+    pf->w = (double **)calloc((size_t)pf->nrep, sizeof(double *));
+    pf->m = (double *)malloc(sizeof(double) * (size_t)(f->n > 0 ? f->n : 1));
+    pf->eps2 = (double *)malloc(sizeof(double) * (size_t)(f->n > 0 ? f->n : 1));
+    if (!pf->w || !pf->m || !pf->eps2) return -2;
+    nsum mt = {0, 0};
+    for (int64_t i = 0; i < f->n; ++i) {
+        double e = f->soft ? f->soft[i] : f->soft_scalar;
+        pf->m[i] = f->mass[i];
+        pf->eps2[i] = e * e;
+        nadd(&mt, f->mass[i]);
+    }
+    if (f->replicated) pf->rho_bar = nval(mt) / (f->L * f->L * f->L);
+    for (int j = 0; j < pf->nrep; ++j) {
+        pf->w[j] = (double *)malloc(sizeof(double) * 3 * (size_t)(f->n > 0 ? f->n : 1));
+        if (!pf->w[j]) return -2;
+        if (f->replicated) replica_world(f, j, pf->w[j]);
+        else memcpy(pf->w[j], f->pos, sizeof(double) * 3 * (size_t)f->n);
+    }
+    return 0;
+}
+
+static void prep_free(prep_field *pf)
+{
+    if (pf->w)
+        for (int j = 0; j < pf->nrep; ++j) free(pf->w[j]);
+    free(pf->w);
+    free(pf->m);
+    free(pf->eps2);
+}
+
+/* Eqs. psi and derivs with phi = a psi (Eq. phicotophys), evaluated as a
+ * Plummer-softened sum over particles (comoving):
+ *   phi(r)      = - mu_G sum_p m_p (|r - x_p|^2 + eps_p^2)^(-1/2)
+ *   grad phi(r) =   mu_G sum_p m_p (r - x_p) (|r - x_p|^2 + eps_p^2)^(-3/2)
+ * For mean-subtracted boxes the field of the replica's uniform mean density
+ * is removed (Sec. 3.3, "the mean matter density is then subtracted off"). */
+static void field_eval(const orc_field *f, const prep_field *pf, int rep, const double *r,
+                       double out[4], double *npairs)
+{
+    const double *w = pf->w[f->replicated ? rep : 0];
+    nsum ph = {0, 0}, gx = {0, 0}, gy = {0, 0}, gz = {0, 0};
+    for (int64_t i = 0; i < pf->n; ++i) {
+        double dx = r[0] - w[3 * i], dy = r[1] - w[3 * i + 1], dz = r[2] - w[3 * i + 2];
+        double r2 = dx * dx + dy * dy + dz * dz + pf->eps2[i];
+        double inv = 1.0 / sqrt(r2);
+        double mi = pf->m[i] * inv;
+        double mi3 = mi * inv * inv;
+        nadd(&ph, mi);
+        nadd(&gx, mi3 * dx);
+        nadd(&gy, mi3 * dy);
+        nadd(&gz, mi3 * dz);
+    }
+    double mu = orc_mu_G();
+    out[0] = -mu * nval(ph);
+    out[1] = mu * nval(gx);
+    out[2] = mu * nval(gy);
+    out[3] = mu * nval(gz);
+    if (npairs) *npairs += (double)pf->n;
+    if (f->replicated && f->mean_subtract) {
+        double L = f->L;
+        double lo[3] = {-0.5 * L, -0.5 * L, (double)rep * L};
+        double hi[3] = {0.5 * L, 0.5 * L, (double)(rep + 1) * L};
+        double I[4];
+        orc_prism(lo, hi, r, I);
+        /* phi_bg = -mu_G rho I ; subtract it */
+        double k = mu * pf->rho_bar;
+        out[0] += k * I[0];
+        out[1] += k * I[1];
+        out[2] += k * I[2];
+        out[3] += k * I[3];
+    }
+}
+
+static int rep_of(const orc_field *f, double x3)
+{
+    if (!f->replicated) return 0;
+    double q = floor(x3 / f->L);
+    if (q < 0.0) return 0;
+    if (q > (double)(f->n_rep - 1)) return f->n_rep - 1;
+    return (int)q;
+}
+
+int orc_potential(const orc_field *f, int64_t n, const double *pts, const int32_t *rep,
+                  double *out, int nthreads)
+{
+    prep_field pf;
+    if (prep_make(f, &pf) != 0) { prep_free(&pf); return -2; }
+    for (int64_t i = 0; i < n; ++i)
+        if (f->replicated && (rep[i] < 0 || rep[i] >= f->n_rep)) { prep_free(&pf); return -1; }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int64_t i = 0; i < n; ++i)
+        field_eval(f, &pf, f->replicated ? rep[i] : 0, pts + 3 * i, out + 4 * i, NULL);
+    prep_free(&pf);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* geodesic equation (Eq. geodesiceqn) with the Christoffel symbols of      */
+/* App. A, contracted literally: d^2 x^a / dl^2 = -Gamma^a_bc u^b u^c.      */
+/* index 0 = t, 1..3 = x, y, z.                                              */
+/* ------------------------------------------------------------------------ */
+void orc_geodesic_rhs(const orc_cosmo *c, const double y[8], const double F[4],
+                      int christoffel, double dy[8])
+{
+    double a = orc_a_of_t(c, y[0]), ad = orc_adot_of_t(c, y[0]);
+    double phi = F[0];
+    const double *g = F + 1; /* phi_{,i} */
+    double G[4][4][4];
+    memset(G, 0, sizeof(G));
+    for (int i = 1; i <= 3; ++i) {
+        G[i][0][0] = g[i - 1] / (a * a * a);                 /* Gamma^i_tt */
+        G[i][0][i] = G[i][i][0] = ad * (a + phi) / (a * a);   /* Gamma^i_ti */
+        G[0][0][i] = G[0][i][0] = g[i - 1] / a;               /* Gamma^t_ti */
+        G[0][i][i] = christoffel == 0 ? ad * (a + phi)        /* Gamma^t_ii, App. A */
+                                      : ad * (a - 3.0 * phi); /* derived from the metric */
+        for (int j = 1; j <= 3; ++j) {
+            if (j == i) {
+                G[i][i][i] = -g[i - 1] / a;                   /* Gamma^i_ii */
+            } else {
+                G[i][j][j] = g[i - 1] / a;                    /* Gamma^i_jj, j != i */
+                G[i][i][j] = G[i][j][i] = -g[j - 1] / a;      /* Gamma^i_ij, j != i */
+            }
+        }
+    }
+    G[0][0][0] = -ad * phi / (a * a);                         /* Gamma^t_tt */
+    const double *u = y + 4;
+    for (int k = 0; k < 4; ++k) dy[k] = u[k];
+    for (int al = 0; al < 4; ++al) {
+        double s = 0.0;
+        for (int b = 0; b < 4; ++b)
+            for (int d = 0; d < 4; ++d) s += G[al][b][d] * u[b] * u[d];
+        dy[4 + al] = -s;
+    }
+}
+
+/* ------------------------------------------------------------------------ */
+/* bundle Jacobian (Sec. 3.1 ray bundle; Eqs. lensmap, magnification).      */
+/* READING: the ellipse fit is the least-squares linear map of the polygon  */
+/* offsets, A = (sum dbeta dtheta^T)(sum dtheta dtheta^T)^-1.                */
+/* ------------------------------------------------------------------------ */
+void orc_bundle_jacobian(int n_ring, const double *theta0, const double *dtheta,
+                         const double *xy, double chi_s, double out[6])
+{
+    (void)theta0;
+    double M[2][2] = {{0, 0}, {0, 0}}, N[2][2] = {{0, 0}, {0, 0}};
+    for (int k = 1; k <= n_ring; ++k) {
+        double db[2] = {(xy[2 * k] - xy[0]) / chi_s, (xy[2 * k + 1] - xy[1]) / chi_s};
+        const double *dt = dtheta + 2 * (k - 1);
+        for (int r = 0; r < 2; ++r)
+            for (int q = 0; q < 2; ++q) {
+                M[r][q] += db[r] * dt[q];
+                N[r][q] += dt[r] * dt[q];
+            }
+    }
+    double dn = N[0][0] * N[1][1] - N[0][1] * N[1][0];
+    double Ni[2][2] = {{N[1][1] / dn, -N[0][1] / dn}, {-N[1][0] / dn, N[0][0] / dn}};
+    double A[2][2];
+    for (int r = 0; r < 2; ++r)
+        for (int q = 0; q < 2; ++q) A[r][q] = M[r][0] * Ni[0][q] + M[r][1] * Ni[1][q];
+    double det = A[0][0] * A[1][1] - A[0][1] * A[1][0];
+    out[0] = 1.0 / det;                          /* mu */
+    out[1] = 1.0 - 0.5 * (A[0][0] + A[1][1]);    /* kappa */
+    out[2] = 0.5 * (A[1][1] - A[0][0]);          /* gamma1 */
+    out[3] = -0.5 * (A[0][1] + A[1][0]);         /* gamma2 */
+    out[4] = 0.5 * (A[0][1] - A[1][0]);          /* omega (rotation) */
+    out[5] = 0.0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* full trace: RK4 with fixed steps in lambda (Sec. 3.4), terminated on x3, */
+/* linear interpolation at the overshoot.                                    */
+/* READING (initial conditions): t = 0, x = 0, direction (theta_x,          */
+/* theta_y, 1) with dx3/dlambda = 1, dt/dlambda from the null condition.    */
+/* READING (volume): at each stage the bundle uses the replica holding its  */
+/* central ray's stage position.                                            */
+/* ------------------------------------------------------------------------ */
+int orc_trace(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b,
+              const double *theta, const orc_trace_opts *o, double *ray_out,
+              double *bundle_out, int32_t *steps_out, double *n_pairs, int nthreads)
+{
+    if (o->n_ring < 2 || o->n_steps < 1 || !(z_s > 0.0)) return -1;
+    const int nr = 1 + o->n_ring;
+    const double chi_s = orc_chi(c, z_s);
+    double *dlam = (double *)malloc(sizeof(double) * (size_t)o->n_steps);
+    if (!dlam) return -2;
+    if (orc_schedule(c, chi_s, o->schedule, o->n_steps, o->lens_chi, o->asinh_s, dlam, NULL) != 0) {
+        free(dlam);
+        return -1;
+    }
+    prep_field pf;
+    if (prep_make(f, &pf) != 0) { prep_free(&pf); free(dlam); return -2; }
+    double total_pairs = 0.0;
+    const double cs[4] = {0.0, 0.5, 0.5, 1.0};
+    const int max_steps = o->n_steps + (o->max_extra > 0 ? o->max_extra : 0);
+
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : total_pairs)
+    for (int64_t b = 0; b < n_b; ++b) {
+        double y[9][8], ys[9][8], kk[4][9][8], fin[9][8], th[9][2];
+        int done[9], steps[9];
+        double pairs = 0.0;
+        th[0][0] = theta[2 * b];
+        th[0][1] = theta[2 * b + 1];
+        for (int k = 1; k < nr; ++k) {
+            double ang = o->phase + 2.0 * M_PI * (double)(k - 1) / (double)o->n_ring;
+            th[k][0] = th[0][0] + o->theta_r * cos(ang);
+            th[k][1] = th[0][1] + o->theta_r * sin(ang);
+        }
+        for (int k = 0; k < nr; ++k) {
+            double v[3] = {th[k][0], th[k][1], 1.0};
+            y[k][0] = 0.0;
+            y[k][1] = y[k][2] = y[k][3] = 0.0;
+            y[k][5] = v[0];
+            y[k][6] = v[1];
+            y[k][7] = v[2];
+            double F[4];
+            field_eval(f, &pf, rep_of(f, 0.0), y[k] + 1, F, &pairs);
+            double a = orc_a_of_t(c, 0.0), vn = sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+            /* null condition of Eq. expandingmetric with psi = phi/a */
+            y[k][4] = a * vn * sqrt((1.0 - 2.0 * F[0] / a) / (1.0 + 2.0 * F[0] / a));
+            done[k] = 0;
+            steps[k] = -1;
+        }
+        for (int step = 0; step < max_steps; ++step) {
+            double dl = dlam[step < o->n_steps ? step : o->n_steps - 1];
+            for (int s = 0; s < 4; ++s) {
+                for (int k = 0; k < nr; ++k)
+                    for (int q = 0; q < 8; ++q)
+                        ys[k][q] = s == 0 ? y[k][q] : y[k][q] + cs[s] * dl * kk[s - 1][k][q];
+                int rep = rep_of(f, ys[0][3]);
+                for (int k = 0; k < nr; ++k) {
+                    double F[4];
+                    field_eval(f, &pf, rep, ys[k] + 1, F, done[k] ? NULL : &pairs);
+                    orc_geodesic_rhs(c, ys[k], F, o->christoffel, kk[s][k]);
+                }
+            }
+            int all = 1;
+            for (int k = 0; k < nr; ++k) {
+                double yn[8];
+                for (int q = 0; q < 8; ++q)
+                    yn[q] = y[k][q] + dl / 6.0 * (kk[0][k][q] + 2.0 * kk[1][k][q] + 2.0 * kk[2][k][q] + kk[3][k][q]);
+                if (!done[k] && yn[3] >= chi_s) {
+                    double sfr = (chi_s - y[k][3]) / (yn[3] - y[k][3]);
+                    for (int q = 0; q < 8; ++q) fin[k][q] = y[k][q] + sfr * (yn[q] - y[k][q]);
+                    done[k] = 1;
+                    steps[k] = step + 1;
+                }
+                for (int q = 0; q < 8; ++q) y[k][q] = yn[q];
+                all &= done[k];
+            }
+            if (all) break;
+        }
+        int flags = 0;
+        for (int k = 0; k < nr; ++k) {
+            if (!done[k]) {
+                flags |= ORC_F_NOCROSS;
+                for (int q = 0; q < 8; ++q) fin[k][q] = y[k][q];
+            }
+            for (int q = 0; q < 8; ++q) {
+                if (!isfinite(fin[k][q])) flags |= ORC_F_NONFINITE;
+                ray_out[((size_t)b * nr + k) * 8 + q] = fin[k][q];
+            }
+            if (steps_out) steps_out[(size_t)b * nr + k] = steps[k];
+        }
+        double xy[18], dth[16];
+        for (int k = 0; k < nr; ++k) {
+            xy[2 * k] = fin[k][1];
+            xy[2 * k + 1] = fin[k][2];
+        }
+        for (int k = 1; k < nr; ++k) {
+            dth[2 * (k - 1)] = th[k][0] - th[0][0];
+            dth[2 * (k - 1) + 1] = th[k][1] - th[0][1];
+        }
+        double J[6];
+        orc_bundle_jacobian(o->n_ring, th[0], dth, xy, chi_s, J);
+        if (!isfinite(J[0])) flags |= ORC_F_NONFINITE;
+        if (J[0] < 0.0) flags |= ORC_F_NEGPARITY;
+        J[5] = (double)flags;
+        for (int q = 0; q < 6; ++q) bundle_out[(size_t)b * 6 + q] = J[q];
+        total_pairs += pairs;
+    }
+    if (n_pairs) *n_pairs = total_pairs;
+    prep_free(&pf);
+    free(dlam);
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* mu PDF (Sec. 5.3, Eq. weighthisto): counts weighted by 1/mu.             */
+/* READING: bins uniform in log10|mu|; negative parity binned by |mu| and   */
+/* counted; flagged (no-cross, non-finite) bundles are excluded.            */
+/* ------------------------------------------------------------------------ */
+int orc_histogram(int64_t n, const double *mu, const int32_t *flags, const orc_hist_opts *o,
+                  uint64_t *counts, uint64_t *wfix, double *sc)
+{
+    if (o->bins < 1 || !(o->mu_min > 0.0) || !(o->mu_max > o->mu_min)) return -1;
+    memset(counts, 0, sizeof(uint64_t) * (size_t)o->bins);
+    memset(wfix, 0, sizeof(uint64_t) * (size_t)o->bins);
+    double lmin = log10(o->mu_min);
+    double dl = (log10(o->mu_max) - lmin) / (double)o->bins;
+    int64_t used = 0, under = 0, over = 0, neg = 0, bad = 0;
+    nsum W = {0, 0}, S1 = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        int fl = flags ? flags[i] : 0;
+        if ((fl & (ORC_F_NOCROSS | ORC_F_NONFINITE)) || !isfinite(mu[i]) || mu[i] == 0.0) { ++bad; continue; }
+        double m = fabs(mu[i]);
+        if (mu[i] < 0.0) ++neg;
+        double w = 1.0 / m;
+        nadd(&W, w);
+        nadd(&S1, w * m);
+        double bb = floor((log10(m) - lmin) / dl);
+        if (bb < 0.0) ++under;
+        else if (bb >= (double)o->bins) ++over;
+        else {
+            int64_t k = (int64_t)bb;
+            counts[k] += 1;
+            wfix[k] += (uint64_t)llrint(ldexp(w, 32));
+        }
+        ++used;
+    }
+    double Wt = nval(W), mean = used ? nval(S1) / Wt : 0.0;
+    nsum S2 = {0, 0};
+    for (int64_t i = 0; i < n; ++i) {
+        int fl = flags ? flags[i] : 0;
+        if ((fl & (ORC_F_NOCROSS | ORC_F_NONFINITE)) || !isfinite(mu[i]) || mu[i] == 0.0) continue;
+        double m = fabs(mu[i]), d = m - mean;
+        nadd(&S2, d * d / m);
+    }
+    sc[0] = (double)used;
+    sc[1] = (double)under;
+    sc[2] = (double)over;
+    sc[3] = (double)neg;
+    sc[4] = (double)bad;
+    sc[5] = Wt;
+    sc[6] = mean;
+    sc[7] = used ? sqrt(nval(S2) / Wt) : 0.0;
+    return 0;
+}

@@ -1,0 +1,126 @@
+/*
+ * orc.h -- plain FP64 CPU oracle for 3D ray-bundle tracing through a particle
+ * mass distribution (Killedar, Lasky, Lewis & Fluke 2011, "Gravitational
+ * Lensing with Three-Dimensional Ray Tracing").
+ *
+ * TEST INFRASTRUCTURE ONLY.  This library is the reference against which the
+ * CUDA path is checked.  Only the test-suite, the smoke check and the
+ * benchmark's CPU-baseline leg may load it; the product path never does.  It
+ * shares no code, header, table or constant with the CUDA library.
+ *
+ * Units: comoving lengths in Mpc, time in Mpc (c = 1), masses in solar
+ * masses.  G/c^2 is folded into ORC_MU_G (Mpc per solar mass).
+ *
+ * Every routine is a direct transcription of the paper's definitions, in
+ * FP64, with naive loops and Neumaier-compensated sums; nothing is blocked,
+ * fused or reordered beyond what the definition states.
+ */
+#ifndef ORC_H
+#define ORC_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- cosmology (Sec. 3.5, Sec. 5.1, App. E) ---------------------------- */
+typedef struct {
+    double omega_m; /* Omega_M,0 */
+    double omega_l; /* Omega_Lambda,0 ; flat: omega_m + omega_l = 1 */
+    double h;       /* H0 = 100 h km/s/Mpc */
+} orc_cosmo;
+
+double orc_mu_G(void);                              /* G Msun / c^2 in Mpc */
+double orc_H0(const orc_cosmo *c);                  /* H0 / c in 1/Mpc */
+double orc_E(const orc_cosmo *c, double z);         /* H(z)/H0 */
+double orc_chi(const orc_cosmo *c, double z);       /* Eq. raytracedistance */
+double orc_z_of_chi(const orc_cosmo *c, double chi);
+double orc_t0(const orc_cosmo *c);                  /* Eq. lookbacksingularity (a(0)=1 reading) */
+double orc_a_of_t(const orc_cosmo *c, double t);    /* Eq. scalefac2, t = lookback time */
+double orc_adot_of_t(const orc_cosmo *c, double t); /* da/dt, t = lookback time */
+double orc_D_fb(const orc_cosmo *c, double z);      /* Eq. angularDD12 */
+double orc_D_eb(const orc_cosmo *c, double z);      /* Eq. DRempty */
+
+/* step schedule (Eq. RKstepsize with the resolution length replaced by a
+ * node table).  kind 0: uniform nodes in x3; kind 1: lens-centred asinh
+ * nodes x3_k = chi_l + s sinh(u_k).  dlam[k] = int_{x3_k}^{x3_{k+1}} a^2 dchi
+ * along the unperturbed ray.  nodes may be NULL. */
+int orc_schedule(const orc_cosmo *c, double chi_s, int kind, int n_steps,
+                 double chi_l, double s, double *dlam, double *nodes);
+
+/* ---- mass distribution (Sec. 3.3, Sec. 5.2) ---------------------------- */
+typedef struct {
+    int64_t n;
+    const double *pos;    /* n*3 comoving Mpc.  isolated: world frame;
+                             replicated: box frame [0,L)^3 */
+    const double *mass;   /* n, Msun */
+    const double *soft;   /* n Plummer softening lengths (comoving Mpc), or NULL */
+    double soft_scalar;   /* used when soft == NULL */
+    int replicated;       /* 0 isolated field, 1 box replicated along x3 */
+    double L;             /* box length (replicated only) */
+    int n_rep;            /* number of replicas along the line of sight */
+    const int32_t *rot;   /* n_rep * 9 row-major signed permutation matrices */
+    const double *shift;  /* n_rep * 3 shifts in [0, L) */
+    int mean_subtract;    /* subtract the field of the replica's uniform mean */
+} orc_field;
+
+/* phi and grad phi (Eqs. psi, derivs, phicotophys, as a Plummer-softened
+ * direct sum) at n points; rep[i] selects the replica for point i (ignored
+ * for isolated fields).  out: n*4 = (phi, dphi/dx1, dphi/dx2, dphi/dx3). */
+int orc_potential(const orc_field *f, int64_t n, const double *pts,
+                  const int32_t *rep, double *out, int nthreads);
+
+/* Newtonian-form integral of a uniform rectangular prism:
+ * I = int dV / |r - r'| over [lo, hi] and its gradient with respect to r.
+ * out = (I, dI/dx1, dI/dx2, dI/dx3). */
+void orc_prism(const double lo[3], const double hi[3], const double r[3], double out[4]);
+
+/* ---- geodesic right-hand side (Eq. geodesiceqn, App. A) ---------------- */
+/* y = (t, x1, x2, x3, dt/dl, dx1/dl, dx2/dl, dx3/dl); F = (phi, grad phi).
+ * christoffel 0: App. A as printed; 1: Gamma^t_ij derived from the metric. */
+void orc_geodesic_rhs(const orc_cosmo *c, const double y[8], const double F[4],
+                      int christoffel, double dy[8]);
+
+/* ---- full trace (Secs. 3.1, 3.4, 5.3) ---------------------------------- */
+typedef struct {
+    int n_ring;         /* rays on the bundle polygon (paper: 8; default 4) */
+    double theta_r;     /* polygon radius, rad */
+    double phase;       /* polygon orientation, rad */
+    int schedule;       /* 0 uniform, 1 asinh */
+    int n_steps;
+    double lens_chi;    /* asinh centre */
+    double asinh_s;     /* asinh scale */
+    int max_extra;      /* extra steps of the last size after the table ends */
+    int christoffel;    /* 0 paper App. A, 1 derived */
+} orc_trace_opts;
+
+enum { ORC_F_NOCROSS = 1, ORC_F_NONFINITE = 2, ORC_F_NEGPARITY = 4 };
+
+/* ray_out: n_b*(1+n_ring)*8 final states at x3 = chi_s.
+ * bundle_out: n_b*6 = (mu, kappa, gamma1, gamma2, omega, flags).
+ * steps_out (optional): n_b*(1+n_ring) steps taken until the crossing.
+ * Returns the number of (ray, particle) pair evaluations in *n_pairs. */
+int orc_trace(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b,
+              const double *theta, const orc_trace_opts *o, double *ray_out,
+              double *bundle_out, int32_t *steps_out, double *n_pairs, int nthreads);
+
+/* Jacobian of one bundle from its final states (Eqs. lensmap, magnification). */
+void orc_bundle_jacobian(int n_ring, const double *theta0, const double *dtheta,
+                         const double *xy_final, double chi_s, double out[6]);
+
+/* ---- mu PDF (Eq. weighthisto) ------------------------------------------ */
+typedef struct {
+    int bins;
+    double mu_min, mu_max;
+} orc_hist_opts;
+
+/* counts[bins], wfix[bins] = sum of round(2^32/|mu|) per bin,
+ * scalars: (n_used, n_under, n_over, n_neg, n_bad, W_total, mean_w, sigma_w). */
+int orc_histogram(int64_t n, const double *mu, const int32_t *flags,
+                  const orc_hist_opts *o, uint64_t *counts, uint64_t *wfix,
+                  double *scalars);
+
+#ifdef __cplusplus
+}
+#endif
+#endif
