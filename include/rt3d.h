@@ -1,0 +1,219 @@
+/*
+ * rt3d.h -- C ABI of the GB300 (sm_103a) 3D ray-bundle lensing library.
+ *
+ * The library integrates bundles of null geodesics from the observer to a
+ * source plane through a particle mass distribution, without the thin-lens
+ * approximation, following Killedar, Lasky, Lewis & Fluke (2011),
+ * "Gravitational Lensing with Three-Dimensional Ray Tracing":
+ *   - metric: the weakly perturbed flat FRW metric, Eq. expandingmetric, with
+ *     psi = phi / a (Eq. phicotophys);
+ *   - potential: Eqs. psi / derivs evaluated as a Plummer-softened direct sum
+ *     over the particles (comoving), optionally minus the field of the
+ *     replica's uniform mean density (Sec. 3.3);
+ *   - geodesic equation: Eq. geodesiceqn with the Christoffel symbols of
+ *     App. A, classical RK4 with fixed steps in the affine parameter,
+ *     terminated on the x3 coordinate with linear interpolation (Sec. 3.4);
+ *   - scale factor: Eq. scalefac2 of the lookback time carried by each ray;
+ *   - bundles: a central ray and a regular polygon of rays (Sec. 3.1); the
+ *     lens-map Jacobian (Eq. lensmap) gives mu, kappa, gamma (Eq. magnification);
+ *   - muPDF: counts weighted by 1/mu (Eq. weighthisto).
+ *
+ * Units: comoving Mpc for lengths, Mpc for time (c = 1), solar masses,
+ * radians for angles.
+ *
+ * Conventions for every entry point:
+ *   - return RT3D_OK (0) or a negative RT3D_E* code; nothing aborts or
+ *     throws across the ABI; rt3d_last_error() holds a message per context;
+ *   - host pointers are read during the call only; output arrays are owned
+ *     by the caller and sized as stated; the context owns all device memory
+ *     it allocates and frees it in rt3d_destroy();
+ *   - one context per host thread; calls on one context are not reentrant;
+ *   - entry points without "_device" are synchronous; the _device variants
+ *     take device pointers and a cudaStream_t and only enqueue work.
+ */
+#ifndef RT3D_H
+#define RT3D_H
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define RT3D_OK 0
+#define RT3D_EINVAL (-1)   /* bad argument (NaN, negative mass, empty, out of range) */
+#define RT3D_ENOMEM (-2)   /* device or host allocation failed */
+#define RT3D_ECUDA (-3)    /* a CUDA runtime call failed */
+#define RT3D_ETIMEOUT (-4) /* a device watchdog expired */
+#define RT3D_ENOTIMPL (-5) /* option not implemented */
+#define RT3D_ENOCOSMO (-6) /* trace before rt3d_set_cosmology */
+#define RT3D_ENOFIELD (-7) /* field id not loaded */
+
+#define RT3D_MIXED 0 /* FP32 pair sums with compensated accumulation, FP64 ray state */
+#define RT3D_FP64 1  /* every step in FP64 */
+
+#define RT3D_CHRISTOFFEL_PAPER 0   /* App. A as printed: Gamma^t_ii = a-dot (a + phi) */
+#define RT3D_CHRISTOFFEL_DERIVED 1 /* from the metric to first order: a-dot (a - 3 phi) */
+
+#define RT3D_SCHED_UNIFORM 0 /* nodes uniform in x3 */
+#define RT3D_SCHED_ASINH 1   /* nodes x3_k = chi_l + s sinh(u_k), u uniform */
+
+#define RT3D_F_NOCROSS 1   /* a ray did not reach x3 = chi_s within n_steps + max_extra */
+#define RT3D_F_NONFINITE 2 /* a non-finite state or magnification */
+#define RT3D_F_NEGPARITY 4 /* det A < 0 (image of negative parity) */
+
+#define RT3D_MAX_FIELDS 1024
+
+typedef struct rt3d_ctx rt3d_ctx;
+
+typedef struct {
+    int precision;         /* RT3D_MIXED (default) or RT3D_FP64 */
+    int christoffel;       /* RT3D_CHRISTOFFEL_PAPER (default) or _DERIVED */
+    int rays_per_thread;   /* force-kernel register blocking (1, 2, 4); 0 = tuned */
+    int threads_per_block; /* force-kernel block size (64..512); 0 = tuned */
+    int splits;            /* particle splits per ray block; 0 = tuned */
+    int autotune;          /* 1: time candidate launch shapes once per size bucket */
+    double watchdog_s;     /* limit for the persistent kernel's waits; 0 = 10 s */
+    int time_kernels;      /* 1: bracket every pair-sum launch with CUDA events (stats.force_ms) */
+} rt3d_options;
+
+/* Mass distribution layout.
+ * replicated = 0: an isolated field; positions are world coordinates.
+ * replicated = 1: a periodic box [0, box_length)^3; replica j is the box
+ *   rotated about its centre by rot[j] (a 3x3 signed permutation, row-major),
+ *   shifted by shift[j] with periodic wrap, centred on the optical axis in
+ *   x1, x2 and placed at x3 in [j L, (j+1) L) (Sec. 5.2).  A bundle uses the
+ *   replica that holds its central ray's stage position. */
+typedef struct {
+    int replicated;
+    double box_length;
+    int n_replicas;
+    const int32_t *rot;   /* n_replicas * 9 (host) */
+    const double *shift;  /* n_replicas * 3 (host), in [0, box_length) */
+    int mean_subtract;    /* subtract the field of the box's mean particle density */
+} rt3d_volume;
+
+typedef struct {
+    int n_ring;      /* rays on the polygon (2..8); the paper uses 8, default 4 */
+    double theta_r;  /* polygon radius (rad) */
+    double phase;    /* polygon orientation (rad) */
+    int schedule;    /* RT3D_SCHED_* */
+    int n_steps;     /* RK4 steps in the node table */
+    double lens_chi; /* asinh schedule: centre (comoving Mpc) */
+    double asinh_s;  /* asinh schedule: scale (comoving Mpc) */
+    int max_extra;   /* further steps of the last size for rays not yet across (<= 64) */
+} rt3d_bundle_opts;
+
+/* Per-bundle results (caller-owned host arrays of n_bundles; optional ones may be NULL). */
+typedef struct {
+    double *mu, *kappa, *gamma1, *gamma2, *omega;
+    int32_t *flags;
+    double *ray_state;  /* optional: n_bundles*(1+n_ring)*8 final (t,x1,x2,x3,dt,dx1,dx2,dx3) */
+    int32_t *ray_steps; /* optional: n_bundles*(1+n_ring) step at which each ray crossed */
+} rt3d_bundle_result;
+
+typedef struct {
+    int bins;      /* >= 1 */
+    double mu_min; /* > 0 */
+    double mu_max; /* > mu_min */
+} rt3d_hist_opts;
+
+typedef struct {
+    uint64_t *counts; /* caller-owned [bins] */
+    uint64_t *wfix;   /* caller-owned [bins]: sum of round(2^32 / |mu|) */
+    int64_t n_used, n_under, n_over, n_neg, n_bad;
+    double W_total, mean_w, sigma_w;
+} rt3d_hist;
+
+typedef struct {
+    double interactions;  /* (ray, particle) pairs evaluated for rays not yet across */
+    double device_ms;     /* device time of the last trace/batch (CUDA events) */
+    double force_ms;      /* device time inside the pair-sum kernels */
+    int64_t launches;     /* kernels launched by the last trace/batch */
+    int64_t force_launches;
+    int steps;            /* RK4 steps issued */
+    int rays_per_thread, threads_per_block, splits; /* force launch shape used */
+} rt3d_stats;
+
+/* One light cone of a batch (Sec. 5): its field, source redshift, bundles and steps. */
+typedef struct {
+    int field_id;
+    double z_s;
+    int64_t n_bundles;
+    const double *theta; /* host n_bundles*2 */
+    int n_steps;
+} rt3d_cone;
+
+/* Create a context on CUDA device cuda_device; opt may be NULL (defaults). */
+int rt3d_create(rt3d_ctx **out, int cuda_device, const rt3d_options *opt);
+/* Free every device allocation of the context. */
+int rt3d_destroy(rt3d_ctx *ctx);
+
+/* Flat LCDM background (Sec. 3.5): |omega_m + omega_l - 1| <= 1e-12, h > 0. */
+int rt3d_set_cosmology(rt3d_ctx *ctx, double omega_m, double omega_l, double h);
+
+/* Copy a particle set to the device as field field_id (0..RT3D_MAX_FIELDS-1,
+ * replacing any previous one).  pos: n*3, mass: n (> 0), soft: n Plummer
+ * softening lengths if soft_per_particle, else soft[0] for all (>= 0).
+ * Positions are stored as integers on a grid of 2^-e Mpc (the finest that
+ * holds the field), so coordinates that are multiples of 2^-22 Mpc are kept
+ * exactly.  vol may be NULL (isolated field). */
+int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos,
+                        const double *mass, const double *soft, int soft_per_particle,
+                        const rt3d_volume *vol);
+
+/* Trace n_bundles bundles with centres theta (n_bundles*2, tangent-plane
+ * angles: direction (theta_x, theta_y, 1)) from the observer to the plane
+ * x3 = chi(z_s), and fill out. */
+int rt3d_trace(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_bundles, const double *theta,
+               const rt3d_bundle_opts *b, rt3d_bundle_result *out);
+
+/* As rt3d_trace, with device pointers, enqueued on stream (a cudaStream_t;
+ * NULL = default stream) without host synchronisation.
+ * d_theta: n_bundles*2; d_bundle_out: n_bundles*6 doubles
+ * (mu, kappa, gamma1, gamma2, omega, flags as a double);
+ * d_ray_out (optional): n_bundles*(1+n_ring)*8. */
+int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_bundles,
+                      const double *d_theta, const rt3d_bundle_opts *b, double *d_bundle_out,
+                      double *d_ray_out);
+
+/* Trace many independent cones (each with its own field, z_s, bundles and
+ * step count) in one persistent launch recorded in a CUDA graph.
+ * outs[i] receives cone i's results. */
+int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones,
+                     const rt3d_bundle_opts *b, rt3d_bundle_result *outs);
+
+/* muPDF of n magnifications (Eq. weighthisto): bins uniform in log10|mu|
+ * (bin = floor((log10|mu| - log10 mu_min) / dl) in FP64), counts and
+ * fixed-point weights round(2^32/|mu|); flagged (NOCROSS / NONFINITE) and
+ * non-finite entries are excluded; flags may be NULL. */
+int rt3d_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const int32_t *flags,
+                   const rt3d_hist_opts *o, rt3d_hist *out);
+
+/* phi and grad phi (comoving, with mean subtraction when enabled) at n
+ * points: out = n*4 (phi, dphi/dx1, dphi/dx2, dphi/dx3).  rep: replica per
+ * point (replicated fields; NULL = 0).  Uses the context's precision. */
+int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const double *pts, const int32_t *rep,
+                   double *out);
+
+/* Step table of a trace: chi_s = chi(z_s) and the n_steps affine-parameter
+ * steps dlam (int of a^2 dchi between nodes on the unperturbed ray). */
+int rt3d_schedule(rt3d_ctx *ctx, double z_s, int kind, int n_steps, double chi_l, double s,
+                  double *dlam_out, double *chi_s_out);
+
+/* muPDF of a device bundle-result array as written by rt3d_trace_device
+ * (n*6 doubles: mu at offset 0, flags at offset 5), enqueued on stream.
+ * d_counts, d_wfix: device [bins] uint64; d_scalars: device 8 doubles
+ * (n_used, n_under, n_over, n_neg, n_bad, W_total, mean_w, sigma_w). */
+int rt3d_histogram_device(rt3d_ctx *ctx, void *stream, int64_t n, const double *d_bundle_out,
+                          const rt3d_hist_opts *o, uint64_t *d_counts, uint64_t *d_wfix, double *d_scalars);
+
+/* Counters of the last trace or batch. */
+int rt3d_get_stats(rt3d_ctx *ctx, rt3d_stats *out);
+
+const char *rt3d_status_string(int status);
+const char *rt3d_last_error(rt3d_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,834 @@
+// api.cu -- the C ABI (include/rt3d.h): context, particle staging, trace
+// orchestration, histogram, potential and schedule entry points.
+#include <math.h>
+#include <string.h>
+
+#include <algorithm>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "force.cuh"
+#include "rt3d_internal.cuh"
+
+namespace rt3d {
+cudaError_t dispatch_mixed(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
+cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
+
+// ---------------------------------------------------------------------------
+// particle staging (S2): FP64 input -> integer grid + scaled masses
+// ---------------------------------------------------------------------------
+// One block: bounding box, largest and total mass (Kahan), in a fixed order.
+__global__ void __launch_bounds__(1024) k_field_stats(int64_t n, const double *__restrict__ pos,
+                                                      const double *__restrict__ mass, double *out)
+{
+    __shared__ double s[8][1024];
+    double mn[3] = {1e300, 1e300, 1e300}, mx[3] = {-1e300, -1e300, -1e300}, mm = 0.0, sum = 0.0, c = 0.0;
+    for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
+        for (int d = 0; d < 3; ++d) {
+            mn[d] = fmin(mn[d], pos[3 * i + d]);
+            mx[d] = fmax(mx[d], pos[3 * i + d]);
+        }
+        mm = fmax(mm, mass[i]);
+        const double y = mass[i] - c, t = sum + y;
+        c = (t - sum) - y;
+        sum = t;
+    }
+    for (int d = 0; d < 3; ++d) {
+        s[d][threadIdx.x] = mn[d];
+        s[3 + d][threadIdx.x] = mx[d];
+    }
+    s[6][threadIdx.x] = mm;
+    s[7][threadIdx.x] = sum;
+    __syncthreads();
+    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
+        if (threadIdx.x < h) {
+            for (int d = 0; d < 3; ++d) {
+                s[d][threadIdx.x] = fmin(s[d][threadIdx.x], s[d][threadIdx.x + h]);
+                s[3 + d][threadIdx.x] = fmax(s[3 + d][threadIdx.x], s[3 + d][threadIdx.x + h]);
+            }
+            s[6][threadIdx.x] = fmax(s[6][threadIdx.x], s[6][threadIdx.x + h]);
+            s[7][threadIdx.x] += s[7][threadIdx.x + h];
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 8) out[threadIdx.x] = s[threadIdx.x][0];
+}
+
+// grid position q = round((p - O) 2^e) (isolated) or round(p 2^e) mod Lq
+// (replicated box); mass mu_G m 2^ms in FP32 bits and FP64; eps^2 in grid units
+__global__ void k_stage_particles(int64_t n, const double *__restrict__ pos, const double *__restrict__ mass,
+                                  const double *__restrict__ soft, int soft_pp, double soft0, int replicated,
+                                  long long Lq, double O0, double O1, double O2, double two_e, double mscale,
+                                  int4 *part, double *m64, float *eps2, double *eps2_64)
+{
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const double O[3] = {O0, O1, O2};
+    int q[3];
+    for (int d = 0; d < 3; ++d) {
+        long long v = __double2ll_rn((pos[3 * i + d] - O[d]) * two_e);
+        if (replicated) {
+            v %= Lq;
+            if (v < 0) v += Lq;
+        }
+        q[d] = (int)v;
+    }
+    const double m = kMuG * mass[i] * mscale;
+    part[i] = make_int4(q[0], q[1], q[2], __float_as_int((float)m));
+    m64[i] = m;
+    if (soft_pp) {
+        const double e = soft[i] * two_e;
+        eps2[i] = (float)(e * e);
+        eps2_64[i] = e * e;
+    }
+    (void)soft0;
+}
+
+int force_max_splits(const ForceShape &, int64_t n_particles)
+{
+    const int64_t t = (n_particles + kTile - 1) / kTile;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(t, 65535));
+}
+
+size_t partials_bytes(const ForceShape &sh, int64_t n_rays, bool)
+{
+    return (size_t)sh.splits * 4 * (size_t)n_rays * 8;
+}
+
+}  // namespace rt3d
+
+using namespace rt3d;
+
+// ---------------------------------------------------------------------------
+// context
+// ---------------------------------------------------------------------------
+struct FieldSlot {
+    bool loaded = false;
+    DevField df{};
+    int4 *d_part = nullptr;
+    float *d_eps2 = nullptr;
+    double *d_m64 = nullptr, *d_eps2_64 = nullptr;
+    int *d_rot = nullptr, *d_shift = nullptr;
+    int64_t n = 0;
+};
+
+struct rt3d_ctx {
+    int device = 0;
+    rt3d_options opt{};
+    std::string err;
+    bool have_cosmo = false;
+    Cosmo cosmo{};
+    std::vector<FieldSlot> fields;
+    Scratch scr;
+    cudaStream_t stream = nullptr;
+    cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+    rt3d_stats stats{};
+    double last_npart = 0.0;
+    bool stats_pending = false;
+    std::vector<cudaEvent_t> tev;  // per-launch timing events
+    int tev_used = 0;
+    unsigned long long *d_hist_u64 = nullptr;  // bins*2 + 5
+    double *d_hist_f64 = nullptr;              // 8
+    int hist_cap = 0;
+    double *d_io = nullptr;                    // staging for potential / histogram inputs
+    size_t d_io_n = 0;
+};
+
+static int fail(rt3d_ctx *c, int code, const char *msg)
+{
+    if (c) c->err = msg;
+    return code;
+}
+
+#define CK(call)                                                                              \
+    do {                                                                                      \
+        cudaError_t e_ = (call);                                                              \
+        if (e_ != cudaSuccess) {                                                              \
+            char b_[256];                                                                     \
+            snprintf(b_, sizeof b_, "%s failed: %s", #call, cudaGetErrorString(e_));          \
+            return fail(ctx, e_ == cudaErrorMemoryAllocation ? RT3D_ENOMEM : RT3D_ECUDA, b_); \
+        }                                                                                     \
+    } while (0)
+
+template <typename T>
+static cudaError_t grow(T *&p, size_t &cap, size_t need)
+{
+    if (need <= cap && p) return cudaSuccess;
+    if (p) cudaFree(p);
+    p = nullptr;
+    cap = 0;
+    cudaError_t e = cudaMalloc((void **)&p, std::max<size_t>(need, 1) * sizeof(T));
+    if (e == cudaSuccess) cap = need;
+    return e;
+}
+
+static void free_field(FieldSlot &s)
+{
+    cudaFree(s.d_part);
+    cudaFree(s.d_eps2);
+    cudaFree(s.d_m64);
+    cudaFree(s.d_eps2_64);
+    cudaFree(s.d_rot);
+    cudaFree(s.d_shift);
+    s = FieldSlot{};
+}
+
+extern "C" const char *rt3d_status_string(int s)
+{
+    switch (s) {
+    case RT3D_OK: return "ok";
+    case RT3D_EINVAL: return "invalid argument";
+    case RT3D_ENOMEM: return "out of memory";
+    case RT3D_ECUDA: return "CUDA error";
+    case RT3D_ETIMEOUT: return "device watchdog expired";
+    case RT3D_ENOTIMPL: return "not implemented";
+    case RT3D_ENOCOSMO: return "cosmology not set";
+    case RT3D_ENOFIELD: return "field not loaded";
+    default: return "unknown status";
+    }
+}
+
+extern "C" const char *rt3d_last_error(rt3d_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+extern "C" int rt3d_create(rt3d_ctx **out, int dev, const rt3d_options *opt)
+{
+    if (!out) return RT3D_EINVAL;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || dev < 0 || dev >= ndev) return RT3D_EINVAL;
+    rt3d_ctx *ctx = new (std::nothrow) rt3d_ctx();
+    if (!ctx) return RT3D_ENOMEM;
+    ctx->device = dev;
+    if (opt) ctx->opt = *opt;
+    if (ctx->opt.precision != RT3D_MIXED && ctx->opt.precision != RT3D_FP64) {
+        delete ctx;
+        return RT3D_EINVAL;
+    }
+    if (ctx->opt.christoffel != RT3D_CHRISTOFFEL_PAPER && ctx->opt.christoffel != RT3D_CHRISTOFFEL_DERIVED) {
+        delete ctx;
+        return RT3D_EINVAL;
+    }
+    ctx->fields.resize(RT3D_MAX_FIELDS);
+    int rc = RT3D_OK;
+    do {
+        if (cudaSetDevice(dev) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        if (cudaMalloc((void **)&ctx->scr.misc, 16 * sizeof(double)) != cudaSuccess) { rc = RT3D_ENOMEM; break; }
+        if (cudaMalloc((void **)&ctx->scr.counters, 8 * sizeof(unsigned long long)) != cudaSuccess) { rc = RT3D_ENOMEM; break; }
+    } while (0);
+    if (rc != RT3D_OK) {
+        rt3d_destroy(ctx);
+        return rc;
+    }
+    *out = ctx;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_destroy(rt3d_ctx *ctx)
+{
+    if (!ctx) return RT3D_EINVAL;
+    cudaSetDevice(ctx->device);
+    if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+    for (auto &f : ctx->fields) free_field(f);
+    Scratch &s = ctx->scr;
+    cudaFree(s.partials);
+    cudaFree(s.dlam);
+    cudaFree(s.misc);
+    cudaFree(s.counters);
+    cudaFree(s.state);
+    cudaFree(s.ints);
+    cudaFree(s.theta);
+    cudaFree(s.bout);
+    cudaFree(s.rout);
+    cudaFree(ctx->d_hist_u64);
+    cudaFree(ctx->d_hist_f64);
+    cudaFree(ctx->d_io);
+    for (auto e : ctx->tev) cudaEventDestroy(e);
+    if (ctx->ev0) cudaEventDestroy(ctx->ev0);
+    if (ctx->ev1) cudaEventDestroy(ctx->ev1);
+    if (ctx->stream) cudaStreamDestroy(ctx->stream);
+    delete ctx;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_set_cosmology(rt3d_ctx *ctx, double om, double ol, double h)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (!(om > 0.0) || !(ol > 0.0) || !(h > 0.0) || !isfinite(om + ol + h) || fabs(om + ol - 1.0) > 1e-12)
+        return fail(ctx, RT3D_EINVAL, "cosmology must be flat with omega_m, omega_l, h > 0");
+    Cosmo &c = ctx->cosmo;
+    c.om = om;
+    c.ol = ol;
+    c.h = h;
+    c.H0 = 100.0 * h / kCkms;
+    // Eq. lookbacksingularity with the argument sqrt(OL/OM), so that a(0) = 1
+    c.t0 = 2.0 / (3.0 * c.H0 * sqrt(ol)) * asinh(sqrt(ol / om));
+    c.k = 1.5 * sqrt(ol) * c.H0;
+    c.r = om / ol;
+    ctx->have_cosmo = true;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
+                                   const double *soft, int soft_pp, const rt3d_volume *vol)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS) return fail(ctx, RT3D_EINVAL, "field id out of range");
+    if (n < 0 || (n > 0 && (!pos || !mass)) || (!soft && n > 0)) return fail(ctx, RT3D_EINVAL, "null particle arrays");
+    if (n >= (int64_t)1 << 40) return fail(ctx, RT3D_EINVAL, "too many particles");
+    const bool repl = vol && vol->replicated;
+    for (int64_t i = 0; i < n; ++i) {
+        if (!isfinite(pos[3 * i]) || !isfinite(pos[3 * i + 1]) || !isfinite(pos[3 * i + 2]))
+            return fail(ctx, RT3D_EINVAL, "non-finite particle position");
+        if (!(mass[i] > 0.0) || !isfinite(mass[i])) return fail(ctx, RT3D_EINVAL, "particle masses must be > 0");
+        const double e = soft_pp ? soft[i] : soft[0];
+        if (!(e >= 0.0) || !isfinite(e)) return fail(ctx, RT3D_EINVAL, "softening must be >= 0");
+    }
+    if (n == 0 && soft && !(soft[0] >= 0.0)) return fail(ctx, RT3D_EINVAL, "softening must be >= 0");
+    double L = 0.0;
+    if (repl) {
+        L = vol->box_length;
+        if (!(L > 0.0) || !isfinite(L) || vol->n_replicas < 1 || !vol->rot || !vol->shift)
+            return fail(ctx, RT3D_EINVAL, "replicated volume needs box_length > 0 and replica transforms");
+        for (int j = 0; j < vol->n_replicas; ++j) {
+            const int32_t *R = vol->rot + 9 * j;
+            int colused = 0;
+            for (int r = 0; r < 3; ++r) {
+                int nz = 0;
+                for (int k = 0; k < 3; ++k)
+                    if (R[3 * r + k] != 0) {
+                        if (R[3 * r + k] != 1 && R[3 * r + k] != -1) return fail(ctx, RT3D_EINVAL, "rot must be a signed permutation");
+                        ++nz;
+                        colused |= 1 << k;
+                    }
+                if (nz != 1) return fail(ctx, RT3D_EINVAL, "rot must be a signed permutation");
+            }
+            if (colused != 7) return fail(ctx, RT3D_EINVAL, "rot must be a signed permutation");
+            for (int d = 0; d < 3; ++d)
+                if (!(vol->shift[3 * j + d] >= 0.0) || !(vol->shift[3 * j + d] < L))
+                    return fail(ctx, RT3D_EINVAL, "replica shift outside [0, L)");
+        }
+        for (int64_t i = 0; i < 3 * n; ++i)
+            if (pos[i] < 0.0 || pos[i] > L) return fail(ctx, RT3D_EINVAL, "box positions outside [0, L]");
+    }
+    CK(cudaSetDevice(ctx->device));
+    FieldSlot &slot = ctx->fields[field_id];
+    CK(cudaStreamSynchronize(ctx->stream));
+    free_field(slot);
+
+    const int64_t nn = std::max<int64_t>(n, 1);
+    double *d_pos = nullptr, *d_mass = nullptr, *d_soft = nullptr, *d_stats = nullptr;
+    int rc = RT3D_OK;
+    double st[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+    do {
+        if (cudaMalloc((void **)&d_pos, 3 * nn * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&d_mass, nn * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&d_soft, (soft_pp ? nn : 1) * sizeof(double)) != cudaSuccess ||
+            cudaMalloc((void **)&d_stats, 8 * sizeof(double)) != cudaSuccess) { rc = RT3D_ENOMEM; break; }
+        if (n > 0) {
+            if (cudaMemcpyAsync(d_pos, pos, 3 * n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+                cudaMemcpyAsync(d_mass, mass, n * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+                cudaMemcpyAsync(d_soft, soft, (soft_pp ? n : 1) * sizeof(double), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+            k_field_stats<<<1, 1024, 0, ctx->stream>>>(n, d_pos, d_mass, d_stats);
+            if (cudaGetLastError() != cudaSuccess ||
+                cudaMemcpyAsync(st, d_stats, 8 * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream) != cudaSuccess ||
+                cudaStreamSynchronize(ctx->stream) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        }
+        // grid: the finest 2^-e that holds the field in 2^30 (isolated, centred)
+        // or the box in 2^31 (replicated) grid units
+        DevField &f = slot.df;
+        f = DevField{};
+        int e = 40;
+        double O[3] = {0.0, 0.0, 0.0};
+        long long Lq = 0;
+        const double q22 = ldexp(1.0, -22);
+        if (repl) {
+            e = (int)floor(log2(2147483000.0 / L));
+            if (e > 40) e = 40;
+            Lq = llround(ldexp(L, e));
+            if (Lq & 1) Lq += 1;
+        } else if (n > 0) {
+            double H = 0.0;
+            for (int d = 0; d < 3; ++d) {
+                O[d] = nearbyint(0.5 * (st[d] + st[3 + d]) / q22) * q22;
+                H = std::max(H, std::max(fabs(st[3 + d] - O[d]), fabs(st[d] - O[d])));
+            }
+            if (H > 0.0) e = std::min(40, (int)floor(log2(1073741824.0 / H)));
+        }
+        const double two_e = ldexp(1.0, e);
+        const double mmax = kMuG * st[6];
+        const int ms = mmax > 0.0 ? -(int)nearbyint(log2(mmax)) : 0;
+        const double mscale = ldexp(1.0, ms);
+        if (cudaMalloc((void **)&slot.d_part, nn * sizeof(int4)) != cudaSuccess ||
+            cudaMalloc((void **)&slot.d_m64, nn * sizeof(double)) != cudaSuccess) { rc = RT3D_ENOMEM; break; }
+        if (soft_pp && (cudaMalloc((void **)&slot.d_eps2, nn * sizeof(float)) != cudaSuccess ||
+                        cudaMalloc((void **)&slot.d_eps2_64, nn * sizeof(double)) != cudaSuccess)) { rc = RT3D_ENOMEM; break; }
+        if (n > 0) {
+            k_stage_particles<<<(unsigned)((n + 255) / 256), 256, 0, ctx->stream>>>(
+                n, d_pos, d_mass, d_soft, soft_pp, soft[0], repl ? 1 : 0, repl ? Lq : 0, O[0], O[1], O[2], two_e,
+                mscale, slot.d_part, slot.d_m64, slot.d_eps2, slot.d_eps2_64);
+            if (cudaGetLastError() != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        }
+        if (repl) {
+            std::vector<int> rot(9 * vol->n_replicas), sh(3 * vol->n_replicas);
+            for (int j = 0; j < 9 * vol->n_replicas; ++j) rot[j] = vol->rot[j];
+            for (int j = 0; j < 3 * vol->n_replicas; ++j) {
+                long long v = llround(ldexp(vol->shift[j], e)) % Lq;
+                sh[j] = (int)v;
+            }
+            if (cudaMalloc((void **)&slot.d_rot, rot.size() * sizeof(int)) != cudaSuccess ||
+                cudaMalloc((void **)&slot.d_shift, sh.size() * sizeof(int)) != cudaSuccess) { rc = RT3D_ENOMEM; break; }
+            if (cudaMemcpyAsync(slot.d_rot, rot.data(), rot.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess ||
+                cudaMemcpyAsync(slot.d_shift, sh.data(), sh.size() * sizeof(int), cudaMemcpyHostToDevice, ctx->stream) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        }
+        if (cudaStreamSynchronize(ctx->stream) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        f.part = slot.d_part;
+        f.eps2 = slot.d_eps2;
+        f.m64 = slot.d_m64;
+        f.eps2_64 = slot.d_eps2_64;
+        f.rot = slot.d_rot;
+        f.shift = slot.d_shift;
+        f.n = n;
+        const double e0 = soft_pp ? 0.0 : soft[0] * two_e;
+        f.eps2u = (float)(e0 * e0);
+        f.eps2u64 = e0 * e0;
+        f.replicated = repl ? 1 : 0;
+        f.mean_subtract = (repl && vol->mean_subtract) ? 1 : 0;
+        f.n_rep = repl ? vol->n_replicas : 1;
+        f.Lq = (int)Lq;
+        f.delta = ldexp(1.0, -e);
+        f.inv_delta = two_e;
+        f.O[0] = O[0];
+        f.O[1] = O[1];
+        f.O[2] = O[2];
+        f.L = repl ? (double)Lq * f.delta : 0.0;
+        f.mscale_inv = ldexp(1.0, -ms);
+        f.rho_term = repl ? kMuG * st[7] / (f.L * f.L * f.L) : 0.0;
+        slot.n = n;
+        slot.loaded = true;
+    } while (0);
+    cudaFree(d_pos);
+    cudaFree(d_mass);
+    cudaFree(d_soft);
+    cudaFree(d_stats);
+    if (rc != RT3D_OK) {
+        free_field(slot);
+        return fail(ctx, rc, "particle staging failed");
+    }
+    return RT3D_OK;
+}
+
+// ---------------------------------------------------------------------------
+// launch shape
+// ---------------------------------------------------------------------------
+static ForceShape choose_shape(rt3d_ctx *ctx, int64_t n_points, int64_t n_particles, bool fp64)
+{
+    ForceShape sh;
+    if (fp64) {
+        sh.R = 2;
+        sh.NT = 128;
+    } else {
+        sh.R = ctx->opt.rays_per_thread > 0 ? ctx->opt.rays_per_thread : 4;
+        sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : 128;
+    }
+    const int64_t per_block = (int64_t)sh.R * sh.NT;
+    const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
+    int S;
+    if (ctx->opt.splits > 0) {
+        S = ctx->opt.splits;
+    } else {
+        const int64_t target = 152 * 4 * 2;  // two waves of four blocks per SM
+        S = (int)std::max<int64_t>(1, (target + nrb - 1) / nrb);
+    }
+    const int tiles = force_max_splits(sh, n_particles);
+    S = std::min(S, tiles);
+    // balance: whole tiles per split, then the number of splits actually used
+    const int64_t tps = (tiles + S - 1) / S;
+    S = (int)((tiles + tps - 1) / tps);
+    sh.splits = std::max(1, S);
+    return sh;
+}
+
+static int64_t per_split_of(const ForceShape &sh, int64_t n_particles)
+{
+    const int64_t tiles = std::max<int64_t>(1, (n_particles + kTile - 1) / kTile);
+    return ((tiles + sh.splits - 1) / sh.splits) * kTile;
+}
+
+static cudaError_t run_force(rt3d_ctx *ctx, const DevField &f, const double *px, const double *py, const double *pz,
+                             const int *rep, int group, int64_t n, const ForceShape &sh, bool fp64, void *partials,
+                             const unsigned long long *gate, cudaStream_t st)
+{
+    ForceArgs A;
+    A.f = f;
+    A.px = px;
+    A.py = py;
+    A.pz = pz;
+    A.rep = rep;
+    A.group = group;
+    A.n = n;
+    A.per_split = per_split_of(sh, f.n);
+    A.out = partials;
+    A.gate = gate;
+    (void)ctx;
+    return fp64 ? dispatch_fp64(A, sh, st) : dispatch_mixed(A, sh, st);
+}
+
+// ---------------------------------------------------------------------------
+// trace orchestration
+// ---------------------------------------------------------------------------
+static int check_bundle_opts(rt3d_ctx *ctx, const rt3d_bundle_opts *b)
+{
+    if (!b) return fail(ctx, RT3D_EINVAL, "null bundle options");
+    if (b->n_ring < 2 || b->n_ring > 8) return fail(ctx, RT3D_EINVAL, "n_ring must be 2..8");
+    if (!(b->theta_r > 0.0) || !isfinite(b->theta_r) || !isfinite(b->phase)) return fail(ctx, RT3D_EINVAL, "bad theta_r/phase");
+    if (b->n_steps < 1 || b->n_steps > 10000000) return fail(ctx, RT3D_EINVAL, "n_steps out of range");
+    if (b->max_extra < 0 || b->max_extra > 64) return fail(ctx, RT3D_EINVAL, "max_extra must be 0..64");
+    if (b->schedule == RT3D_SCHED_ASINH) {
+        if (!(b->asinh_s > 0.0) || !isfinite(b->lens_chi)) return fail(ctx, RT3D_EINVAL, "asinh schedule needs s > 0");
+    } else if (b->schedule != RT3D_SCHED_UNIFORM) {
+        return fail(ctx, RT3D_EINVAL, "unknown schedule");
+    }
+    return RT3D_OK;
+}
+
+static cudaEvent_t timing_event(rt3d_ctx *ctx)
+{
+    if (ctx->tev_used == (int)ctx->tev.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+        ctx->tev.push_back(e);
+    }
+    return ctx->tev[ctx->tev_used++];
+}
+
+static int ensure_trace_scratch(rt3d_ctx *ctx, int64_t n_b, int nr, int n_steps, const ForceShape &sh)
+{
+    Scratch &s = ctx->scr;
+    const int64_t n_rays = n_b * nr;
+    CK(grow(s.state, s.state_rays, (size_t)(32 * n_rays)));
+    CK(grow(s.ints, s.ints_n, (size_t)(2 * n_rays + 2 * n_b)));
+    CK(grow(s.dlam, s.dlam_n, (size_t)n_steps));
+    size_t pb = partials_bytes(sh, n_rays, false);
+    CK(grow(*(char **)&s.partials, s.partials_bytes, pb));
+    return RT3D_OK;
+}
+
+static RayState make_state(rt3d_ctx *ctx, int64_t n_b, int nr)
+{
+    Scratch &s = ctx->scr;
+    RayState rs;
+    rs.n_rays = n_b * nr;
+    rs.n_b = n_b;
+    rs.nr = nr;
+    rs.y = s.state;
+    rs.ys = s.state + 8 * rs.n_rays;
+    rs.ks = s.state + 16 * rs.n_rays;
+    rs.fin = s.state + 24 * rs.n_rays;
+    rs.done = s.ints;
+    rs.steps = s.ints + rs.n_rays;
+    rs.rep = s.ints + 2 * rs.n_rays;
+    return rs;
+}
+
+// enqueue one full trace on st: schedule, init, RK4 stages, reduce
+static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t n_b, const double *d_theta,
+                         const rt3d_bundle_opts *b, double *d_bout, double *d_rout, cudaStream_t st, bool timed)
+{
+    const bool fp64 = ctx->opt.precision == RT3D_FP64;
+    const int nr = 1 + b->n_ring;
+    const int64_t n_rays = n_b * nr;
+    ForceShape sh = choose_shape(ctx, n_rays, fs.n, fp64);
+    int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
+    if (rc) return rc;
+    RayState rs = make_state(ctx, n_b, nr);
+    TraceParams tp;
+    tp.cosmo = ctx->cosmo;
+    tp.chi_s = 0.0;
+    tp.n_ring = b->n_ring;
+    tp.theta_r = b->theta_r;
+    tp.phase = b->phase;
+    tp.christoffel = ctx->opt.christoffel;
+    tp.n_steps = b->n_steps;
+    tp.max_extra = b->max_extra;
+    Scratch &s = ctx->scr;
+    int64_t launches = 0, flaunch = 0;
+    ctx->tev_used = 0;
+    CK(launch_schedule(ctx->cosmo, z_s, b->schedule, b->n_steps, b->lens_chi, b->asinh_s, s.dlam, s.misc, st));
+    CK(launch_init(tp, fs.df, d_theta, rs, s.counters, st));
+    launches += 2;
+    const int total = b->n_steps + b->max_extra;
+    for (int step = 0; step < total; ++step) {
+        for (int stage = 0; stage < 4; ++stage) {
+            const int g = step * 4 + stage;
+            const unsigned long long *gate = step >= b->n_steps ? s.counters + ((step - 1) & 1) : nullptr;
+            cudaEvent_t e0 = nullptr, e1 = nullptr;
+            if (timed && !gate) {
+                e0 = timing_event(ctx);
+                e1 = timing_event(ctx);
+                if (e0) CK(cudaEventRecord(e0, st));
+            }
+            CK(run_force(ctx, fs.df, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, rs.rep + (g & 1) * n_b,
+                         nr, n_rays, sh, fp64, s.partials, gate, st));
+            if (e1) CK(cudaEventRecord(e1, st));
+            CK(launch_stage(tp, fs.df, rs, sh, fp64, s.partials, s.dlam, s.misc, step, stage, s.counters, st));
+            launches += 2;
+            flaunch += gate ? 0 : 1;
+        }
+    }
+    CK(launch_reduce(tp, d_theta, rs, s.misc, d_bout, d_rout, st));
+    launches += 1;
+    ctx->stats.launches = launches;
+    ctx->stats.force_launches = flaunch;
+    ctx->stats.steps = total;
+    ctx->stats.rays_per_thread = sh.R;
+    ctx->stats.threads_per_block = sh.NT;
+    ctx->stats.splits = sh.splits;
+    ctx->last_npart = (double)fs.n;
+    ctx->stats_pending = true;
+    return RT3D_OK;
+}
+
+static int finish_stats(rt3d_ctx *ctx)
+{
+    if (!ctx->stats_pending) return RT3D_OK;
+    unsigned long long c[3];
+    CK(cudaMemcpy(c, ctx->scr.counters, sizeof c, cudaMemcpyDeviceToHost));
+    ctx->stats.interactions = (double)c[2] * ctx->last_npart;
+    double fms = 0.0;
+    for (int i = 0; i + 1 < ctx->tev_used; i += 2) {
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, ctx->tev[i], ctx->tev[i + 1]) == cudaSuccess) fms += ms;
+    }
+    ctx->stats.force_ms = fms;
+    ctx->stats_pending = false;
+    return RT3D_OK;
+}
+
+static int check_trace_args(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, const rt3d_bundle_opts *b)
+{
+    if (!ctx->have_cosmo) return fail(ctx, RT3D_ENOCOSMO, "set the cosmology first");
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS || !ctx->fields[field_id].loaded)
+        return fail(ctx, RT3D_ENOFIELD, "field not loaded");
+    if (!(z_s > 0.0) || !isfinite(z_s) || z_s > 20.0) return fail(ctx, RT3D_EINVAL, "z_s must be in (0, 20]");
+    if (n_b < 1 || n_b > ((int64_t)1 << 28)) return fail(ctx, RT3D_EINVAL, "n_bundles out of range");
+    return check_bundle_opts(ctx, b);
+}
+
+extern "C" int rt3d_trace(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, const double *theta,
+                          const rt3d_bundle_opts *b, rt3d_bundle_result *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
+    if (rc) return rc;
+    if (!theta || !out || !out->mu) return fail(ctx, RT3D_EINVAL, "null theta or result arrays");
+    for (int64_t i = 0; i < 2 * n_b; ++i)
+        if (!isfinite(theta[i])) return fail(ctx, RT3D_EINVAL, "non-finite theta");
+    CK(cudaSetDevice(ctx->device));
+    const int nr = 1 + b->n_ring;
+    const int64_t n_rays = n_b * nr;
+    Scratch &s = ctx->scr;
+    CK(grow(s.theta, s.theta_n, (size_t)(2 * n_b)));
+    CK(grow(s.bout, s.bout_n, (size_t)(6 * n_b)));
+    const bool want_rays = out->ray_state != nullptr;
+    if (want_rays) CK(grow(s.rout, s.rout_n, (size_t)(8 * n_rays)));
+    cudaStream_t st = ctx->stream;
+    CK(cudaEventRecord(ctx->ev0, st));
+    CK(cudaMemcpyAsync(s.theta, theta, 2 * n_b * sizeof(double), cudaMemcpyHostToDevice, st));
+    rc = enqueue_trace(ctx, ctx->fields[field_id], z_s, n_b, s.theta, b, s.bout, want_rays ? s.rout : nullptr, st,
+                       ctx->opt.time_kernels != 0);
+    if (rc) return rc;
+    std::vector<double> bo((size_t)(6 * n_b));
+    CK(cudaMemcpyAsync(bo.data(), s.bout, 6 * n_b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (want_rays) CK(cudaMemcpyAsync(out->ray_state, s.rout, 8 * n_rays * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (out->ray_steps)
+        CK(cudaMemcpyAsync(out->ray_steps, ctx->scr.ints + n_rays, n_rays * sizeof(int), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    ctx->stats.device_ms = ms;
+    rc = finish_stats(ctx);
+    if (rc) return rc;
+    for (int64_t i = 0; i < n_b; ++i) {
+        out->mu[i] = bo[6 * i];
+        if (out->kappa) out->kappa[i] = bo[6 * i + 1];
+        if (out->gamma1) out->gamma1[i] = bo[6 * i + 2];
+        if (out->gamma2) out->gamma2[i] = bo[6 * i + 3];
+        if (out->omega) out->omega[i] = bo[6 * i + 4];
+        if (out->flags) out->flags[i] = (int32_t)bo[6 * i + 5];
+    }
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_b,
+                                 const double *d_theta, const rt3d_bundle_opts *b, double *d_bundle_out,
+                                 double *d_ray_out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
+    if (rc) return rc;
+    if (!d_theta || !d_bundle_out) return fail(ctx, RT3D_EINVAL, "null device arrays");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = (cudaStream_t)stream;
+    return enqueue_trace(ctx, ctx->fields[field_id], z_s, n_b, d_theta, b, d_bundle_out, d_ray_out, st,
+                         ctx->opt.time_kernels != 0);
+}
+
+extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const rt3d_bundle_opts *b,
+                                rt3d_bundle_result *outs)
+{
+    if (!ctx) return RT3D_EINVAL;
+    (void)n_cones;
+    (void)cones;
+    (void)b;
+    (void)outs;
+    return fail(ctx, RT3D_ENOTIMPL, "batched trace not built yet");
+}
+
+static int ensure_hist(rt3d_ctx *ctx, int bins)
+{
+    if (bins > ctx->hist_cap) {
+        cudaFree(ctx->d_hist_u64);
+        cudaFree(ctx->d_hist_f64);
+        ctx->d_hist_u64 = nullptr;
+        ctx->d_hist_f64 = nullptr;
+        ctx->hist_cap = 0;
+        CK(cudaMalloc((void **)&ctx->d_hist_u64, (2 * (size_t)bins + 8) * sizeof(unsigned long long)));
+        CK(cudaMalloc((void **)&ctx->d_hist_f64, 8 * sizeof(double)));
+        ctx->hist_cap = bins;
+    }
+    return RT3D_OK;
+}
+
+static int check_hist(rt3d_ctx *ctx, const rt3d_hist_opts *o)
+{
+    if (!o || o->bins < 1 || o->bins > (1 << 20) || !(o->mu_min > 0.0) || !(o->mu_max > o->mu_min) ||
+        !isfinite(o->mu_max))
+        return fail(ctx, RT3D_EINVAL, "histogram needs bins >= 1 and 0 < mu_min < mu_max");
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const int32_t *flags,
+                              const rt3d_hist_opts *o, rt3d_hist *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    int rc = check_hist(ctx, o);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !mu) || !out || !out->counts || !out->wfix) return fail(ctx, RT3D_EINVAL, "null arrays");
+    CK(cudaSetDevice(ctx->device));
+    rc = ensure_hist(ctx, o->bins);
+    if (rc) return rc;
+    cudaStream_t st = ctx->stream;
+    const size_t need = (size_t)std::max<int64_t>(n, 1) * 2;
+    CK(grow(ctx->d_io, ctx->d_io_n, need));
+    double *d_mu = ctx->d_io;
+    int *d_fl = flags ? (int *)(ctx->d_io + std::max<int64_t>(n, 1)) : nullptr;
+    if (n > 0) CK(cudaMemcpyAsync(d_mu, mu, n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (flags && n > 0) CK(cudaMemcpyAsync(d_fl, flags, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    unsigned long long *cnt = ctx->d_hist_u64, *wf = cnt + o->bins, *sc = wf + o->bins;
+    CK(launch_histogram(n, d_mu, 1, d_fl, nullptr, o->bins, o->mu_min, o->mu_max, cnt, wf, sc, ctx->d_hist_f64, st));
+    double o8[8];
+    CK(cudaMemcpyAsync(out->counts, cnt, o->bins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out->wfix, wf, o->bins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(o8, ctx->d_hist_f64, sizeof o8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->n_used = (int64_t)o8[0];
+    out->n_under = (int64_t)o8[1];
+    out->n_over = (int64_t)o8[2];
+    out->n_neg = (int64_t)o8[3];
+    out->n_bad = (int64_t)o8[4];
+    out->W_total = o8[5];
+    out->mean_w = o8[6];
+    out->sigma_w = o8[7];
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_histogram_device(rt3d_ctx *ctx, void *stream, int64_t n, const double *d_bundle_out,
+                                     const rt3d_hist_opts *o, uint64_t *d_counts, uint64_t *d_wfix,
+                                     double *d_scalars)
+{
+    if (!ctx) return RT3D_EINVAL;
+    int rc = check_hist(ctx, o);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && !d_bundle_out) || !d_counts || !d_wfix || !d_scalars)
+        return fail(ctx, RT3D_EINVAL, "null device arrays");
+    CK(cudaSetDevice(ctx->device));
+    rc = ensure_hist(ctx, o->bins);
+    if (rc) return rc;
+    cudaStream_t st = (cudaStream_t)stream;
+    unsigned long long *sc = ctx->d_hist_u64 + 2 * o->bins;
+    CK(launch_histogram(n, d_bundle_out, 6, nullptr, d_bundle_out + 5, o->bins, o->mu_min, o->mu_max,
+                        (unsigned long long *)d_counts, (unsigned long long *)d_wfix, sc, d_scalars, st));
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const double *pts, const int32_t *rep,
+                              double *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS || !ctx->fields[field_id].loaded)
+        return fail(ctx, RT3D_ENOFIELD, "field not loaded");
+    if (n < 1 || !pts || !out) return fail(ctx, RT3D_EINVAL, "need n >= 1 points");
+    const FieldSlot &fs = ctx->fields[field_id];
+    for (int64_t i = 0; i < n; ++i) {
+        if (!isfinite(pts[3 * i]) || !isfinite(pts[3 * i + 1]) || !isfinite(pts[3 * i + 2]))
+            return fail(ctx, RT3D_EINVAL, "non-finite point");
+        if (rep && (rep[i] < 0 || rep[i] >= fs.df.n_rep)) return fail(ctx, RT3D_EINVAL, "replica index out of range");
+    }
+    CK(cudaSetDevice(ctx->device));
+    const bool fp64 = ctx->opt.precision == RT3D_FP64;
+    ForceShape sh = choose_shape(ctx, n, fs.n, fp64);
+    Scratch &s = ctx->scr;
+    CK(grow(*(char **)&s.partials, s.partials_bytes, partials_bytes(sh, n, fp64)));
+    CK(grow(ctx->d_io, ctx->d_io_n, (size_t)(3 * n + 4 * n + n)));
+    double *d_pts = ctx->d_io, *d_out = ctx->d_io + 3 * n;
+    int *d_rep = rep ? (int *)(ctx->d_io + 7 * n) : nullptr;
+    std::vector<double> soa((size_t)(3 * n));
+    for (int64_t i = 0; i < n; ++i)
+        for (int d = 0; d < 3; ++d) soa[d * n + i] = pts[3 * i + d];
+    cudaStream_t st = ctx->stream;
+    CK(cudaMemcpyAsync(d_pts, soa.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
+    if (rep) CK(cudaMemcpyAsync(d_rep, rep, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    CK(run_force(ctx, fs.df, d_pts, d_pts + n, d_pts + 2 * n, d_rep, 1, n, sh, fp64, s.partials, nullptr, st));
+    CK(launch_stage_field(fs.df, sh, fp64, s.partials, d_pts, d_rep, n, d_out, st));
+    CK(cudaMemcpyAsync(out, d_out, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_schedule(rt3d_ctx *ctx, double z_s, int kind, int n_steps, double chi_l, double s,
+                             double *dlam_out, double *chi_s_out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (!ctx->have_cosmo) return fail(ctx, RT3D_ENOCOSMO, "set the cosmology first");
+    if (!(z_s > 0.0) || n_steps < 1 || !dlam_out || (kind != RT3D_SCHED_UNIFORM && kind != RT3D_SCHED_ASINH) ||
+        (kind == RT3D_SCHED_ASINH && !(s > 0.0)))
+        return fail(ctx, RT3D_EINVAL, "bad schedule arguments");
+    CK(cudaSetDevice(ctx->device));
+    Scratch &sc = ctx->scr;
+    CK(grow(sc.dlam, sc.dlam_n, (size_t)n_steps));
+    cudaStream_t st = ctx->stream;
+    CK(launch_schedule(ctx->cosmo, z_s, kind, n_steps, chi_l, s, sc.dlam, sc.misc, st));
+    CK(cudaMemcpyAsync(dlam_out, sc.dlam, n_steps * sizeof(double), cudaMemcpyDeviceToHost, st));
+    double chi = 0.0;
+    CK(cudaMemcpyAsync(&chi, sc.misc, sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (chi_s_out) *chi_s_out = chi;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_get_stats(rt3d_ctx *ctx, rt3d_stats *out)
+{
+    if (!ctx || !out) return RT3D_EINVAL;
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->stats_pending) {
+        CK(cudaDeviceSynchronize());
+        int rc = finish_stats(ctx);
+        if (rc) return rc;
+    }
+    *out = ctx->stats;
+    return RT3D_OK;
+}

@@ -1,0 +1,237 @@
+// rt3d_internal.cuh -- shared definitions of the sm_103a ray-bundle library.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/rt3d.h"
+
+namespace rt3d {
+
+// ---------------------------------------------------------------------------
+// physical constants (IAU nominal G Msun, SI c, Mpc)
+// ---------------------------------------------------------------------------
+constexpr double kGMsun = 1.32712440018e20;          // m^3 s^-2
+constexpr double kC = 299792458.0;                   // m s^-1
+constexpr double kMpc = 3.0856775814913673e22;       // m
+constexpr double kMuG = kGMsun / (kC * kC) / kMpc;   // G Msun / c^2 in Mpc
+constexpr double kCkms = 299792.458;                 // c in km s^-1
+
+struct Cosmo {
+    double om, ol, h;
+    double H0;  // H0 / c in 1/Mpc
+    double t0;  // lookback time of the big bang (Mpc)
+    double k;   // 1.5 sqrt(OL) H0
+    double r;   // OM / OL
+};
+
+// Eq. scalefac2: a(t) for t the lookback time.
+__device__ __forceinline__ double cosmo_a(const Cosmo &c, double t)
+{
+    double s = sinh(c.k * (c.t0 - t));
+    return cbrt(c.r * s * s);
+}
+
+// d a / d t (lookback): -a H(a) for the same flat Lemaitre model.
+__device__ __forceinline__ double cosmo_adot(const Cosmo &c, double a)
+{
+    return -a * c.H0 * sqrt(c.om / (a * a * a) + c.ol);
+}
+
+// ---------------------------------------------------------------------------
+// field of a uniform rectangular prism (mean subtraction, Sec. 3.3):
+// I = int dV / |r - r'| and dI/dr, from the closed-form antiderivative.
+// ---------------------------------------------------------------------------
+// log(u + rho) with rho = |(u, v, w)|, q = v^2 + w^2; stable for u < 0.
+template <typename T>
+__device__ __forceinline__ T prism_log(T u, T rho, T q)
+{
+    if (u >= T(0)) return log(u + rho);
+    if (q == T(0)) return T(0);  // only ever multiplied by a zero coefficient
+    return log(q / (rho - u));
+}
+
+template <typename T>
+__device__ __forceinline__ void prism_corner(T x, T y, T z, T &F, T &Hx, T &Hy, T &Hz)
+{
+    T xx = x * x, yy = y * y, zz = z * z;
+    T rho = sqrt(xx + yy + zz);
+    T lx = prism_log(x, rho, yy + zz), ly = prism_log(y, rho, xx + zz), lz = prism_log(z, rho, xx + yy);
+    T tx = (x != T(0)) ? atan(y * z / (x * rho)) : T(0);
+    T ty = (y != T(0)) ? atan(z * x / (y * rho)) : T(0);
+    T tz = (z != T(0)) ? atan(x * y / (z * rho)) : T(0);
+    F = x * y * lz + y * z * lx + z * x * ly - T(0.5) * (xx * tx + yy * ty + zz * tz);
+    Hx = y * lz + z * ly - x * tx;
+    Hy = z * lx + x * lz - y * ty;
+    Hz = x * ly + y * lx - z * tz;
+}
+
+// out = (I, dI/dx1, dI/dx2, dI/dx3) for the prism [lo, hi] at point p.
+template <typename T>
+__device__ __forceinline__ void prism_field(const T lo[3], const T hi[3], const T p[3], T out[4])
+{
+    T I = 0, gx = 0, gy = 0, gz = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const T x = ((c & 1) ? hi[0] : lo[0]) - p[0];
+        const T y = ((c & 2) ? hi[1] : lo[1]) - p[1];
+        const T z = ((c & 4) ? hi[2] : lo[2]) - p[2];
+        T F, Hx, Hy, Hz;
+        prism_corner(x, y, z, F, Hx, Hy, Hz);
+        // inclusion-exclusion over the corners: (-1)^(number of lower limits)
+        const T sg = ((3 - __popc(c)) & 1) ? T(-1) : T(1);
+        I += sg * F;
+        gx -= sg * Hx;
+        gy -= sg * Hy;
+        gz -= sg * Hz;
+    }
+    out[0] = I;
+    out[1] = gx;
+    out[2] = gy;
+    out[3] = gz;
+}
+
+// ---------------------------------------------------------------------------
+// device-side particle field
+// ---------------------------------------------------------------------------
+struct DevField {
+    const int4 *part;      // (qx, qy, qz, m32 bits): integer grid position, scaled mass (FP32)
+    const float *eps2;     // per-particle eps^2 in grid units^2, or nullptr
+    const double *m64;     // scaled masses (FP64 path)
+    const double *eps2_64; // per-particle eps^2 (FP64 path) or nullptr
+    const int *rot;        // n_rep * 9
+    const int *shift;      // n_rep * 3, grid units
+    int64_t n;
+    float eps2u;           // uniform eps^2 (grid units^2)
+    double eps2u64;
+    int replicated, mean_subtract, n_rep;
+    int Lq;                // box length in grid units (replicated)
+    double delta, inv_delta;  // grid spacing 2^-e (Mpc) and its inverse
+    double O[3];           // world position of grid origin (isolated fields)
+    double L;              // box length (Mpc)
+    double mscale_inv;     // 1 / 2^ms (masses are stored as mu_G m 2^ms)
+    double rho_term;       // mu_G * mean density (mean subtraction), Mpc^-2
+};
+
+// world position of the grid origin of replica j (replicated) or the field origin
+__device__ __forceinline__ void frame_origin(const DevField &f, int j, double o[3])
+{
+    if (f.replicated) {
+        o[0] = -0.5 * f.L;
+        o[1] = -0.5 * f.L;
+        o[2] = (double)j * f.L;
+    } else {
+        o[0] = f.O[0];
+        o[1] = f.O[1];
+        o[2] = f.O[2];
+    }
+}
+
+// replica transform of a box-frame grid position (exact integer arithmetic):
+// q' = wrap(R (q - c) + c + s), c = Lq/2
+__device__ __forceinline__ void replica_q(const DevField &f, int j, int qx, int qy, int qz, long long out[3])
+{
+    const long long c = f.Lq / 2;
+    const long long d[3] = {qx - c, qy - c, qz - c};
+    const int *R = f.rot + 9 * j;
+    const int *S = f.shift + 3 * j;
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        long long v = (long long)R[3 * r] * d[0] + (long long)R[3 * r + 1] * d[1] + (long long)R[3 * r + 2] * d[2];
+        v += c + S[r];
+        if (v >= f.Lq) v -= f.Lq;
+        if (v >= f.Lq) v -= f.Lq;
+        if (v < 0) v += f.Lq;
+        out[r] = v;
+    }
+}
+
+__device__ __forceinline__ int replica_of(const DevField &f, double x3)
+{
+    if (!f.replicated) return 0;
+    double q = floor(x3 / f.L);
+    if (q < 0.0) return 0;
+    if (q > (double)(f.n_rep - 1)) return f.n_rep - 1;
+    return (int)q;
+}
+
+// ---------------------------------------------------------------------------
+// ray state (SoA, FP64): index [component * n_rays + ray]
+// ---------------------------------------------------------------------------
+struct RayState {
+    double *y;     // 8 x nr  current state
+    double *ys;    // 8 x nr  stage state (positions read by the pair sum)
+    double *ks;    // 8 x nr  RK4 accumulator
+    double *fin;   // 8 x nr  state interpolated to x3 = chi_s
+    int *done;     // nr
+    int *steps;    // nr
+    int *rep;      // n_bundles: replica for the current stage
+    int64_t n_rays, n_b;
+    int nr;        // rays per bundle (1 + n_ring)
+};
+
+struct TraceParams {
+    Cosmo cosmo;
+    double chi_s;
+    int n_ring;
+    double theta_r, phase;
+    int christoffel;
+    int n_steps, max_extra;
+};
+
+// force launch shape
+struct ForceShape {
+    int R;       // rays per thread
+    int NT;      // threads per block
+    int splits;  // particle splits
+};
+
+// device scratch of a trace (grow-only, owned by the context)
+struct Scratch {
+    void *partials = nullptr;      // splits * 4 * n_rays (float2 or double)
+    size_t partials_bytes = 0;
+    double *dlam = nullptr;        // n_steps
+    size_t dlam_n = 0;
+    double *misc = nullptr;        // [0] chi_s, [1..] spare
+    unsigned long long *counters = nullptr; // [0] active-after slot 0, [1] slot 1, [2] active ray-stages
+    double *state = nullptr;       // 32 * n_rays
+    size_t state_rays = 0;
+    int *ints = nullptr;           // 2 * n_rays + n_b
+    size_t ints_n = 0;
+    double *theta = nullptr;       // n_b * 2
+    size_t theta_n = 0;
+    double *bout = nullptr;        // n_b * 6
+    size_t bout_n = 0;
+    double *rout = nullptr;        // n_rays * 8
+    size_t rout_n = 0;
+};
+
+// kernels (launch wrappers; return cudaError_t of the launch)
+cudaError_t launch_schedule(const Cosmo &c, double z_s, int kind, int n, double chi_l, double s,
+                            double *d_dlam, double *d_misc, cudaStream_t st);
+cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *d_theta, RayState rs,
+                        unsigned long long *d_counters, cudaStream_t st);
+cudaError_t launch_force(const DevField &f, const RayState &rs, const ForceShape &sh, bool fp64,
+                         void *d_partials, const unsigned long long *d_active, int gate, cudaStream_t st);
+cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, const ForceShape &sh,
+                         bool fp64, const void *d_partials, const double *d_dlam, const double *d_misc,
+                         int step, int stage, unsigned long long *d_counters, cudaStream_t st);
+cudaError_t launch_reduce(const TraceParams &tp, const double *d_theta, RayState rs, const double *d_misc,
+                          double *d_bout, double *d_rout, cudaStream_t st);
+cudaError_t launch_histogram(int64_t n, const double *d_mu, int mu_stride, const int *d_flags,
+                             const double *d_flagsd, int bins, double mu_min, double mu_max,
+                             unsigned long long *d_counts, unsigned long long *d_wfix,
+                             unsigned long long *d_scal, double *d_out8, cudaStream_t st);
+cudaError_t launch_potential(const DevField &f, bool fp64, const double *d_pts, const int *d_rep,
+                             int64_t n, const ForceShape &sh, void *d_partials, double *d_out,
+                             cudaStream_t st);
+cudaError_t launch_stage_field(const DevField &f, const ForceShape &sh, bool fp64, const void *d_partials,
+                               const double *d_pts, const int *d_rep, int64_t n, double *d_out,
+                               cudaStream_t st);
+
+int force_max_splits(const ForceShape &sh, int64_t n_particles);
+size_t partials_bytes(const ForceShape &sh, int64_t n_rays, bool fp64);
+
+}  // namespace rt3d

@@ -1,0 +1,31 @@
+"""Parity at the benchmark's full size and launch configuration: the NFW-halo
+workload (100,000 particles, 4096 bundles, 2000 RK4 steps) traced on the GPU
+exactly as bench.py times it; the oracle recomputes 16 sampled bundles."""
+import numpy as np
+import pytest
+
+import inputs
+from _cases import gpu_load, rel_alpha, rel_mu, run_oracle, trace_kw
+
+pytestmark = pytest.mark.gpu
+
+
+def test_nfw_full_size_sampled(cosmo):
+    import paper_1110_4894_gb300 as P
+    cfg = inputs.config_c2()
+    ctx = P.Context(0, precision=P.MIXED, time_kernels=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    nb = cfg["theta"].shape[0]
+    assert np.all(g["flags"] & (P.F_NOCROSS | P.F_NONFINITE) == 0)
+    idx = np.linspace(0, nb - 1, 16).astype(int)
+    o = run_oracle(cfg, cfg["theta"][idx], cosmo)
+    assert np.array_equal(g["flags"][idx], o.flags)
+    dm = rel_mu(g["mu"][idx], o.mu)
+    da = rel_alpha(g["rays"][idx], o)
+    assert dm.max() < 1e-4, dm
+    assert da.max() < 1e-5, da
+    st = ctx.stats()
+    # every active ray meets every particle at every stage
+    assert st["interactions"] >= nb * 5 * 100000 * 4 * cfg["n_steps"] * 0.99

@@ -1,0 +1,232 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle on the same
+seeded inputs.  Gates: mixed precision |d alpha/alpha| <= 1e-5 per ray and
+|d mu/mu| <= 1e-4 per bundle; the all-FP64 path agrees to rounding."""
+import math
+
+import numpy as np
+import pytest
+
+import inputs
+import oracle
+from _cases import gpu_load, oracle_field, rel_alpha, rel_mu, run_oracle, trace_kw
+
+pytestmark = pytest.mark.gpu
+
+ALPHA_GATE, MU_GATE = 1e-5, 1e-4
+
+
+@pytest.fixture(scope="module")
+def P():
+    import paper_1110_4894_gb300 as P
+    return P
+
+
+def ctx_for(P, precision, **kw):
+    c = P.Context(0, precision=precision, **kw)
+    c.set_cosmology(0.3, 0.7, 0.7)
+    return c
+
+
+def test_schedule_matches_oracle(P, cosmo):
+    ctx = ctx_for(P, P.MIXED)
+    for z_s, kind, n, chi_l, s in ((0.5, 0, 1000, 0.0, 1.0), (0.5, 1, 2000, cosmo.chi(0.25), 5e-3),
+                                   (1.3, 0, 37, 0.0, 1.0), (0.3, 1, 500, 600.0, 0.02)):
+        dl, chi = ctx.schedule(z_s, kind, n, chi_l, s)
+        dl_o, _ = cosmo.schedule(cosmo.chi(z_s), kind, n, chi_l, s)
+        assert abs(chi / cosmo.chi(z_s) - 1) < 1e-13
+        assert np.max(np.abs(dl / dl_o - 1)) < 1e-9
+        assert abs(dl.sum() / dl_o.sum() - 1) < 1e-13
+
+
+def _cloud(n, seed, centre=(0.0, 0.0, 800.0), scale=0.3, per_particle_soft=False):
+    g = inputs.rng(seed)
+    pos = inputs.quantize(np.asarray(centre) + g.normal(size=(n, 3)) * scale)
+    mass = g.uniform(0.5, 2.0, n) * 1e10
+    soft = g.uniform(0.002, 0.02, n) if per_particle_soft else 0.01
+    return pos, mass, soft
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("n", [1, 300, 3 * 256 + 37])
+@pytest.mark.parametrize("pps", [False, True])
+def test_potential_isolated(P, precision, n, pps):
+    pos, mass, soft = _cloud(n, 5 + n, per_particle_soft=pps)
+    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    ctx.load_particles(3, pos, mass, soft)
+    g = inputs.rng(99)
+    pts = np.concatenate([np.array([0.0, 0.0, 800.0]) + g.normal(size=(500, 3)) * 0.4,
+                          np.array([[0.0, 0.0, 0.0], [3.0, -2.0, 500.0], pos[0]])])
+    out = ctx.potential(3, pts)
+    ref = oracle.potential(oracle.MassField(pos, mass, soft), pts)
+    scale_phi = np.abs(ref[:, 0])
+    scale_g = np.linalg.norm(ref[:, 1:], axis=1)
+    err_phi = np.abs(out[:, 0] - ref[:, 0]) / scale_phi
+    err_g = np.linalg.norm(out[:, 1:] - ref[:, 1:], axis=1) / np.maximum(scale_g, 1e-300)
+    if precision == "fp64":
+        assert err_phi.max() < 1e-12 and err_g.max() < 1e-11
+    else:
+        assert err_phi.max() < 2e-6
+        assert np.percentile(err_g, 99) < 5e-6 and err_g.max() < 5e-5
+
+
+def _small_box(n=4000, seed=inputs.BASE_SEED + 33, L_h=20.0, n_halos=12, n_rep=6):
+    L = inputs.box_length(L_h / 0.7)
+    pos, mass, info = inputs.halo_box(n, L, n_halos, seed)
+    rot, shift = inputs.replicas(n_rep, L, seed)
+    return dict(pos=pos, mass=mass, soft=0.016 / 0.7, L=L, rot=rot, shift=shift)
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("mean_subtract", [False, True])
+def test_potential_replicated(P, precision, mean_subtract):
+    b = _small_box()
+    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    ctx.load_particles(1, b["pos"], b["mass"], b["soft"], replicated=True, box_length=b["L"], rot=b["rot"],
+                       shift=b["shift"], mean_subtract=mean_subtract)
+    g = inputs.rng(7)
+    L = b["L"]
+    rep = g.integers(0, 6, 400).astype(np.int32)
+    pts = np.stack([g.uniform(-0.5, 0.5, 400) * L, g.uniform(-0.5, 0.5, 400) * L, (rep + g.random(400)) * L], 1)
+    pts[:4, 2] = rep[:4] * L  # on a replica face
+    out = ctx.potential(1, pts, rep)
+    f = oracle.MassField(b["pos"], b["mass"], b["soft"], replicated=True, L=L, rot=b["rot"], shift=b["shift"],
+                         mean_subtract=mean_subtract)
+    ref = oracle.potential(f, pts, rep)
+    raw = oracle.potential(oracle.MassField(b["pos"], b["mass"], b["soft"], replicated=True, L=L, rot=b["rot"],
+                                            shift=b["shift"]), pts, rep)
+    # errors relative to the particle field itself (mean subtraction cancels most of it)
+    sc_phi = np.abs(raw[:, 0])
+    sc_g = np.linalg.norm(raw[:, 1:], axis=1)
+    e_phi = np.abs(out[:, 0] - ref[:, 0]) / sc_phi
+    e_g = np.linalg.norm(out[:, 1:] - ref[:, 1:], axis=1) / sc_g
+    if precision == "fp64":
+        assert e_phi.max() < 1e-12 and e_g.max() < 1e-11
+    else:
+        assert e_phi.max() < 2e-6 and e_g.max() < 2e-5
+
+
+def test_c1_point_lens_fp64(P, cosmo):
+    cfg = inputs.config_c1()
+    ctx = ctx_for(P, P.FP64)
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    o = run_oracle(cfg, cfg["theta"], cosmo)
+    ok = np.abs(np.abs(cfg["x"]) - 1) > 0.05
+    assert rel_mu(g["mu"], o.mu)[ok].max() < 1e-9
+    assert rel_alpha(g["rays"], o).max() < 1e-10
+    assert np.array_equal(g["flags"], o.flags)
+    assert np.array_equal(g["steps"], o.steps)
+    for k in ("kappa", "gamma1", "gamma2", "omega"):
+        assert np.allclose(g[k][ok], getattr(o, k)[ok], rtol=1e-8, atol=1e-11)
+
+
+def _c2_small(n_particles=20000, n_side=4, n_steps=300):
+    cfg = inputs.config_c2(n_particles=n_particles, n_side=n_side, n_steps=n_steps)
+    return cfg
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c2_small_nfw(P, cosmo, precision):
+    cfg = _c2_small()
+    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    o = run_oracle(cfg, cfg["theta"], cosmo)
+    assert np.array_equal(g["flags"], o.flags)
+    da, dm = rel_alpha(g["rays"], o), rel_mu(g["mu"], o.mu)
+    if precision == "fp64":
+        assert da.max() < 1e-10 and dm.max() < 1e-9
+    else:
+        assert da.max() < ALPHA_GATE and dm.max() < MU_GATE
+    st = ctx.stats()
+    assert st["interactions"] > 0
+
+
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_box_replicas_mean_subtracted(P, cosmo, precision):
+    b = _small_box()
+    L = b["L"]
+    z_s = 0.02
+    chi_s = cosmo.chi(z_s)
+    n_rep = int(math.ceil(chi_s / L)) + 1
+    assert n_rep <= 6
+    half = (0.5 * L - 2.0) / chi_s
+    theta = inputs.bundle_grid(-half, half, 4)
+    cfg = dict(b, replicated=True, mean_subtract=True, cosmo=(0.3, 0.7, 0.7), z_s=z_s, n_ring=4,
+               theta_r=math.radians(1 / 3600), schedule=0, n_steps=120)
+    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    gpu_load(ctx, 2, cfg)
+    g = ctx.trace(2, z_s, theta, want_rays=True, **trace_kw(cfg))
+    o = run_oracle(cfg, theta, cosmo)
+    assert np.array_equal(g["flags"], o.flags)
+    da, dm = rel_alpha(g["rays"], o), rel_mu(g["mu"], o.mu)
+    if precision == "fp64":
+        assert da.max() < 1e-9 and dm.max() < 1e-9
+    else:
+        assert da.max() < ALPHA_GATE and dm.max() < MU_GATE
+
+
+def test_empty_field_is_unlensed(P, cosmo):
+    ctx = ctx_for(P, P.MIXED)
+    ctx.load_particles(0, np.zeros((0, 3)), np.zeros(0), 0.0)
+    th = np.array([[0.0, 0.0], [1e-3, -2e-3]])
+    g = ctx.trace(0, 0.5, th, want_rays=True, n_steps=64)
+    assert np.all(np.abs(g["mu"] - 1) < 1e-9) and np.all(g["flags"] == 0)
+    assert np.all(np.abs(g["rays"][:, :, 1:3] / cosmo.chi(0.5) - oracle.trace(
+        cosmo, oracle.MassField(np.zeros((0, 3)), np.zeros(0), 0.0), 0.5, th, theta_r=1e-6,
+        n_steps=64).beta()) < 1e-15)
+
+
+def test_ring_of_eight_and_derived_symbols(P, cosmo):
+    cfg = _c2_small(n_particles=3000, n_side=2, n_steps=150)
+    cfg["n_ring"] = 8
+    for ch in (0, 1):
+        ctx = ctx_for(P, P.MIXED, christoffel=ch)
+        gpu_load(ctx, 0, cfg)
+        g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+        o = run_oracle(cfg, cfg["theta"], cosmo, christoffel=ch)
+        assert rel_mu(g["mu"], o.mu).max() < MU_GATE
+        assert rel_alpha(g["rays"], o).max() < ALPHA_GATE
+
+
+def test_histogram_bit_exact(P):
+    g = inputs.rng(17)
+    mu = np.exp(g.uniform(np.log(0.3), np.log(8.0), 20000))
+    mu[::9] *= -1
+    flags = np.zeros(mu.size, np.int32)
+    flags[::101] = oracle.F_NOCROSS
+    mu[7] = np.inf
+    ctx = ctx_for(P, P.MIXED)
+    for bins, lo, hi in ((200, 0.5, 5.0), (37, 0.9, 1.7), (1, 0.1, 10.0)):
+        c_g, w_g, s_g = ctx.histogram(mu, flags, bins, lo, hi)
+        c_o, w_o, s_o = oracle.histogram(mu, flags, bins, lo, hi)
+        assert np.array_equal(c_g, c_o) and np.array_equal(w_g, w_o)
+        for k in ("n_used", "n_under", "n_over", "n_neg", "n_bad"):
+            assert s_g[k] == s_o[k]
+        for k in ("W_total", "mean_w", "sigma_w"):
+            assert abs(s_g[k] / s_o[k] - 1) < 1e-12
+
+
+def test_errors_are_reported(P):
+    ctx = P.Context(0)
+    with pytest.raises(P.Rt3dError) as e:
+        ctx.trace(0, 0.5, np.zeros((1, 2)))
+    assert e.value.code == -6
+    ctx.set_cosmology()
+    with pytest.raises(P.Rt3dError) as e:
+        ctx.trace(5, 0.5, np.zeros((1, 2)))
+    assert e.value.code == -7
+    with pytest.raises(P.Rt3dError) as e:
+        ctx.set_cosmology(0.3, 0.8, 0.7)
+    assert e.value.code == -1
+    with pytest.raises(P.Rt3dError):
+        ctx.load_particles(0, np.zeros((2, 3)), np.array([1.0, -1.0]), 0.0)
+    with pytest.raises(P.Rt3dError):
+        ctx.load_particles(0, np.full((1, 3), np.nan), np.array([1.0]), 0.0)
+    ctx.load_particles(0, np.zeros((1, 3)) + 5.0, np.array([1e10]), 0.01)
+    with pytest.raises(P.Rt3dError):
+        ctx.trace(0, -1.0, np.zeros((1, 2)))
+    with pytest.raises(P.Rt3dError):
+        ctx.trace(0, 0.5, np.zeros((1, 2)), n_ring=1)
+    with pytest.raises(P.Rt3dError):
+        ctx.trace(0, 0.5, np.full((1, 2), np.nan))
