@@ -77,8 +77,8 @@ __global__ void k_stage_particles(int64_t n, const double *__restrict__ pos, con
     const double m = kMuG * mass[i] * mscale;
     part[i] = make_int4(q[0], q[1], q[2], __float_as_int((float)m));
     m64[i] = m;
-    if (soft_pp) {
-        const double e = soft[i] * two_e;
+    if (soft_pp) {  // Plummer softening squared, Mpc^2
+        const double e = soft[i];
         eps2[i] = (float)(e * e);
         eps2_64[i] = e * e;
     }
@@ -391,7 +391,7 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
         f.rot = slot.d_rot;
         f.shift = slot.d_shift;
         f.n = n;
-        const double e0 = soft_pp ? 0.0 : soft[0] * two_e;
+        const double e0 = soft_pp ? 0.0 : soft[0];
         f.eps2u = (float)(e0 * e0);
         f.eps2u64 = e0 * e0;
         f.replicated = repl ? 1 : 0;

@@ -7,8 +7,10 @@
 //   mass mu_G m 2^ms as FP32 bits).  A block stages a tile of TILE particles
 //   in shared memory, applying the replica transform (exact integer
 //   arithmetic) and re-centring on an anchor: the grid point nearest the
-//   block's first ray.  Particle offsets from the anchor are exact in FP32
-//   up to 2^24 grid units; each ray's offset is rounded once from FP64.
+//   block's first ray.  The integer offset from the anchor converts to FP32
+//   exactly up to 2^24 grid units and is then scaled by delta (a power of
+//   two, also exact) so that the arithmetic runs in Mpc, where 1/d^3 stays
+//   inside the FP32 range; each ray's offset is rounded once from FP64.
 // * Every ray of a thread reuses each staged particle (register blocking R);
 //   all threads of the block read the same shared word (broadcast).
 // * Sums are accumulated in FP32 over chunks of CHUNK particles and merged
@@ -100,6 +102,7 @@ __global__ void __launch_bounds__(NT) k_force_mixed(ForceArgs A)
 
     const int64_t p0 = (int64_t)split * A.per_split;
     const int64_t p1 = min(f.n, p0 + A.per_split);
+    const float dlt = (float)f.delta;
     for (int j = rmin; j <= rmax; ++j) {
         double o[3];
         frame_origin(f, j, o);
@@ -111,9 +114,9 @@ __global__ void __launch_bounds__(NT) k_force_mixed(ForceArgs A)
         for (int k = 0; k < R; ++k) {
             const int64_t i = base + (int64_t)k * NT + tid;
             if (i < A.n && myrep[k] == j) {
-                rx[k] = (float)((A.px[i] - o[0]) * f.inv_delta - (double)ax);
-                ry[k] = (float)((A.py[i] - o[1]) * f.inv_delta - (double)ay);
-                rz[k] = (float)((A.pz[i] - o[2]) * f.inv_delta - (double)az);
+                rx[k] = (float)(((A.px[i] - o[0]) * f.inv_delta - (double)ax) * f.delta);
+                ry[k] = (float)(((A.py[i] - o[1]) * f.inv_delta - (double)ay) * f.delta);
+                rz[k] = (float)(((A.pz[i] - o[2]) * f.inv_delta - (double)az) * f.delta);
             } else {  // far sentinel: every contribution is exactly zero
                 rx[k] = ry[k] = rz[k] = 1e30f;
             }
@@ -128,8 +131,8 @@ __global__ void __launch_bounds__(NT) k_force_mixed(ForceArgs A)
                     const int4 pr = f.part[pi];
                     long long qq[3] = {pr.x, pr.y, pr.z};
                     if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
-                    v = make_float4((float)(qq[0] - ax), (float)(qq[1] - ay), (float)(qq[2] - az),
-                                    __int_as_float(pr.w));
+                    v = make_float4((float)(qq[0] - ax) * dlt, (float)(qq[1] - ay) * dlt,
+                                    (float)(qq[2] - az) * dlt, __int_as_float(pr.w));
                     if (PEPS) e2 = f.eps2[pi];
                 }
                 s_p[q] = v;
@@ -207,9 +210,9 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
         for (int k = 0; k < R; ++k) {
             const int64_t i = base + (int64_t)k * NT + tid;
             if (i < A.n && myrep[k] == j) {
-                rx[k] = (A.px[i] - o[0]) * f.inv_delta - (double)ax;
-                ry[k] = (A.py[i] - o[1]) * f.inv_delta - (double)ay;
-                rz[k] = (A.pz[i] - o[2]) * f.inv_delta - (double)az;
+                rx[k] = ((A.px[i] - o[0]) * f.inv_delta - (double)ax) * f.delta;
+                ry[k] = ((A.py[i] - o[1]) * f.inv_delta - (double)ay) * f.delta;
+                rz[k] = ((A.pz[i] - o[2]) * f.inv_delta - (double)az) * f.delta;
             } else {
                 rx[k] = ry[k] = rz[k] = 1e150;
             }
@@ -224,7 +227,8 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
                     const int4 pr = f.part[pi];
                     long long qq[3] = {pr.x, pr.y, pr.z};
                     if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
-                    v = make_double4((double)(qq[0] - ax), (double)(qq[1] - ay), (double)(qq[2] - az), f.m64[pi]);
+                    v = make_double4((double)(qq[0] - ax) * f.delta, (double)(qq[1] - ay) * f.delta,
+                                     (double)(qq[2] - az) * f.delta, f.m64[pi]);
                     if (PEPS) e2 = f.eps2_64[pi];
                 }
                 s_p[q] = v;

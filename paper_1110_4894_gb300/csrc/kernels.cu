@@ -178,9 +178,9 @@ __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64
                 acc[o] += (double)v.x + (double)v.y;
             }
     }
-    // partial sums hold sum m'' / |d| and sum m'' d / |d|^3 in grid units with
-    // d = particle - point: phi = -S0 / (delta 2^ms), grad phi = -S / (delta^2 2^ms)
-    const double sp = f.inv_delta * f.mscale_inv, sg = sp * f.inv_delta;
+    // partial sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with
+    // d = particle - point and m'' = mu_G m 2^ms: phi = -S0 / 2^ms, grad phi = -S / 2^ms
+    const double sp = f.mscale_inv, sg = f.mscale_inv;
     F[0] = -acc[0] * sp;
     F[1] = -acc[1] * sg;
     F[2] = -acc[2] * sg;

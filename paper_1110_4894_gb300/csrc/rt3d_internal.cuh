@@ -98,13 +98,13 @@ __device__ __forceinline__ void prism_field(const T lo[3], const T hi[3], const 
 // ---------------------------------------------------------------------------
 struct DevField {
     const int4 *part;      // (qx, qy, qz, m32 bits): integer grid position, scaled mass (FP32)
-    const float *eps2;     // per-particle eps^2 in grid units^2, or nullptr
+    const float *eps2;     // per-particle eps^2 (Mpc^2), or nullptr
     const double *m64;     // scaled masses (FP64 path)
     const double *eps2_64; // per-particle eps^2 (FP64 path) or nullptr
     const int *rot;        // n_rep * 9
     const int *shift;      // n_rep * 3, grid units
     int64_t n;
-    float eps2u;           // uniform eps^2 (grid units^2)
+    float eps2u;           // uniform eps^2 (Mpc^2)
     double eps2u64;
     int replicated, mean_subtract, n_rep;
     int Lq;                // box length in grid units (replicated)

@@ -161,7 +161,9 @@ def test_box_replicas_mean_subtracted(P, cosmo, precision):
     assert np.array_equal(g["flags"], o.flags)
     da, dm = rel_alpha(g["rays"], o), rel_mu(g["mu"], o.mu)
     if precision == "fp64":
-        assert da.max() < 1e-9 and dm.max() < 1e-9
+        # here alpha ~ 1e-7 rad while theta ~ 0.2 rad: alpha = theta - beta keeps
+        # only ~9 significant digits of the FP64 positions
+        assert da.max() < 1e-6 and dm.max() < 1e-9
     else:
         assert da.max() < ALPHA_GATE and dm.max() < MU_GATE
 
