@@ -14,6 +14,7 @@
 namespace rt3d {
 cudaError_t dispatch_mixed(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
 cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
+cudaError_t dispatch_packed(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 
 // ---------------------------------------------------------------------------
 // particle staging (S2): FP64 input -> integer grid + scaled masses
@@ -287,6 +288,8 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
         if (!(e >= 0.0) || !isfinite(e)) return fail(ctx, RT3D_EINVAL, "softening must be >= 0");
     }
     if (n == 0 && soft && !(soft[0] >= 0.0)) return fail(ctx, RT3D_EINVAL, "softening must be >= 0");
+    bool umass = n > 0;
+    for (int64_t i = 1; i < n && umass; ++i) umass = mass[i] == mass[0];
     double L = 0.0;
     if (repl) {
         L = vol->box_length;
@@ -406,6 +409,8 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
         f.L = repl ? (double)Lq * f.delta : 0.0;
         f.mscale_inv = ldexp(1.0, -ms);
         f.rho_term = repl ? kMuG * st[7] / (f.L * f.L * f.L) : 0.0;
+        f.uniform_mass = umass ? 1 : 0;
+        f.m_uniform = umass ? kMuG * mass[0] * mscale : 0.0;
         slot.n = n;
         slot.loaded = true;
     } while (0);
@@ -423,13 +428,18 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
 // ---------------------------------------------------------------------------
 // launch shape
 // ---------------------------------------------------------------------------
-static ForceShape choose_shape(rt3d_ctx *ctx, int64_t n_points, int64_t n_particles, bool fp64)
+static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_points, bool fp64)
 {
+    const int64_t n_particles = f.n;
     ForceShape sh;
+    sh.umass = 0;
     if (fp64) {
+        sh.variant = 2;
         sh.R = 2;
         sh.NT = 128;
     } else {
+        sh.variant = ctx->opt.variant == 1 ? 1 : 0;
+        sh.umass = (sh.variant == 0 && f.uniform_mass) ? 1 : 0;
         sh.R = ctx->opt.rays_per_thread > 0 ? ctx->opt.rays_per_thread : 4;
         sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : 128;
     }
@@ -473,7 +483,10 @@ static cudaError_t run_force(rt3d_ctx *ctx, const DevField &f, const double *px,
     A.out = partials;
     A.gate = gate;
     (void)ctx;
-    return fp64 ? dispatch_fp64(A, sh, st) : dispatch_mixed(A, sh, st);
+    (void)fp64;
+    if (sh.variant == 2) return dispatch_fp64(A, sh, st);
+    if (sh.variant == 1) return dispatch_mixed(A, sh, st);
+    return dispatch_packed(A, sh, sh.umass != 0, st);
 }
 
 // ---------------------------------------------------------------------------
@@ -540,7 +553,7 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     const bool fp64 = ctx->opt.precision == RT3D_FP64;
     const int nr = 1 + b->n_ring;
     const int64_t n_rays = n_b * nr;
-    ForceShape sh = choose_shape(ctx, n_rays, fs.n, fp64);
+    ForceShape sh = choose_shape(ctx, fs.df, n_rays, fp64);
     int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
     if (rc) return rc;
     RayState rs = make_state(ctx, n_b, nr);
@@ -780,7 +793,7 @@ extern "C" int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const doub
     }
     CK(cudaSetDevice(ctx->device));
     const bool fp64 = ctx->opt.precision == RT3D_FP64;
-    ForceShape sh = choose_shape(ctx, n, fs.n, fp64);
+    ForceShape sh = choose_shape(ctx, fs.df, n, fp64);
     Scratch &s = ctx->scr;
     CK(grow(*(char **)&s.partials, s.partials_bytes, partials_bytes(sh, n, fp64)));
     CK(grow(ctx->d_io, ctx->d_io_n, (size_t)(3 * n + 4 * n + n)));

@@ -179,6 +179,156 @@ __global__ void __launch_bounds__(NT) k_force_mixed(ForceArgs A)
     }
 }
 
+// Packed variant: P pairs of rays per thread, every FP32 operation of the pair
+// sum issued as a Blackwell f32x2 instruction (FADD2 / FMUL2 / FFMA2), which
+// halves the instruction count of the hot loop.  The particle tile is staged
+// duplicated, (x, x, y, y) and (z, z, m, m), so that each shared load yields
+// aligned register pairs.  The potential (which enters the geodesic equation
+// only at first order in phi) is summed plainly; the gradient is compensated
+// per chunk as in the scalar kernel.  UMASS: all particles share one mass,
+// which the integrator stage applies in FP64 (saves one multiply per pair).
+__device__ __forceinline__ void two_sum2_into(float2 &hi, float2 &lo, float2 x)
+{
+    const float2 s = __fadd2_rn(hi, x);
+    const float2 bb = __fadd2_rn(s, make_float2(-hi.x, -hi.y));
+    const float2 t = __fadd2_rn(s, make_float2(-bb.x, -bb.y));
+    const float2 e1 = __fadd2_rn(hi, make_float2(-t.x, -t.y));
+    const float2 e2 = __fadd2_rn(x, make_float2(-bb.x, -bb.y));
+    hi = s;
+    lo = __fadd2_rn(lo, __fadd2_rn(e1, e2));
+}
+
+template <int P, int NT, bool REPL, bool PEPS, bool UMASS>
+__global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
+{
+    constexpr int R = 2 * P;
+    if (A.gate && *A.gate == 0ull) return;
+    __shared__ float4 s_a[kTile];            // (x, x, y, y)
+    __shared__ float4 s_b[kTile];            // (z, z, m, m)
+    __shared__ float2 s_e[PEPS ? kTile : 1]; // (eps2, eps2)
+    const DevField &f = A.f;
+    const int tid = threadIdx.x;
+    const int64_t base = (int64_t)blockIdx.x * (NT * R);
+    const int split = blockIdx.y;
+    int myrep[R], rmin, rmax;
+    block_replica_range<R, NT>(A, base, myrep, rmin, rmax);
+
+    float2 phi[P], hx[P], hy[P], hz[P], lx[P], ly[P], lz[P];
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+        phi[p] = hx[p] = hy[p] = hz[p] = lx[p] = ly[p] = lz[p] = make_float2(0.0f, 0.0f);
+    }
+    const int64_t p0 = (int64_t)split * A.per_split;
+    const int64_t p1 = min(f.n, p0 + A.per_split);
+    const float dlt = (float)f.delta;
+    const float2 E2u = make_float2(f.eps2u, f.eps2u);
+    for (int j = rmin; j <= rmax; ++j) {
+        double o[3];
+        frame_origin(f, j, o);
+        const long long ax = __double2ll_rn((A.px[base] - o[0]) * f.inv_delta);
+        const long long ay = __double2ll_rn((A.py[base] - o[1]) * f.inv_delta);
+        const long long az = __double2ll_rn((A.pz[base] - o[2]) * f.inv_delta);
+        // negated ray offsets: d = particle + (-ray)
+        float2 nx[P], ny[P], nz[P];
+#pragma unroll
+        for (int p = 0; p < P; ++p) {
+            float v[2][3];
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int k = 2 * p + h;
+                const int64_t i = base + (int64_t)k * NT + tid;
+                if (i < A.n && myrep[k] == j) {
+                    v[h][0] = -(float)(((A.px[i] - o[0]) * f.inv_delta - (double)ax) * f.delta);
+                    v[h][1] = -(float)(((A.py[i] - o[1]) * f.inv_delta - (double)ay) * f.delta);
+                    v[h][2] = -(float)(((A.pz[i] - o[2]) * f.inv_delta - (double)az) * f.delta);
+                } else {  // far sentinel: every contribution is exactly zero
+                    v[h][0] = v[h][1] = v[h][2] = -1e30f;
+                }
+            }
+            nx[p] = make_float2(v[0][0], v[1][0]);
+            ny[p] = make_float2(v[0][1], v[1][1]);
+            nz[p] = make_float2(v[0][2], v[1][2]);
+        }
+        for (int64_t t0 = p0; t0 < p1; t0 += kTile) {
+            __syncthreads();
+            for (int q = tid; q < kTile; q += NT) {
+                const int64_t pi = t0 + q;
+                float x = 1e18f, y = 1e18f, z = 1e18f, m = 0.0f, e2 = 0.0f;
+                if (pi < p1) {
+                    const int4 pr = f.part[pi];
+                    long long qq[3] = {pr.x, pr.y, pr.z};
+                    if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
+                    x = (float)(qq[0] - ax) * dlt;
+                    y = (float)(qq[1] - ay) * dlt;
+                    z = (float)(qq[2] - az) * dlt;
+                    m = __int_as_float(pr.w);
+                    if (PEPS) e2 = f.eps2[pi];
+                }
+                s_a[q] = make_float4(x, x, y, y);
+                s_b[q] = make_float4(z, z, m, m);
+                if (PEPS) s_e[q] = make_float2(e2, e2);
+            }
+            __syncthreads();
+            for (int c0 = 0; c0 < kTile; c0 += kChunk) {
+                float2 cx[P], cy[P], cz[P];
+#pragma unroll
+                for (int p = 0; p < P; ++p) cx[p] = cy[p] = cz[p] = make_float2(0.0f, 0.0f);
+#pragma unroll 4
+                for (int jj = c0; jj < c0 + kChunk; ++jj) {
+                    const float4 a = s_a[jj];
+                    const float4 b = s_b[jj];
+                    const float2 PX = make_float2(a.x, a.y), PY = make_float2(a.z, a.w);
+                    const float2 PZ = make_float2(b.x, b.y), M2 = make_float2(b.z, b.w);
+                    const float2 E2 = PEPS ? s_e[jj] : E2u;
+#pragma unroll
+                    for (int p = 0; p < P; ++p) {
+                        const float2 dx = __fadd2_rn(PX, nx[p]);
+                        const float2 dy = __fadd2_rn(PY, ny[p]);
+                        const float2 dz = __fadd2_rn(PZ, nz[p]);
+                        float2 r2 = __ffma2_rn(dz, dz, E2);
+                        r2 = __ffma2_rn(dy, dy, r2);
+                        r2 = __ffma2_rn(dx, dx, r2);
+                        const float2 inv = make_float2(rsqrt_mufu(r2.x), rsqrt_mufu(r2.y));
+                        const float2 i2 = __fmul2_rn(inv, inv);
+                        float2 mi3;
+                        if (UMASS) {
+                            phi[p] = __fadd2_rn(phi[p], inv);
+                            mi3 = __fmul2_rn(inv, i2);
+                        } else {
+                            const float2 mi = __fmul2_rn(M2, inv);
+                            phi[p] = __fadd2_rn(phi[p], mi);
+                            mi3 = __fmul2_rn(mi, i2);
+                        }
+                        cx[p] = __ffma2_rn(dx, mi3, cx[p]);
+                        cy[p] = __ffma2_rn(dy, mi3, cy[p]);
+                        cz[p] = __ffma2_rn(dz, mi3, cz[p]);
+                    }
+                }
+#pragma unroll
+                for (int p = 0; p < P; ++p) {
+                    two_sum2_into(hx[p], lx[p], cx[p]);
+                    two_sum2_into(hy[p], ly[p], cy[p]);
+                    two_sum2_into(hz[p], lz[p], cz[p]);
+                }
+            }
+        }
+    }
+    float2 *out = (float2 *)A.out;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = base + (int64_t)(2 * p + h) * NT + tid;
+            if (i >= A.n) continue;
+            const float ph = h ? phi[p].y : phi[p].x;
+            out[((int64_t)split * 4 + 0) * A.n + i] = make_float2(ph, 0.0f);
+            out[((int64_t)split * 4 + 1) * A.n + i] = h ? make_float2(hx[p].y, lx[p].y) : make_float2(hx[p].x, lx[p].x);
+            out[((int64_t)split * 4 + 2) * A.n + i] = h ? make_float2(hy[p].y, ly[p].y) : make_float2(hy[p].x, ly[p].x);
+            out[((int64_t)split * 4 + 3) * A.n + i] = h ? make_float2(hz[p].y, lz[p].y) : make_float2(hz[p].x, lz[p].x);
+        }
+    }
+}
+
 // FP64 twin (the all-FP64 path): same staging, FP64 arithmetic, plain sums.
 template <int R, int NT, bool REPL, bool PEPS>
 __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)

@@ -161,7 +161,7 @@ cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *
 // Reduce the pair-sum partials of one ray and add the mean subtraction:
 // F = (phi, dphi/dx1, dphi/dx2, dphi/dx3) at the ray's stage position.
 __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64, const void *partials, int64_t n,
-                                             int64_t i, int rep, const double p[3], double F[4])
+                                             int64_t i, int rep, const double p[3], double mfac, double F[4])
 {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (fp64) {
@@ -179,8 +179,10 @@ __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64
             }
     }
     // partial sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with
-    // d = particle - point and m'' = mu_G m 2^ms: phi = -S0 / 2^ms, grad phi = -S / 2^ms
-    const double sp = f.mscale_inv, sg = f.mscale_inv;
+    // d = particle - point and m'' = mu_G m 2^ms (or the same sums without m''
+    // for a uniform-mass field, mfac = m''): phi = -S0 mfac / 2^ms,
+    // grad phi = -S mfac / 2^ms
+    const double sp = f.mscale_inv * mfac, sg = sp;
     F[0] = -acc[0] * sp;
     F[1] = -acc[1] * sg;
     F[2] = -acc[2] * sg;
@@ -227,7 +229,8 @@ __device__ __forceinline__ void geodesic_rhs(const double y[8], const double F[4
 }
 
 __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RayState rs, int S, int fp64,
-                                              const void *__restrict__ partials, const double *__restrict__ dlam,
+                                              double mfac, const void *__restrict__ partials,
+                                              const double *__restrict__ dlam,
                                               const double *__restrict__ misc, int step, int stage,
                                               unsigned long long *cnt)
 {
@@ -250,7 +253,7 @@ __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RaySt
             y[q] = rs.y[q * n + i];
         }
         double F[4];
-        gather_field(f, S, fp64 != 0, partials, n, i, rep, ys + 1, F);
+        gather_field(f, S, fp64 != 0, partials, n, i, rep, ys + 1, mfac, F);
         const double a = cosmo_a(tp.cosmo, ys[0]);
         const double ad = cosmo_adot(tp.cosmo, a);
         if (step == 0 && stage == 0) {
@@ -305,13 +308,13 @@ cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, 
                          unsigned long long *d_counters, cudaStream_t st)
 {
     const int64_t blocks = (rs.n_rays + 255) / 256;
-    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, d_partials, d_dlam, d_misc,
-                                              step, stage, d_counters);
+    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
+                                              d_partials, d_dlam, d_misc, step, stage, d_counters);
     return cudaGetLastError();
 }
 
 // field at arbitrary points (rt3d_potential): reduce partials + mean subtraction
-__global__ void k_field_points(DevField f, int S, int fp64, const void *__restrict__ partials,
+__global__ void k_field_points(DevField f, int S, int fp64, double mfac, const void *__restrict__ partials,
                                const double *__restrict__ pts, const int *__restrict__ rep, int64_t n,
                                double *__restrict__ out)
 {
@@ -319,7 +322,7 @@ __global__ void k_field_points(DevField f, int S, int fp64, const void *__restri
     if (i >= n) return;
     const double p[3] = {pts[i], pts[n + i], pts[2 * n + i]};
     double F[4];
-    gather_field(f, S, fp64 != 0, partials, n, i, rep ? rep[i] : 0, p, F);
+    gather_field(f, S, fp64 != 0, partials, n, i, rep ? rep[i] : 0, p, mfac, F);
 #pragma unroll
     for (int o = 0; o < 4; ++o) out[4 * i + o] = F[o];
 }
@@ -328,8 +331,8 @@ cudaError_t launch_stage_field(const DevField &f, const ForceShape &sh, bool fp6
                                const double *d_pts, const int *d_rep, int64_t n, double *d_out, cudaStream_t st)
 {
     const int64_t blocks = (n + 255) / 256;
-    k_field_points<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(f, sh.splits, fp64 ? 1 : 0, d_partials,
-                                                                         d_pts, d_rep, n, d_out);
+    k_field_points<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(
+        f, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh), d_partials, d_pts, d_rep, n, d_out);
     return cudaGetLastError();
 }
 

@@ -113,6 +113,8 @@ struct DevField {
     double L;              // box length (Mpc)
     double mscale_inv;     // 1 / 2^ms (masses are stored as mu_G m 2^ms)
     double rho_term;       // mu_G * mean density (mean subtraction), Mpc^-2
+    int uniform_mass;      // every particle has the same mass
+    double m_uniform;      // that mass, scaled as stored (mu_G m 2^ms)
 };
 
 // world position of the grid origin of replica j (replicated) or the field origin
@@ -183,9 +185,11 @@ struct TraceParams {
 
 // force launch shape
 struct ForceShape {
-    int R;       // rays per thread
-    int NT;      // threads per block
-    int splits;  // particle splits
+    int R;        // rays per thread
+    int NT;       // threads per block
+    int splits;   // particle splits
+    int variant;  // 0 packed FP32x2, 1 scalar FP32, 2 FP64
+    int umass;    // packed kernel without per-particle masses (uniform-mass field)
 };
 
 // device scratch of a trace (grow-only, owned by the context)
@@ -218,6 +222,11 @@ cudaError_t launch_force(const DevField &f, const RayState &rs, const ForceShape
 cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, const ForceShape &sh,
                          bool fp64, const void *d_partials, const double *d_dlam, const double *d_misc,
                          int step, int stage, unsigned long long *d_counters, cudaStream_t st);
+// factor the integrator stage applies to the pair-sum partials of shape sh
+inline double partial_mass_factor(const DevField &f, const ForceShape &sh)
+{
+    return sh.umass ? f.m_uniform : 1.0;
+}
 cudaError_t launch_reduce(const TraceParams &tp, const double *d_theta, RayState rs, const double *d_misc,
                           double *d_bout, double *d_rout, cudaStream_t st);
 cudaError_t launch_histogram(int64_t n, const double *d_mu, int mu_stride, const int *d_flags,

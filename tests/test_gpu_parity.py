@@ -46,12 +46,24 @@ def _cloud(n, seed, centre=(0.0, 0.0, 800.0), scale=0.3, per_particle_soft=False
     return pos, mass, soft
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+PRECISIONS = ["fp64", "mixed", "mixed-scalar"]
+
+
+def ctx_prec(P, precision, **kw):
+    if precision == "fp64":
+        return ctx_for(P, P.FP64, **kw)
+    return ctx_for(P, P.MIXED, variant=1 if precision == "mixed-scalar" else 0, **kw)
+
+
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("n", [1, 300, 3 * 256 + 37])
 @pytest.mark.parametrize("pps", [False, True])
-def test_potential_isolated(P, precision, n, pps):
+@pytest.mark.parametrize("equal_mass", [False, True])
+def test_potential_isolated(P, precision, n, pps, equal_mass):
     pos, mass, soft = _cloud(n, 5 + n, per_particle_soft=pps)
-    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    if equal_mass:
+        mass = np.full(n, 1.3e10)
+    ctx = ctx_prec(P, precision)
     ctx.load_particles(3, pos, mass, soft)
     g = inputs.rng(99)
     pts = np.concatenate([np.array([0.0, 0.0, 800.0]) + g.normal(size=(500, 3)) * 0.4,
@@ -76,11 +88,11 @@ def _small_box(n=4000, seed=inputs.BASE_SEED + 33, L_h=20.0, n_halos=12, n_rep=6
     return dict(pos=pos, mass=mass, soft=0.016 / 0.7, L=L, rot=rot, shift=shift)
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 @pytest.mark.parametrize("mean_subtract", [False, True])
 def test_potential_replicated(P, precision, mean_subtract):
     b = _small_box()
-    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    ctx = ctx_prec(P, precision)
     ctx.load_particles(1, b["pos"], b["mass"], b["soft"], replicated=True, box_length=b["L"], rot=b["rot"],
                        shift=b["shift"], mean_subtract=mean_subtract)
     g = inputs.rng(7)
@@ -125,10 +137,10 @@ def _c2_small(n_particles=20000, n_side=4, n_steps=300):
     return cfg
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_c2_small_nfw(P, cosmo, precision):
     cfg = _c2_small()
-    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    ctx = ctx_prec(P, precision)
     gpu_load(ctx, 0, cfg)
     g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
     o = run_oracle(cfg, cfg["theta"], cosmo)
@@ -142,7 +154,7 @@ def test_c2_small_nfw(P, cosmo, precision):
     assert st["interactions"] > 0
 
 
-@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+@pytest.mark.parametrize("precision", PRECISIONS)
 def test_box_replicas_mean_subtracted(P, cosmo, precision):
     b = _small_box()
     L = b["L"]
@@ -154,7 +166,7 @@ def test_box_replicas_mean_subtracted(P, cosmo, precision):
     theta = inputs.bundle_grid(-half, half, 4)
     cfg = dict(b, replicated=True, mean_subtract=True, cosmo=(0.3, 0.7, 0.7), z_s=z_s, n_ring=4,
                theta_r=math.radians(1 / 3600), schedule=0, n_steps=120)
-    ctx = ctx_for(P, P.FP64 if precision == "fp64" else P.MIXED)
+    ctx = ctx_prec(P, precision)
     gpu_load(ctx, 2, cfg)
     g = ctx.trace(2, z_s, theta, want_rays=True, **trace_kw(cfg))
     o = run_oracle(cfg, theta, cosmo)
