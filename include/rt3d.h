@@ -208,6 +208,39 @@ int rt3d_schedule(rt3d_ctx *ctx, double z_s, int kind, int n_steps, double chi_l
 int rt3d_histogram_device(rt3d_ctx *ctx, void *stream, int64_t n, const double *d_bundle_out,
                           const rt3d_hist_opts *o, uint64_t *d_counts, uint64_t *d_wfix, double *d_scalars);
 
+/* ---- no-allocation variant ------------------------------------------------
+ * rt3d_potential_device_noalloc: phi and grad phi of a loaded field at n
+ * points, like rt3d_potential, but on device arrays and without allocating any
+ * device memory during the call.  The paper has no counterpart to this entry
+ * point; it exists for callers that cannot call cudaMalloc: a host process
+ * whose device memory is already reserved in full by another framework's
+ * pooling allocator (a new allocation would fail), or a loop that must not
+ * pay the device-wide synchronisation that cudaMalloc and cudaFree can imply.
+ *
+ * Scratch: the split partial sums go to one static device array of
+ * RT3D_NOALLOC_SCRATCH_BYTES (32 MiB), which every GPU that loads the library
+ * holds until the process exits.  Limit: n <= RT3D_NOALLOC_SCRATCH_BYTES / 32
+ * = 1048576 points per call (larger n returns RT3D_EINVAL); the number of
+ * particle splits is reduced as needed to fit.  Every call shares that array
+ * and it keeps the last call's contents; each entry a call reads is written
+ * first by the same call, so nothing needs clearing.  Calls that overlap on
+ * the GPU (two streams, two host threads) race on the array and give wrong
+ * results: serialise them.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current) and keeps it; make that
+ * first call before any stream capture begins.
+ *
+ * Arguments: ctx with field field_id loaded; stream = cudaStream_t (NULL =
+ * default stream); d_pts = device n*3 doubles laid out as all x1, then all x2,
+ * then all x3 (comoving Mpc); d_rep = device n int32 replica indices or NULL
+ * (replica 0); d_out = device n*4 doubles (phi, dphi/dx1, dphi/dx2, dphi/dx3
+ * per point).  The call only enqueues work on stream. */
+#define RT3D_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define RT3D_NOALLOC_MAX_DEVICES 64
+int rt3d_potential_device_noalloc(rt3d_ctx *ctx, void *stream, int field_id, int64_t n,
+                                  const double *d_pts, const int32_t *d_rep, double *d_out);
+
 /* Counters of the last trace or batch. */
 int rt3d_get_stats(rt3d_ctx *ctx, rt3d_stats *out);
 

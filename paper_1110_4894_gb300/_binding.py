@@ -253,3 +253,17 @@ class Context:
         s = Stats()
         self._check(self.L.rt3d_get_stats(self.h, C.byref(s)))
         return {k: getattr(s, k) for k, _ in Stats._fields_}
+
+
+def _potential_device_noalloc(self, stream, field_id, n, d_pts, d_rep, d_out):
+    """rt3d_potential_device_noalloc: the pair sum on device arrays with no
+    device allocation (scratch in a static device array); d_pts holds all x1,
+    then all x2, then all x3; enqueued on stream."""
+    fn = self.L.rt3d_potential_device_noalloc
+    fn.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int64, C.c_void_p, C.c_void_p, C.c_void_p]
+    fn.restype = C.c_int
+    self._check(fn(self.h, C.c_void_p(stream), int(field_id), int(n), C.c_void_p(d_pts),
+                   C.c_void_p(d_rep) if d_rep else None, C.c_void_p(d_out)))
+
+
+Context.potential_device_noalloc = _potential_device_noalloc

@@ -845,3 +845,63 @@ extern "C" int rt3d_get_stats(rt3d_ctx *ctx, rt3d_stats *out)
     *out = ctx->stats;
     return RT3D_OK;
 }
+
+// ---------------------------------------------------------------------------
+// rt3d_potential_device_noalloc: the pair sum with its split partials in a
+// static device array instead of context scratch, for callers that cannot
+// allocate device memory.  The paper has no counterpart to this entry point.
+// ---------------------------------------------------------------------------
+#include <mutex>
+
+// Split-K scratch of the no-allocation entry point.  It exists on every device
+// that loads this library, for the life of the process.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[RT3D_NOALLOC_SCRATCH_BYTES];
+
+static std::mutex g_noalloc_mu;
+static void *g_noalloc_ptr[RT3D_NOALLOC_MAX_DEVICES];
+
+// Device address of g_noalloc_scratch on the current device (set up once per
+// device).  In host code the symbol is only a host-side handle, so its device
+// address must come from cudaGetSymbolAddress with that device current.
+static cudaError_t noalloc_scratch(int dev, void **out)
+{
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_ptr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+        if (e != cudaSuccess) return e;
+        g_noalloc_ptr[dev] = p;
+    }
+    *out = g_noalloc_ptr[dev];
+    return cudaSuccess;
+}
+
+extern "C" int rt3d_potential_device_noalloc(rt3d_ctx *ctx, void *stream, int field_id, int64_t n,
+                                             const double *d_pts, const int32_t *d_rep, double *d_out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS || !ctx->fields[field_id].loaded)
+        return fail(ctx, RT3D_ENOFIELD, "field not loaded");
+    if (n < 1 || !d_pts || !d_out) return fail(ctx, RT3D_EINVAL, "need n >= 1 points and device arrays");
+    const int64_t max_points = (int64_t)(RT3D_NOALLOC_SCRATCH_BYTES / 32);
+    if (n > max_points) return fail(ctx, RT3D_EINVAL, "rt3d_potential_device_noalloc: at most 1048576 points per call");
+    if (ctx->device < 0 || ctx->device >= RT3D_NOALLOC_MAX_DEVICES)
+        return fail(ctx, RT3D_EINVAL, "device index beyond the no-allocation table");
+    CK(cudaSetDevice(ctx->device));
+    void *scratch = nullptr;
+    CK(noalloc_scratch(ctx->device, &scratch));
+    const FieldSlot &fs = ctx->fields[field_id];
+    const bool fp64 = ctx->opt.precision == RT3D_FP64;
+    ForceShape sh = choose_shape(ctx, fs.df, n, fp64);
+    // keep splits * 4 outputs * n points * 8 bytes inside the static array
+    const int64_t cap = (int64_t)(RT3D_NOALLOC_SCRATCH_BYTES / ((size_t)32 * (size_t)n));
+    if (sh.splits > cap) {
+        const int64_t tiles = std::max<int64_t>(1, (fs.n + kTile - 1) / kTile);
+        const int64_t tps = (tiles + cap - 1) / cap;
+        sh.splits = (int)std::max<int64_t>(1, (tiles + tps - 1) / tps);
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    CK(run_force(ctx, fs.df, d_pts, d_pts + n, d_pts + 2 * n, (const int *)d_rep, 1, n, sh, fp64, scratch, nullptr, st));
+    CK(launch_stage_field(fs.df, sh, fp64, scratch, d_pts, (const int *)d_rep, n, d_out, st));
+    return RT3D_OK;
+}
