@@ -34,6 +34,7 @@ FLOPS_PER_INTERACTION = 20  # direct N-body convention (3 sub, 6 fma/mul for r^2
 N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6  # FLOP/s at the maximum SM clock
 HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
+PROFILED_DRAM_BYTES = 2130432  # dram__bytes_read.sum + dram__bytes_write.sum of one k_force_packed launch
 
 
 def workload(full=True):
@@ -164,12 +165,15 @@ def run_ours(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     cfg, name = workload(full=not args.small)
+    if args.rk4_steps:
+        cfg["n_steps"] = args.rk4_steps
+        name += "_rk4x%d" % args.rk4_steps
     kw = trace_kw(cfg)
     nb = cfg["theta"].shape[0]
     nr = 1 + cfg["n_ring"]
     npart = len(cfg["mass"])
 
-    ctx = P.Context(local, precision=P.MIXED, time_kernels=1)
+    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=1)
     ctx.set_cosmology(*cfg["cosmo"])
     ctx.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"])
     d_theta = torch.from_numpy(np.ascontiguousarray(cfg["theta"])).to(dev)
@@ -243,6 +247,11 @@ def run_ours(args):
         per_launch = inter / max(1, force_launches)
         avg_launch_s = force_ms / 1e3 / max(1, force_launches)
         achieved = FLOPS_PER_INTERACTION * per_launch / avg_launch_s if avg_launch_s > 0 else 0.0
+        shape = ctx.stats()
+        # DRAM bytes per pair-sum launch from the ncu capture summarised in
+        # profiles/k_force_packed_nfw_1e5p_4096b.md (particles and positions;
+        # the split partials stay in L2); reported for the kernel as captured
+        traffic = PROFILED_DRAM_BYTES if not args.small else None
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -255,8 +264,8 @@ def run_ours(args):
                                            "threads_per_block": ctx.stats()["threads_per_block"],
                                            "splits": ctx.stats()["splits"]}},
                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK / 1e12,
-                            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": None,
-                            "kernel": "k_force_mixed", "flops_per_interaction": FLOPS_PER_INTERACTION,
+                            "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": traffic,
+                            "kernel": "k_force_packed", "flops_per_interaction": FLOPS_PER_INTERACTION,
                             "interactions_per_launch": per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                             "peak_basis": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
                "clocks": clocks,
@@ -281,6 +290,7 @@ def main():
     ap.add_argument("--small", action="store_true", help="reduced workload for quick checks")
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=250)
+    ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":

@@ -5,7 +5,9 @@
 
 #include <algorithm>
 #include <cstdio>
+#include <map>
 #include <string>
+#include <tuple>
 #include <vector>
 
 #include "force.cuh"
@@ -134,6 +136,8 @@ struct rt3d_ctx {
     int hist_cap = 0;
     double *d_io = nullptr;                    // staging for potential / histogram inputs
     size_t d_io_n = 0;
+    // launch shapes chosen by the autotuner, per size class
+    std::map<std::tuple<int, int, int, int, int, int>, ForceShape> tuned;
 };
 
 static int fail(rt3d_ctx *c, int code, const char *msg)
@@ -449,7 +453,9 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
     if (ctx->opt.splits > 0) {
         S = ctx->opt.splits;
     } else {
-        const int64_t target = 152 * 4 * 2;  // two waves of four blocks per SM
+        // about five waves of resident blocks (152 SMs x ~5 blocks): many
+        // small blocks balance the SMs better than one exact wave
+        const int64_t target = 152 * 5 * 5;
         S = (int)std::max<int64_t>(1, (target + nrb - 1) / nrb);
     }
     const int tiles = force_max_splits(sh, n_particles);
@@ -487,6 +493,93 @@ static cudaError_t run_force(rt3d_ctx *ctx, const DevField &f, const double *px,
     if (sh.variant == 2) return dispatch_fp64(A, sh, st);
     if (sh.variant == 1) return dispatch_mixed(A, sh, st);
     return dispatch_packed(A, sh, sh.umass != 0, st);
+}
+
+// ---------------------------------------------------------------------------
+// autotuner: time candidate launch shapes of the pair sum once per size class
+// (variant, uniform mass, replicated, per-particle softening, log2 points,
+// log2 particles) on the caller's data, keep the fastest.  Shapes differ only
+// in how the FP32 partial sums are split, so results agree to rounding.
+// ---------------------------------------------------------------------------
+static int ilog2(int64_t v)
+{
+    int l = 0;
+    while (v > 1) {
+        v >>= 1;
+        ++l;
+    }
+    return l;
+}
+
+static ForceShape with_splits(ForceShape sh, int64_t n_points, int64_t n_particles, int waves)
+{
+    const int64_t per_block = (int64_t)sh.R * sh.NT;
+    const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
+    const int64_t slots = 152 * std::max(1, 640 / sh.NT);
+    int S = (int)std::max<int64_t>(1, (waves * slots + nrb - 1) / nrb);
+    const int tiles = force_max_splits(sh, n_particles);
+    S = std::min(S, tiles);
+    const int64_t tps = (tiles + S - 1) / S;
+    sh.splits = (int)std::max<int64_t>(1, (tiles + tps - 1) / tps);
+    return sh;
+}
+
+static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, const double *py, const double *pz,
+                       const int *rep, int group, int64_t n, bool fp64, cudaStream_t st, ForceShape &out)
+{
+    ForceShape base = choose_shape(ctx, fs.df, n, fp64);
+    if (!ctx->opt.autotune || ctx->opt.rays_per_thread > 0 || ctx->opt.threads_per_block > 0 || ctx->opt.splits > 0) {
+        out = base;
+        return RT3D_OK;
+    }
+    const auto key = std::make_tuple(base.variant, base.umass, fs.df.replicated, fs.df.eps2 != nullptr ? 1 : 0,
+                                     ilog2(n), ilog2(std::max<int64_t>(1, fs.n)));
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end()) {
+        out = with_splits(it->second, n, fs.n, it->second.splits);  // splits slot holds the wave count
+        return RT3D_OK;
+    }
+    std::vector<ForceShape> cand;
+    std::vector<int> waves;
+    const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
+    const int rn64[][2] = {{2, 128}, {1, 128}};
+    const int nrn = fp64 ? 2 : 4;
+    for (int c = 0; c < nrn; ++c)
+        for (int w : {2, 3, 5, 8}) {
+            ForceShape s = base;
+            s.R = fp64 ? rn64[c][0] : rn[c][0];
+            s.NT = fp64 ? rn64[c][1] : rn[c][1];
+            cand.push_back(with_splits(s, n, fs.n, w));
+            waves.push_back(w);
+        }
+    size_t need = 0;
+    for (auto &s : cand) need = std::max(need, partials_bytes(s, n, fp64));
+    CK(grow(*(char **)&ctx->scr.partials, ctx->scr.partials_bytes, need));
+    cudaEvent_t e0, e1;
+    CK(cudaEventCreate(&e0));
+    CK(cudaEventCreate(&e1));
+    float best = 1e30f;
+    size_t bi = 0;
+    for (size_t c = 0; c < cand.size(); ++c) {
+        CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
+        CK(cudaEventRecord(e0, st));
+        CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
+        CK(cudaEventRecord(e1, st));
+        CK(cudaEventSynchronize(e1));
+        float ms = 0.0f;
+        CK(cudaEventElapsedTime(&ms, e0, e1));
+        if (ms < best) {
+            best = ms;
+            bi = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    ForceShape keep = cand[bi];
+    keep.splits = waves[bi];
+    ctx->tuned[key] = keep;
+    out = cand[bi];
+    return RT3D_OK;
 }
 
 // ---------------------------------------------------------------------------
@@ -557,6 +650,7 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
     if (rc) return rc;
     RayState rs = make_state(ctx, n_b, nr);
+    bool tune_pending = ctx->opt.autotune != 0;
     TraceParams tp;
     tp.cosmo = ctx->cosmo;
     tp.chi_s = 0.0;
@@ -572,6 +666,13 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     CK(launch_schedule(ctx->cosmo, z_s, b->schedule, b->n_steps, b->lens_chi, b->asinh_s, s.dlam, s.misc, st));
     CK(launch_init(tp, fs.df, d_theta, rs, s.counters, st));
     launches += 2;
+    if (tune_pending) {  // rays now sit at the observer: time shapes on this field
+        rc = tuned_shape(ctx, fs, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, rs.rep, nr, n_rays, fp64, st, sh);
+        if (rc) return rc;
+        rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
+        if (rc) return rc;
+        rs = make_state(ctx, n_b, nr);
+    }
     const int total = b->n_steps + b->max_extra;
     for (int step = 0; step < total; ++step) {
         for (int stage = 0; stage < 4; ++stage) {

@@ -170,13 +170,23 @@ __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64
 #pragma unroll
             for (int o = 0; o < 4; ++o) acc[o] += pd[((int64_t)s * 4 + o) * n + i];
     } else {
+        // the (hi, lo) FP32 pairs are added as double-float numbers (TwoSum on
+        // hi, lo carried separately): ~48-bit sums on the FP32 pipe, converted
+        // to FP64 once, instead of 2S conversions and adds on the FP64 pipe
         const float2 *pm = (const float2 *)partials;
+        float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
         for (int s = 0; s < S; ++s)
 #pragma unroll
             for (int o = 0; o < 4; ++o) {
                 const float2 v = pm[((int64_t)s * 4 + o) * n + i];
-                acc[o] += (double)v.x + (double)v.y;
+                const float t = hi[o] + v.x;
+                const float bb = t - hi[o];
+                const float err = (hi[o] - (t - bb)) + (v.x - bb);
+                hi[o] = t;
+                lo[o] += err + v.y;
             }
+#pragma unroll
+        for (int o = 0; o < 4; ++o) acc[o] = (double)hi[o] + (double)lo[o];
     }
     // partial sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with
     // d = particle - point and m'' = mu_G m 2^ms (or the same sums without m''
@@ -307,9 +317,11 @@ cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, 
                          const void *d_partials, const double *d_dlam, const double *d_misc, int step, int stage,
                          unsigned long long *d_counters, cudaStream_t st)
 {
-    const int64_t blocks = (rs.n_rays + 255) / 256;
-    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
-                                              d_partials, d_dlam, d_misc, step, stage, d_counters);
+    // small blocks spread the FP64 work of a few thousand rays over every SM
+    const int bs = rs.n_rays >= 152 * 256 ? 256 : 64;
+    const int64_t blocks = (rs.n_rays + bs - 1) / bs;
+    k_stage<<<(unsigned)blocks, bs, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
+                                             d_partials, d_dlam, d_misc, step, stage, d_counters);
     return cudaGetLastError();
 }
 

@@ -244,3 +244,18 @@ def test_errors_are_reported(P):
         ctx.trace(0, 0.5, np.zeros((1, 2)), n_ring=1)
     with pytest.raises(P.Rt3dError):
         ctx.trace(0, 0.5, np.full((1, 2), np.nan))
+
+
+def test_autotuned_shape_keeps_parity(P, cosmo):
+    cfg = _c2_small(n_particles=8000, n_side=4, n_steps=120)
+    ctx = ctx_for(P, P.MIXED, autotune=1)
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    st = ctx.stats()
+    assert (st["rays_per_thread"], st["threads_per_block"]) in {(4, 128), (4, 256), (4, 64), (8, 64)}
+    g2 = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))  # cached shape
+    assert ctx.stats()["splits"] == st["splits"]
+    assert np.array_equal(g["mu"], g2["mu"])
+    o = run_oracle(cfg, cfg["theta"], cosmo)
+    assert rel_mu(g["mu"], o.mu).max() < MU_GATE
+    assert rel_alpha(g["rays"], o).max() < ALPHA_GATE
