@@ -48,6 +48,79 @@ def workload(full=True):
     return cfg, name
 
 
+def cones_workload(n_cones, n_steps):
+    """the batched light-cone workload: n_cones independent halo boxes
+    (50/h Mpc, particles log-uniform in 1e3..1e6, z_s uniform in 0.3..1.5,
+    256..4096 bundles), each traced with a uniform table of n_steps steps"""
+    import inputs
+    cfg = inputs.config_c4(n_cones=n_cones, n_steps=n_steps)
+    return cfg, "light_cones_%dc_%ds" % (n_cones, n_steps)
+
+
+def run_cones(args):
+    """One step = one rt3d_trace_batch of every cone (a single persistent
+    launch in a CUDA graph).  Compared with the all-FP64 path run one cone
+    per launch on the first cones of the same batch."""
+    import torch
+
+    import paper_1110_4894_gb300 as P
+    cfg, name = cones_workload(args.cones, args.cone_steps)
+    ctx = P.Context(0, precision=P.MIXED, autotune=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    cones = []
+    npart = 0
+    for i, c in enumerate(cfg["cones"]):
+        ctx.load_particles(i, c["pos"], c["mass"], c["soft"], replicated=True, box_length=c["L"], rot=c["rot"],
+                           shift=c["shift"], mean_subtract=True)
+        cones.append(dict(field_id=i, z_s=c["z_s"], theta=c["theta"], n_steps=c["n_steps"]))
+        npart += len(c["mass"])
+    kw = dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0)
+    for _ in range(args.warmup):
+        ctx.trace_batch(cones, **kw)
+    times, inter = [], 0.0
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            ctx.trace_batch(cones, **kw)
+            times.append(time.perf_counter() - t0)
+            st = ctx.stats()
+            inter += st["interactions"]
+    clocks = clk.summary()
+    dev_s = st["device_ms"] / 1e3
+    value = inter / sum(times)
+    # all-FP64 reference: the same cones, one per launch (a subset for time)
+    sub = cones[: args.fp64_cones]
+    c64 = P.Context(0, precision=P.FP64)
+    c64.set_cosmology(*cfg["cosmo"])
+    for i in range(len(sub)):
+        c = cfg["cones"][i]
+        c64.load_particles(i, c["pos"], c["mass"], c["soft"], replicated=True, box_length=c["L"], rot=c["rot"],
+                           shift=c["shift"], mean_subtract=True)
+    t0 = time.perf_counter()
+    r64 = c64.trace_batch(sub, **kw)
+    t64 = time.perf_counter() - t0
+    i64 = c64.stats()["interactions"]
+    rm = ctx.trace_batch(cones, **kw)
+    dmu = max(float(np.max(np.abs(a["mu"] / b["mu"] - 1))) for a, b in zip(rm[: len(sub)], r64))
+    nb = sum(len(c["theta"]) for c in cfg["cones"])
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "bundles_per_s": nb * args.steps / sum(times),
+           "config": {"workload": name, "cones": args.cones, "particles": npart, "bundles": nb,
+                      "rk4_steps_per_cone": args.cone_steps, "launch_shape": {k: st[k] for k in ("threads_per_block",
+                                                                                                "splits")}},
+           "roofline": {"bound": "alu", "achieved": FLOPS_PER_INTERACTION * st["interactions"] / dev_s / 1e12,
+                        "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
+                        "frac": FLOPS_PER_INTERACTION * st["interactions"] / dev_s / FP32_PEAK, "traffic": None,
+                        "kernel": "k_batch_run (whole persistent launch)"},
+           "fp64_one_cone_per_launch": {"cones": len(sub), "interactions_per_s": i64 / t64,
+                                        "speedup_of_mixed_batched": value / (i64 / t64),
+                                        "max_rel_dmu_vs_mixed": dmu},
+           "clocks": clocks}
+    print(json.dumps(out))
+    return 0
+
+
 def trace_kw(cfg):
     return dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=cfg["schedule"], n_steps=cfg["n_steps"],
                 lens_chi=cfg["lens_chi"], asinh_s=cfg["asinh_s"])
@@ -291,10 +364,16 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
+    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones"])
+    ap.add_argument("--cones", type=int, default=512)
+    ap.add_argument("--cone-steps", type=int, default=8)
+    ap.add_argument("--fp64-cones", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "cones":
+        return run_cones(args)
     return run_ours(args)
 
 

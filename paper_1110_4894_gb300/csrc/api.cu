@@ -10,6 +10,7 @@
 #include <tuple>
 #include <vector>
 
+#include "batch_layout.cuh"
 #include "force.cuh"
 #include "rt3d_internal.cuh"
 
@@ -17,6 +18,7 @@ namespace rt3d {
 cudaError_t dispatch_mixed(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
 cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
 cudaError_t dispatch_packed(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
+struct BatchArgs;
 
 // ---------------------------------------------------------------------------
 // particle staging (S2): FP64 input -> integer grid + scaled masses
@@ -138,6 +140,35 @@ struct rt3d_ctx {
     size_t d_io_n = 0;
     // launch shapes chosen by the autotuner, per size class
     std::map<std::tuple<int, int, int, int, int, int>, ForceShape> tuned;
+    // batched trace: device scratch, the captured graph and its key
+    struct Batch {
+        void *cones = nullptr;
+        size_t cones_n = 0;
+        int4 *items = nullptr;
+        size_t items_n = 0;
+        int *rb2cone = nullptr;
+        size_t rb_n = 0;
+        double *state = nullptr;
+        size_t state_n = 0;
+        int *ints = nullptr;
+        size_t ints_n = 0;
+        double *theta = nullptr;
+        size_t theta_n = 0;
+        double *dlam = nullptr;
+        size_t dlam_n = 0;
+        float2 *partials = nullptr;
+        size_t partials_n = 0;
+        unsigned long long *cnt = nullptr;
+        size_t cnt_n = 0;
+        unsigned *bar = nullptr;  // [0] count, [1] generation, [2] error word
+        double *bout = nullptr;
+        size_t bout_n = 0;
+        double *rout = nullptr;
+        size_t rout_n = 0;
+        cudaGraphExec_t exec = nullptr;
+        std::vector<long long> key;
+        std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // (cones, log2 rays, log2 pairs) -> (NT, items)
+    } batch;
 };
 
 static int fail(rt3d_ctx *c, int code, const char *msg)
@@ -251,6 +282,22 @@ extern "C" int rt3d_destroy(rt3d_ctx *ctx)
     cudaFree(ctx->d_hist_f64);
     cudaFree(ctx->d_io);
     for (auto e : ctx->tev) cudaEventDestroy(e);
+    {
+        auto &B = ctx->batch;
+        if (B.exec) cudaGraphExecDestroy(B.exec);
+        cudaFree(B.cones);
+        cudaFree(B.items);
+        cudaFree(B.rb2cone);
+        cudaFree(B.state);
+        cudaFree(B.ints);
+        cudaFree(B.theta);
+        cudaFree(B.dlam);
+        cudaFree(B.partials);
+        cudaFree(B.cnt);
+        cudaFree(B.bar);
+        cudaFree(B.bout);
+        cudaFree(B.rout);
+    }
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
     if (ctx->stream) cudaStreamDestroy(ctx->stream);
@@ -636,6 +683,7 @@ static RayState make_state(rt3d_ctx *ctx, int64_t n_b, int nr)
     rs.done = s.ints;
     rs.steps = s.ints + rs.n_rays;
     rs.rep = s.ints + 2 * rs.n_rays;
+    rs.stride = rs.n_rays;
     return rs;
 }
 
@@ -791,15 +839,326 @@ extern "C" int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, doub
                          ctx->opt.time_kernels != 0);
 }
 
+// ---------------------------------------------------------------------------
+// batched trace (many cones, one persistent launch in a CUDA graph)
+// ---------------------------------------------------------------------------
+struct BatchPlan {
+    int64_t T = 0, n_b_total = 0, dlam_total = 0, partials_total = 0;
+    int max_steps = 0, g_end = 0;
+    std::vector<int64_t> ray_base, b_base, dlam_off, part_off, per_split;
+    std::vector<int> S;
+    std::vector<int4> items;
+    std::vector<int> rb2cone;
+    size_t cone_bytes(int n) const { return sizeof(BatchCone) * (size_t)n; }
+};
+
+// Layout of a batch: each cone's rays padded to whole ray blocks of RB, its
+// particles split into whole tiles of about per_item particles, one work item
+// per (cone, ray block, split).
+static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *cones, int nr, int RB, int64_t per_item,
+                      int max_extra, BatchPlan &p)
+{
+    p = BatchPlan{};
+    for (int c = 0; c < n_cones; ++c) {
+        const int64_t nb = cones[c].n_bundles, n_rays = nb * nr, N = fields[cones[c].field_id].n;
+        const int64_t nrb = (n_rays + RB - 1) / RB;
+        const int64_t tiles = std::max<int64_t>(1, (N + kTile - 1) / kTile);
+        int64_t S = std::max<int64_t>(1, (tiles * kTile + per_item - 1) / per_item);
+        S = std::min(S, tiles);
+        const int64_t tps = (tiles + S - 1) / S;
+        S = (tiles + tps - 1) / tps;
+        p.ray_base.push_back(p.T);
+        p.b_base.push_back(p.n_b_total);
+        p.dlam_off.push_back(p.dlam_total);
+        p.part_off.push_back(p.partials_total);
+        p.per_split.push_back(tps * kTile);
+        p.S.push_back((int)S);
+        for (int64_t rb = 0; rb < nrb; ++rb) {
+            for (int64_t s = 0; s < S; ++s) p.items.push_back(make_int4(c, (int)rb, (int)s, 0));
+            p.rb2cone.push_back(c);
+        }
+        p.T += nrb * RB;
+        p.n_b_total += nb;
+        p.dlam_total += cones[c].n_steps;
+        p.partials_total += S * 4 * n_rays;
+        p.max_steps = std::max(p.max_steps, cones[c].n_steps);
+        p.g_end = std::max(p.g_end, 4 * (cones[c].n_steps + max_extra));
+    }
+    return RT3D_OK;
+}
+
+static void fill_cone_table(const FieldSlot *fields, const Cosmo &cosmo, int christoffel, int n_cones,
+                            const rt3d_cone *cones, const rt3d_bundle_opts *b, const BatchPlan &p, double *state,
+                            int *ints, double *theta, double *dlam, float2 *partials, unsigned long long *cnt,
+                            double *rout, std::vector<unsigned char> &table)
+{
+    table.assign(p.cone_bytes(n_cones), 0);
+    BatchCone *T = (BatchCone *)table.data();
+    const int nr = 1 + b->n_ring;
+    for (int c = 0; c < n_cones; ++c) {
+        BatchCone &C = T[c];
+        const DevField &f = fields[cones[c].field_id].df;
+        C.f = f;
+        RayState &rs = C.rs;
+        rs.stride = p.T;
+        rs.y = state + p.ray_base[c];
+        rs.ys = state + 8 * p.T + p.ray_base[c];
+        rs.ks = state + 16 * p.T + p.ray_base[c];
+        rs.fin = state + 24 * p.T + p.ray_base[c];
+        rs.done = ints + p.ray_base[c];
+        rs.steps = ints + p.T + p.ray_base[c];
+        rs.rep = ints + 2 * p.T + 2 * p.b_base[c];
+        rs.n_b = cones[c].n_bundles;
+        rs.nr = nr;
+        rs.n_rays = rs.n_b * nr;
+        C.tp.cosmo = cosmo;
+        C.tp.chi_s = 0.0;
+        C.tp.n_ring = b->n_ring;
+        C.tp.theta_r = b->theta_r;
+        C.tp.phase = b->phase;
+        C.tp.christoffel = christoffel;
+        C.tp.n_steps = cones[c].n_steps;
+        C.tp.max_extra = b->max_extra;
+        C.theta = theta + 2 * p.b_base[c];
+        C.dlam = dlam + p.dlam_off[c];
+        C.partials = partials + p.part_off[c];
+        C.cnt = cnt + 3 * c;
+        C.rout = rout ? rout + 8 * nr * p.b_base[c] : nullptr;
+        C.chi_s = 0.0;
+        C.z_s = cones[c].z_s;
+        C.chi_l = b->lens_chi;
+        C.s_asinh = b->asinh_s;
+        C.kind = b->schedule;
+        C.mfac = f.uniform_mass ? f.m_uniform : 1.0;
+        C.per_split = p.per_split[c];
+        C.ray_base = p.ray_base[c];
+        C.b_base = p.b_base[c];
+        C.S = p.S[c];
+        C.flags = (f.replicated ? 1 : 0) | (f.eps2 ? 2 : 0) | (f.uniform_mass ? 4 : 0);
+        C.total_steps = cones[c].n_steps + b->max_extra;
+    }
+}
+
+static void unpack_bundles(const double *bo, int64_t nb, rt3d_bundle_result *out)
+{
+    for (int64_t i = 0; i < nb; ++i) {
+        out->mu[i] = bo[6 * i];
+        if (out->kappa) out->kappa[i] = bo[6 * i + 1];
+        if (out->gamma1) out->gamma1[i] = bo[6 * i + 2];
+        if (out->gamma2) out->gamma2[i] = bo[6 * i + 3];
+        if (out->omega) out->omega[i] = bo[6 * i + 4];
+        if (out->flags) out->flags[i] = (int32_t)bo[6 * i + 5];
+    }
+}
+
+// Build the batch layout for launch shape (NT, particles per work item),
+// upload it, and run (or replay) the graph.  g_limit > 0 runs only that many
+// global stages (autotuner timing); then nothing is read back.
+static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const rt3d_bundle_opts *b, int NT,
+                     int64_t per_item, int g_limit, bool want_rays, float *ms_out)
+{
+    auto &BS = ctx->batch;
+    const int P = 2;
+    const int RB = 2 * P * NT;
+    const int nr = 1 + b->n_ring;
+    BatchPlan plan;
+    int rc = plan_batch(ctx->fields.data(), n_cones, cones, nr, RB, per_item, b->max_extra, plan);
+    if (rc) return fail(ctx, rc, "invalid cone list");
+    const int64_t T = plan.T;
+    CK(grow(*(char **)&BS.cones, BS.cones_n, plan.cone_bytes(n_cones)));
+    CK(grow(BS.items, BS.items_n, plan.items.size()));
+    CK(grow(BS.rb2cone, BS.rb_n, plan.rb2cone.size()));
+    CK(grow(BS.state, BS.state_n, (size_t)(32 * T)));
+    CK(grow(BS.ints, BS.ints_n, (size_t)(2 * T + 2 * plan.n_b_total)));
+    CK(grow(BS.theta, BS.theta_n, (size_t)(2 * plan.n_b_total)));
+    CK(grow(BS.dlam, BS.dlam_n, (size_t)plan.dlam_total));
+    CK(grow(BS.partials, BS.partials_n, (size_t)plan.partials_total));
+    CK(grow(BS.cnt, BS.cnt_n, (size_t)(3 * n_cones)));
+    size_t bar_n = BS.bar ? 4 : 0;
+    CK(grow(BS.bar, bar_n, 4));
+    CK(grow(BS.bout, BS.bout_n, (size_t)(6 * plan.n_b_total)));
+    if (want_rays) CK(grow(BS.rout, BS.rout_n, (size_t)(8 * nr * plan.n_b_total)));
+    std::vector<unsigned char> table;
+    fill_cone_table(ctx->fields.data(), ctx->cosmo, ctx->opt.christoffel, n_cones, cones, b, plan, BS.state, BS.ints,
+                    BS.theta, BS.dlam, BS.partials, BS.cnt, want_rays ? BS.rout : nullptr, table);
+    cudaStream_t st = ctx->stream;
+    for (int c = 0; c < n_cones; ++c)
+        CK(cudaMemcpyAsync(BS.theta + 2 * plan.b_base[c], cones[c].theta, 2 * cones[c].n_bundles * sizeof(double),
+                           cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(BS.cones, table.data(), table.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(BS.items, plan.items.data(), plan.items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
+    CK(cudaMemcpyAsync(BS.rb2cone, plan.rb2cone.data(), plan.rb2cone.size() * sizeof(int), cudaMemcpyHostToDevice, st));
+    CK(cudaMemsetAsync(BS.bar, 0, 4 * sizeof(unsigned), st));
+    int grid = 0;
+    CK(batch_resident_blocks(P, NT, &grid));
+    if (grid < 1) return fail(ctx, RT3D_ECUDA, "persistent kernel cannot be resident");
+    BatchArgs A = make_batch_args(BS.cones, n_cones, BS.items, (int64_t)plan.items.size(), BS.rb2cone, T, RB,
+                                  g_limit > 0 ? g_limit : plan.g_end, BS.bar, (int *)(BS.bar + 2),
+                                  ctx->opt.watchdog_s > 0 ? ctx->opt.watchdog_s : 120.0, BS.bout);
+    // the graph is keyed by everything its launches capture
+    std::vector<long long> key = {n_cones, T, (long long)plan.items.size(), A.g_end, NT, per_item, grid,
+                                  plan.max_steps, plan.n_b_total, (long long)(intptr_t)BS.cones,
+                                  (long long)(intptr_t)BS.items, (long long)(intptr_t)BS.bout};
+    CK(cudaEventRecord(ctx->ev0, st));
+    bool use_graph = g_limit == 0;
+    if (use_graph && (BS.key != key || !BS.exec)) {
+        if (BS.exec) {
+            cudaGraphExecDestroy(BS.exec);
+            BS.exec = nullptr;
+        }
+        cudaGraph_t gr = nullptr;
+        CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+        cudaError_t le = batch_launch(A, P, NT, grid, plan.max_steps, plan.n_b_total, st);
+        cudaError_t ce = cudaStreamEndCapture(st, &gr);
+        if (le != cudaSuccess || ce != cudaSuccess) {
+            if (gr) cudaGraphDestroy(gr);
+            cudaGetLastError();
+            use_graph = false;  // capture unsupported here: launch directly
+        } else {
+            cudaError_t ie = cudaGraphInstantiate(&BS.exec, gr, 0);
+            cudaGraphDestroy(gr);
+            if (ie != cudaSuccess) {
+                BS.exec = nullptr;
+                cudaGetLastError();
+                use_graph = false;
+            } else {
+                BS.key = key;
+            }
+        }
+    }
+    if (use_graph) CK(cudaGraphLaunch(BS.exec, st));
+    else CK(batch_launch(A, P, NT, grid, plan.max_steps, plan.n_b_total, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaEventSynchronize(ctx->ev1));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    if (ms_out) *ms_out = ms;
+    unsigned err = 0;
+    CK(cudaMemcpy(&err, BS.bar + 2, sizeof err, cudaMemcpyDeviceToHost));
+    if (err) return fail(ctx, RT3D_ETIMEOUT, "persistent kernel: a grid barrier wait exceeded the watchdog");
+    ctx->stats.device_ms = ms;
+    ctx->stats.launches = 4;
+    ctx->stats.force_launches = 1;
+    ctx->stats.steps = plan.max_steps + b->max_extra;
+    ctx->stats.rays_per_thread = 2 * P;
+    ctx->stats.threads_per_block = NT;
+    ctx->stats.splits = (int)per_item;
+    ctx->stats.force_ms = ms;
+    ctx->stats_pending = false;
+    if (g_limit > 0) return RT3D_OK;
+    std::vector<unsigned long long> cnt((size_t)(3 * n_cones));
+    CK(cudaMemcpy(cnt.data(), BS.cnt, cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    double inter = 0.0;
+    for (int c = 0; c < n_cones; ++c) inter += (double)cnt[3 * c + 2] * (double)ctx->fields[cones[c].field_id].n;
+    ctx->stats.interactions = inter;
+    return RT3D_OK;
+}
+
 extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const rt3d_bundle_opts *b,
                                 rt3d_bundle_result *outs)
 {
     if (!ctx) return RT3D_EINVAL;
-    (void)n_cones;
-    (void)cones;
-    (void)b;
-    (void)outs;
-    return fail(ctx, RT3D_ENOTIMPL, "batched trace not built yet");
+    if (n_cones < 1 || !cones || !outs) return fail(ctx, RT3D_EINVAL, "need n_cones >= 1, cones and outputs");
+    int rc = check_bundle_opts(ctx, b);
+    if (rc) return rc;
+    if (!ctx->have_cosmo) return fail(ctx, RT3D_ENOCOSMO, "set the cosmology first");
+    for (int c = 0; c < n_cones; ++c) {
+        const rt3d_cone &k = cones[c];
+        if (k.field_id < 0 || k.field_id >= RT3D_MAX_FIELDS || !ctx->fields[k.field_id].loaded)
+            return fail(ctx, RT3D_ENOFIELD, "cone field not loaded");
+        if (!(k.z_s > 0.0) || k.z_s > 20.0 || k.n_bundles < 1 || !k.theta || k.n_steps < 1 || k.n_steps > 10000000)
+            return fail(ctx, RT3D_EINVAL, "cone needs z_s in (0, 20], n_bundles >= 1, theta, n_steps >= 1");
+        if (!outs[c].mu) return fail(ctx, RT3D_EINVAL, "null mu output");
+        for (int64_t i = 0; i < 2 * k.n_bundles; ++i)
+            if (!isfinite(k.theta[i])) return fail(ctx, RT3D_EINVAL, "non-finite theta");
+    }
+    CK(cudaSetDevice(ctx->device));
+    if (ctx->opt.precision == RT3D_FP64) {
+        // the all-FP64 reference path: one cone per launch sequence
+        double ms = 0.0, inter = 0.0;
+        for (int c = 0; c < n_cones; ++c) {
+            rt3d_bundle_opts bc = *b;
+            bc.n_steps = cones[c].n_steps;
+            rc = rt3d_trace(ctx, cones[c].field_id, cones[c].z_s, cones[c].n_bundles, cones[c].theta, &bc, &outs[c]);
+            if (rc) return rc;
+            ms += ctx->stats.device_ms;
+            inter += ctx->stats.interactions;
+        }
+        ctx->stats.device_ms = ms;
+        ctx->stats.interactions = inter;
+        return RT3D_OK;
+    }
+    bool want_rays = false;
+    for (int c = 0; c < n_cones; ++c) want_rays |= outs[c].ray_state != nullptr || outs[c].ray_steps != nullptr;
+    // launch shape: block size and particles per work item (autotuned per size class)
+    int NT = ctx->opt.threads_per_block == 64 || ctx->opt.threads_per_block == 256 ? ctx->opt.threads_per_block : 128;
+    int64_t per_item = ctx->opt.splits > 0 ? (int64_t)ctx->opt.splits * kTile : 16 * kTile;
+    if (ctx->opt.autotune && ctx->opt.threads_per_block <= 0 && ctx->opt.splits <= 0) {
+        int64_t rays = 0;
+        double pairs = 0.0;
+        for (int c = 0; c < n_cones; ++c) {
+            rays += cones[c].n_bundles * (1 + b->n_ring);
+            pairs += (double)cones[c].n_bundles * (1 + b->n_ring) * (double)ctx->fields[cones[c].field_id].n;
+        }
+        const auto key = std::make_tuple(n_cones, ilog2(rays), ilog2((int64_t)std::max(1.0, pairs)));
+        auto it = ctx->batch.tuned.find(key);
+        if (it != ctx->batch.tuned.end()) {
+            NT = it->second.first;
+            per_item = it->second.second;
+        } else {
+            float best = 1e30f;
+            for (int nt : {128, 256, 64})
+                for (int tiles : {8, 16, 32}) {
+                    float ms = 0.0f;
+                    rc = batch_run(ctx, n_cones, cones, b, nt, (int64_t)tiles * kTile, 8, false, &ms);
+                    if (rc) return rc;
+                    if (ms < best) {
+                        best = ms;
+                        NT = nt;
+                        per_item = (int64_t)tiles * kTile;
+                    }
+                }
+            ctx->batch.tuned[key] = std::make_pair(NT, (int)per_item);
+        }
+    }
+    rc = batch_run(ctx, n_cones, cones, b, NT, per_item, 0, want_rays, nullptr);
+    if (rc) return rc;
+    // read back per cone
+    auto &BS = ctx->batch;
+    const int nr = 1 + b->n_ring;
+    int64_t nbt = 0;
+    for (int c = 0; c < n_cones; ++c) nbt += cones[c].n_bundles;
+    std::vector<double> bo((size_t)(6 * nbt));
+    CK(cudaMemcpy(bo.data(), BS.bout, bo.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    std::vector<double> ro;
+    if (want_rays) {
+        ro.resize((size_t)(8 * nr * nbt));
+        CK(cudaMemcpy(ro.data(), BS.rout, ro.size() * sizeof(double), cudaMemcpyDeviceToHost));
+    }
+    int64_t off = 0;
+    for (int c = 0; c < n_cones; ++c) {
+        const int64_t nb = cones[c].n_bundles;
+        unpack_bundles(bo.data() + 6 * off, nb, &outs[c]);
+        if (want_rays && outs[c].ray_state)
+            memcpy(outs[c].ray_state, ro.data() + 8 * nr * off, 8 * nr * nb * sizeof(double));
+        off += nb;
+    }
+    if (want_rays) {
+        // crossing steps: read each cone's done/steps view
+        std::vector<int> steps;
+        int64_t T = 0;
+        const int RB = 4 * NT;
+        for (int c = 0; c < n_cones; ++c) T += ((cones[c].n_bundles * nr + RB - 1) / RB) * RB;
+        steps.resize((size_t)T);
+        CK(cudaMemcpy(steps.data(), BS.ints + T, T * sizeof(int), cudaMemcpyDeviceToHost));
+        int64_t base = 0;
+        for (int c = 0; c < n_cones; ++c) {
+            const int64_t n = cones[c].n_bundles * nr;
+            if (outs[c].ray_steps) memcpy(outs[c].ray_steps, steps.data() + base, n * sizeof(int));
+            base += ((n + RB - 1) / RB) * RB;
+        }
+    }
+    return RT3D_OK;
 }
 
 static int ensure_hist(rt3d_ctx *ctx, int bins)

@@ -1,0 +1,218 @@
+// batch.cu -- many independent light cones (each with its own particle field,
+// source redshift, bundles and step table) traced in one persistent launch.
+//
+// The persistent kernel is a cooperative launch of one resident grid.  For
+// every global RK4 stage it runs two phases separated by grid barriers:
+//   force phase: every (cone, ray block, particle split) work item of the
+//                cones still in flight, statically strided over the blocks;
+//   stage phase: the FP64 integrator stage of every ray of those cones.
+// Cones whose rays have all crossed their source plane drop out; cones with
+// fewer steps simply finish earlier.  The barrier waits are bounded by a
+// %globaltimer watchdog: on expiry the kernel sets an error word and returns,
+// and the host reports RT3D_ETIMEOUT.
+#include "batch_layout.cuh"
+#include "force.cuh"
+#include "trace_device.cuh"
+
+namespace rt3d {
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// Grid-wide barrier of a cooperative launch; every wait is bounded.
+__device__ __forceinline__ bool grid_sync(const BatchArgs &B)
+{
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = B.bar + 1;
+        const unsigned g0 = *gen;
+        __threadfence();
+        if (atomicAdd(B.bar, 1u) == gridDim.x - 1) {
+            atomicExch(B.bar, 0u);
+            __threadfence();
+            atomicAdd(B.bar + 1, 1u);
+        } else {
+            const unsigned long long t0 = global_ns();
+            while (*gen == g0) {
+                if (*(volatile int *)B.err) break;
+                if (global_ns() - t0 > B.limit_ns) {
+                    atomicExch(B.err, 1);
+                    break;
+                }
+                __nanosleep(128);
+            }
+        }
+        __threadfence();
+    }
+    __syncthreads();
+    return *(volatile int *)B.err == 0;
+}
+
+__device__ __forceinline__ bool cone_active(const BatchCone &C, int step)
+{
+    if (step >= C.total_steps) return false;
+    if (step < C.tp.n_steps) return true;
+    return *(volatile unsigned long long *)&C.cnt[(step - 1) & 1] != 0ull;
+}
+
+__global__ void k_batch_schedule(BatchArgs B)
+{
+    BatchCone &C = B.cones[blockIdx.y];
+    __shared__ double s_chi;
+    if (threadIdx.x == 0) {
+        s_chi = comoving_distance(C.tp.cosmo, C.z_s);
+        if (blockIdx.x == 0) C.chi_s = s_chi;
+    }
+    __syncthreads();
+    const int n = C.tp.n_steps;
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        C.dlam[k] = schedule_step(C.tp.cosmo, C.kind, n, k, s_chi, C.chi_l, C.s_asinh);
+}
+
+__global__ void k_batch_init(BatchArgs B)
+{
+    const int64_t r = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= B.T) return;
+    const BatchCone &C = B.cones[B.rb2cone[r / B.RB]];
+    const int64_t local = r - C.ray_base;
+    if (local >= C.rs.n_rays) return;
+    if (local == 0) C.cnt[0] = C.cnt[1] = C.cnt[2] = 0ull;
+    init_ray(C.tp, C.f, C.theta, C.rs, local);
+}
+
+template <int P, int NT>
+__device__ __forceinline__ void batch_item(const BatchCone &C, int4 item, int g, float4 *s_a, float4 *s_b,
+                                           float2 *s_e)
+{
+    const int64_t base = (int64_t)item.y * (NT * 2 * P);
+    const int64_t p0 = (int64_t)item.z * C.per_split;
+    const int64_t p1 = min(C.f.n, p0 + C.per_split);
+    const int64_t st = C.rs.stride;
+    const double *px = C.rs.ys + st, *py = C.rs.ys + 2 * st, *pz = C.rs.ys + 3 * st;
+    const int *rep = C.rs.rep + (g & 1) * C.rs.n_b;
+#define RT3D_ITEM(R_, E_, U_)                                                                                   \
+    packed_block_sum<P, NT, R_, E_, U_>(C.f, px, py, pz, rep, C.rs.nr, C.rs.n_rays, base, p0, p1, item.z,        \
+                                        C.partials, s_a, s_b, s_e)
+    switch (C.flags) {
+    case 0: RT3D_ITEM(false, false, false); break;
+    case 1: RT3D_ITEM(true, false, false); break;
+    case 2: RT3D_ITEM(false, true, false); break;
+    case 3: RT3D_ITEM(true, true, false); break;
+    case 4: RT3D_ITEM(false, false, true); break;
+    case 5: RT3D_ITEM(true, false, true); break;
+    case 6: RT3D_ITEM(false, true, true); break;
+    default: RT3D_ITEM(true, true, true); break;
+    }
+#undef RT3D_ITEM
+}
+
+template <int P, int NT>
+__global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
+{
+    __shared__ float4 s_a[kTile];
+    __shared__ float4 s_b[kTile];
+    __shared__ float2 s_e[kTile];
+    const int64_t nthreads = (int64_t)gridDim.x * NT;
+    for (int g = 0; g < B.g_end; ++g) {
+        const int step = g >> 2, stage = g & 3;
+        for (int64_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
+            const int4 item = B.items[it];
+            const BatchCone &C = B.cones[item.x];
+            if (!cone_active(C, step)) continue;  // uniform across the block
+            batch_item<P, NT>(C, item, g, s_a, s_b, s_e);
+        }
+        if (!grid_sync(B)) return;
+        for (int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x; r < B.T; r += nthreads) {
+            const int c = B.rb2cone[r / B.RB];
+            const BatchCone &C = B.cones[c];
+            const int64_t local = r - C.ray_base;
+            bool act = false;
+            if (local < C.rs.n_rays) {
+                if (stage == 0 && local == 0) C.cnt[step & 1] = 0ull;
+                if (cone_active(C, step))
+                    act = stage_ray(C.tp, C.f, C.rs, C.S, false, C.mfac, C.partials, C.dlam, C.chi_s, step, stage,
+                                    C.cnt, local);
+            }
+            // ray blocks are multiples of 32 rays, so a warp never spans two cones
+            const unsigned m = __ballot_sync(0xffffffffu, act);
+            if ((threadIdx.x & 31) == 0 && m) atomicAdd(&C.cnt[2], (unsigned long long)__popc(m));
+        }
+        if (!grid_sync(B)) return;
+    }
+}
+
+__global__ void k_batch_reduce(BatchArgs B, int64_t n_b_total)
+{
+    const int64_t gb = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gb >= n_b_total) return;
+    int lo = 0, hi = B.n_cones - 1;
+    while (lo < hi) {  // last cone whose first bundle is <= gb
+        const int mid = (lo + hi + 1) / 2;
+        if (B.cones[mid].b_base <= gb) lo = mid;
+        else hi = mid - 1;
+    }
+    const BatchCone &C = B.cones[lo];
+    const int64_t b = gb - C.b_base;
+    reduce_bundle(C.tp, C.theta, C.rs, C.chi_s, b, B.bout + 6 * gb, C.rout);
+}
+
+// ---------------------------------------------------------------------------
+// launch wrappers (the host orchestration lives in api.cu)
+// ---------------------------------------------------------------------------
+template <int P, int NT>
+static cudaError_t batch_occupancy(int *blocks_per_sm)
+{
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_run<P, NT>, NT, 0);
+}
+
+cudaError_t batch_resident_blocks(int P, int NT, int *out)
+{
+    int dev = 0, sms = 0, per = 0;
+    cudaError_t e;
+    if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
+    if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
+    if (P == 2 && NT == 128) e = batch_occupancy<2, 128>(&per);
+    else if (P == 2 && NT == 256) e = batch_occupancy<2, 256>(&per);
+    else if (P == 2 && NT == 64) e = batch_occupancy<2, 64>(&per);
+    else return cudaErrorInvalidConfiguration;
+    if (e != cudaSuccess) return e;
+    *out = per * sms;
+    return cudaSuccess;
+}
+
+cudaError_t batch_launch(const BatchArgs &B, int P, int NT, int grid, int max_sched_steps, int64_t n_b_total,
+                         cudaStream_t st)
+{
+    cudaError_t e;
+    {
+        int bx = (max_sched_steps + 127) / 128;
+        if (bx > 64) bx = 64;
+        k_batch_schedule<<<dim3((unsigned)std::max(bx, 1), (unsigned)B.n_cones), 128, 0, st>>>(B);
+        if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    k_batch_init<<<(unsigned)((B.T + 255) / 256), 256, 0, st>>>(B);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)grid);
+    cfg.blockDim = dim3((unsigned)NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (P == 2 && NT == 128) e = cudaLaunchKernelEx(&cfg, k_batch_run<2, 128>, B);
+    else if (P == 2 && NT == 256) e = cudaLaunchKernelEx(&cfg, k_batch_run<2, 256>, B);
+    else if (P == 2 && NT == 64) e = cudaLaunchKernelEx(&cfg, k_batch_run<2, 64>, B);
+    else e = cudaErrorInvalidConfiguration;
+    if (e != cudaSuccess) return e;
+    k_batch_reduce<<<(unsigned)((n_b_total + 127) / 128), 128, 0, st>>>(B, n_b_total);
+    return cudaGetLastError();
+}
+
+}  // namespace rt3d

@@ -198,18 +198,23 @@ __device__ __forceinline__ void two_sum2_into(float2 &hi, float2 &lo, float2 x)
     lo = __fadd2_rn(lo, __fadd2_rn(e1, e2));
 }
 
+// Sum of one block's rays over particles [p0, p1) of field f: the body shared
+// by the pair-sum launch and the batched persistent kernel.  Rays
+// base + k*NT + tid (k < 2P, index < n) with replica rep[i / group]; output
+// (hi, lo) pairs to out[(split*4 + o)*n + i] (phi: (sum, 0)).
 template <int P, int NT, bool REPL, bool PEPS, bool UMASS>
-__global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
+__device__ __forceinline__ void packed_block_sum(const DevField &f, const double *__restrict__ px,
+                                                 const double *__restrict__ py, const double *__restrict__ pz,
+                                                 const int *__restrict__ rep, int group, int64_t n, int64_t base,
+                                                 int64_t p0, int64_t p1, int split, float2 *__restrict__ out,
+                                                 float4 *s_a, float4 *s_b, float2 *s_e)
 {
     constexpr int R = 2 * P;
-    if (A.gate && *A.gate == 0ull) return;
-    __shared__ float4 s_a[kTile];            // (x, x, y, y)
-    __shared__ float4 s_b[kTile];            // (z, z, m, m)
-    __shared__ float2 s_e[PEPS ? kTile : 1]; // (eps2, eps2)
-    const DevField &f = A.f;
     const int tid = threadIdx.x;
-    const int64_t base = (int64_t)blockIdx.x * (NT * R);
-    const int split = blockIdx.y;
+    ForceArgs A;
+    A.rep = rep;
+    A.group = group;
+    A.n = n;
     int myrep[R], rmin, rmax;
     block_replica_range<R, NT>(A, base, myrep, rmin, rmax);
 
@@ -218,16 +223,14 @@ __global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
     for (int p = 0; p < P; ++p) {
         phi[p] = hx[p] = hy[p] = hz[p] = lx[p] = ly[p] = lz[p] = make_float2(0.0f, 0.0f);
     }
-    const int64_t p0 = (int64_t)split * A.per_split;
-    const int64_t p1 = min(f.n, p0 + A.per_split);
     const float dlt = (float)f.delta;
     const float2 E2u = make_float2(f.eps2u, f.eps2u);
     for (int j = rmin; j <= rmax; ++j) {
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((A.px[base] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((A.py[base] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((A.pz[base] - o[2]) * f.inv_delta);
+        const long long ax = __double2ll_rn((px[base] - o[0]) * f.inv_delta);
+        const long long ay = __double2ll_rn((py[base] - o[1]) * f.inv_delta);
+        const long long az = __double2ll_rn((pz[base] - o[2]) * f.inv_delta);
         // negated ray offsets: d = particle + (-ray)
         float2 nx[P], ny[P], nz[P];
 #pragma unroll
@@ -237,10 +240,10 @@ __global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
             for (int h = 0; h < 2; ++h) {
                 const int k = 2 * p + h;
                 const int64_t i = base + (int64_t)k * NT + tid;
-                if (i < A.n && myrep[k] == j) {
-                    v[h][0] = -(float)(((A.px[i] - o[0]) * f.inv_delta - (double)ax) * f.delta);
-                    v[h][1] = -(float)(((A.py[i] - o[1]) * f.inv_delta - (double)ay) * f.delta);
-                    v[h][2] = -(float)(((A.pz[i] - o[2]) * f.inv_delta - (double)az) * f.delta);
+                if (i < n && myrep[k] == j) {
+                    v[h][0] = -(float)(((px[i] - o[0]) * f.inv_delta - (double)ax) * f.delta);
+                    v[h][1] = -(float)(((py[i] - o[1]) * f.inv_delta - (double)ay) * f.delta);
+                    v[h][2] = -(float)(((pz[i] - o[2]) * f.inv_delta - (double)az) * f.delta);
                 } else {  // far sentinel: every contribution is exactly zero
                     v[h][0] = v[h][1] = v[h][2] = -1e30f;
                 }
@@ -313,20 +316,34 @@ __global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
             }
         }
     }
-    float2 *out = (float2 *)A.out;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t i = base + (int64_t)(2 * p + h) * NT + tid;
-            if (i >= A.n) continue;
+            if (i >= n) continue;
             const float ph = h ? phi[p].y : phi[p].x;
-            out[((int64_t)split * 4 + 0) * A.n + i] = make_float2(ph, 0.0f);
-            out[((int64_t)split * 4 + 1) * A.n + i] = h ? make_float2(hx[p].y, lx[p].y) : make_float2(hx[p].x, lx[p].x);
-            out[((int64_t)split * 4 + 2) * A.n + i] = h ? make_float2(hy[p].y, ly[p].y) : make_float2(hy[p].x, ly[p].x);
-            out[((int64_t)split * 4 + 3) * A.n + i] = h ? make_float2(hz[p].y, lz[p].y) : make_float2(hz[p].x, lz[p].x);
+            out[((int64_t)split * 4 + 0) * n + i] = make_float2(ph, 0.0f);
+            out[((int64_t)split * 4 + 1) * n + i] = h ? make_float2(hx[p].y, lx[p].y) : make_float2(hx[p].x, lx[p].x);
+            out[((int64_t)split * 4 + 2) * n + i] = h ? make_float2(hy[p].y, ly[p].y) : make_float2(hy[p].x, ly[p].x);
+            out[((int64_t)split * 4 + 3) * n + i] = h ? make_float2(hz[p].y, lz[p].y) : make_float2(hz[p].x, lz[p].x);
         }
     }
+}
+
+template <int P, int NT, bool REPL, bool PEPS, bool UMASS>
+__global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
+{
+    if (A.gate && *A.gate == 0ull) return;
+    __shared__ float4 s_a[kTile];            // (x, x, y, y)
+    __shared__ float4 s_b[kTile];            // (z, z, m, m)
+    __shared__ float2 s_e[PEPS ? kTile : 1]; // (eps2, eps2)
+    const int64_t base = (int64_t)blockIdx.x * (NT * 2 * P);
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * A.per_split;
+    const int64_t p1 = min(A.f.n, p0 + A.per_split);
+    packed_block_sum<P, NT, REPL, PEPS, UMASS>(A.f, A.px, A.py, A.pz, A.rep, A.group, A.n, base, p0, p1, split,
+                                               (float2 *)A.out, s_a, s_b, s_e);
 }
 
 // FP64 twin (the all-FP64 path): same staging, FP64 arithmetic, plain sums.

@@ -1,68 +1,13 @@
 // kernels.cu -- FP64 kernels of the trace: step schedule (cosmology
 // precompute), bundle initialiser, RK4 integrator stage, bundle reducer,
 // muPDF histogram and particle staging.
-#include <math_constants.h>
-
-#include "rt3d_internal.cuh"
+#include "trace_device.cuh"
 
 namespace rt3d {
 
 // ---------------------------------------------------------------------------
 // background cosmology on the device (Sec. 3.5, Eq. raytracedistance)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double hubble_E(const Cosmo &c, double z)
-{
-    double u = 1.0 + z;
-    return sqrt(c.om * u * u * u + c.ol);
-}
-
-// chi(z) = (1/H0) int_0^z dz'/E(z') by composite Boole's rule (5-point
-// Newton-Cotes, error O(h^7)), panels no wider than 0.02 in z.
-__device__ double comoving_distance(const Cosmo &c, double z)
-{
-    if (z <= 0.0) return 0.0;
-    int panels = (int)ceil(z / 0.02);
-    if (panels < 1) panels = 1;
-    const double w = z / panels, h = 0.25 * w;
-    double acc = 0.0;
-    for (int p = 0; p < panels; ++p) {
-        const double z0 = p * w;
-        const double f0 = 1.0 / hubble_E(c, z0), f1 = 1.0 / hubble_E(c, z0 + h),
-                     f2 = 1.0 / hubble_E(c, z0 + 2 * h), f3 = 1.0 / hubble_E(c, z0 + 3 * h),
-                     f4 = 1.0 / hubble_E(c, z0 + w);
-        acc += (7.0 * (f0 + f4) + 32.0 * (f1 + f3) + 12.0 * f2) * (2.0 * h / 45.0);
-    }
-    return acc / c.H0;
-}
-
-// redshift at comoving distance chi (Newton on chi(z), d chi/dz = 1/(H0 E))
-__device__ double redshift_at(const Cosmo &c, double chi)
-{
-    if (chi <= 0.0) return 0.0;
-    double z = chi * c.H0;
-    for (int it = 0; it < 40; ++it) {
-        const double dz = (comoving_distance(c, z) - chi) * c.H0 * hubble_E(c, z);
-        z -= dz;
-        if (fabs(dz) <= 2e-16 * (1.0 + z)) break;
-    }
-    return z;
-}
-
-__device__ __forceinline__ double a2_at(const Cosmo &c, double chi)
-{
-    const double a = 1.0 / (1.0 + redshift_at(c, chi));
-    return a * a;
-}
-
-__device__ __forceinline__ double sched_node(int kind, int n, int k, double chi_s, double chi_l, double s)
-{
-    if (k == 0) return 0.0;
-    if (k == n) return chi_s;
-    if (kind == RT3D_SCHED_UNIFORM) return chi_s * (double)k / (double)n;
-    const double u0 = asinh((0.0 - chi_l) / s), u1 = asinh((chi_s - chi_l) / s);
-    return chi_l + s * sinh(u0 + (u1 - u0) * (double)k / (double)n);
-}
-
 // One block computes chi_s; every thread then fills dlam[k] = int a^2 dchi over
 // [x_k, x_{k+1}] (the affine step of the unperturbed ray with dx3/dl = 1 at the
 // observer), by composite Boole's rule with 4 panels.
@@ -76,20 +21,8 @@ __global__ void k_schedule(Cosmo c, double z_s, int kind, int n, double chi_l, d
     }
     __syncthreads();
     const double chi_s = s_chi;
-    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x) {
-        const double x0 = sched_node(kind, n, k, chi_s, chi_l, s), x1 = sched_node(kind, n, k + 1, chi_s, chi_l, s);
-        const double w = (x1 - x0) * 0.25, h = 0.25 * w;
-        double acc = 0.0;
-        double fl = a2_at(c, x0);
-        for (int p = 0; p < 4; ++p) {
-            const double xa = x0 + p * w;
-            const double f1 = a2_at(c, xa + h), f2 = a2_at(c, xa + 2 * h), f3 = a2_at(c, xa + 3 * h);
-            const double f4 = a2_at(c, p == 3 ? x1 : xa + w);
-            acc += (7.0 * (fl + f4) + 32.0 * (f1 + f3) + 12.0 * f2) * (2.0 * h / 45.0);
-            fl = f4;
-        }
-        dlam[k] = acc;
-    }
+    for (int k = blockIdx.x * blockDim.x + threadIdx.x; k < n; k += gridDim.x * blockDim.x)
+        dlam[k] = schedule_step(c, kind, n, k, chi_s, chi_l, s);
 }
 
 cudaError_t launch_schedule(const Cosmo &c, double z_s, int kind, int n, double chi_l, double s, double *d_dlam,
@@ -104,20 +37,6 @@ cudaError_t launch_schedule(const Cosmo &c, double z_s, int kind, int n, double 
 // ---------------------------------------------------------------------------
 // bundle initialiser (Sec. 3.1, ray bundle; initial state of Sec. 3.4)
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ void ray_theta(const TraceParams &tp, const double *theta, int64_t b, int k,
-                                          double &tx, double &ty)
-{
-    tx = theta[2 * b];
-    ty = theta[2 * b + 1];
-    if (k > 0) {
-        const double ang = tp.phase + 2.0 * CUDART_PI * (double)(k - 1) / (double)tp.n_ring;
-        double sn, cs;
-        sincos(ang, &sn, &cs);
-        tx += tp.theta_r * cs;
-        ty += tp.theta_r * sn;
-    }
-}
-
 __global__ void k_init(TraceParams tp, DevField f, const double *__restrict__ theta, RayState rs,
                        unsigned long long *cnt)
 {
@@ -126,24 +45,7 @@ __global__ void k_init(TraceParams tp, DevField f, const double *__restrict__ th
         cnt[0] = cnt[1] = cnt[2] = 0ull;
     }
     if (i >= rs.n_rays) return;
-    const int64_t b = i / rs.nr;
-    const int k = (int)(i % rs.nr);
-    double tx, ty;
-    ray_theta(tp, theta, b, k, tx, ty);
-    // observer: t = 0 (lookback), x = 0, direction (theta_x, theta_y, 1) with
-    // dx3/dl = 1; dt/dl is set from the null condition at the first stage
-    const double v[8] = {0.0, 0.0, 0.0, 0.0, sqrt(tx * tx + ty * ty + 1.0), tx, ty, 1.0};
-    const int64_t n = rs.n_rays;
-#pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        rs.y[q * n + i] = v[q];
-        rs.ys[q * n + i] = v[q];
-        rs.ks[q * n + i] = 0.0;
-        rs.fin[q * n + i] = 0.0;
-    }
-    rs.done[i] = 0;
-    rs.steps[i] = -1;
-    if (k == 0) rs.rep[b] = replica_of(f, 0.0);  // stage parity 0
+    init_ray(tp, f, theta, rs, i);
 }
 
 cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *d_theta, RayState rs,
@@ -158,86 +60,6 @@ cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *
 // integrator stage (Eq. geodesiceqn with the App. A symbols, classical RK4,
 // termination on x3 with linear interpolation: Sec. 3.4)
 // ---------------------------------------------------------------------------
-// Reduce the pair-sum partials of one ray and add the mean subtraction:
-// F = (phi, dphi/dx1, dphi/dx2, dphi/dx3) at the ray's stage position.
-__device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64, const void *partials, int64_t n,
-                                             int64_t i, int rep, const double p[3], double mfac, double F[4])
-{
-    double acc[4] = {0.0, 0.0, 0.0, 0.0};
-    if (fp64) {
-        const double *pd = (const double *)partials;
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int o = 0; o < 4; ++o) acc[o] += pd[((int64_t)s * 4 + o) * n + i];
-    } else {
-        // the (hi, lo) FP32 pairs are added as double-float numbers (TwoSum on
-        // hi, lo carried separately): ~48-bit sums on the FP32 pipe, converted
-        // to FP64 once, instead of 2S conversions and adds on the FP64 pipe
-        const float2 *pm = (const float2 *)partials;
-        float hi[4] = {0.0f, 0.0f, 0.0f, 0.0f}, lo[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-        for (int s = 0; s < S; ++s)
-#pragma unroll
-            for (int o = 0; o < 4; ++o) {
-                const float2 v = pm[((int64_t)s * 4 + o) * n + i];
-                const float t = hi[o] + v.x;
-                const float bb = t - hi[o];
-                const float err = (hi[o] - (t - bb)) + (v.x - bb);
-                hi[o] = t;
-                lo[o] += err + v.y;
-            }
-#pragma unroll
-        for (int o = 0; o < 4; ++o) acc[o] = (double)hi[o] + (double)lo[o];
-    }
-    // partial sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with
-    // d = particle - point and m'' = mu_G m 2^ms (or the same sums without m''
-    // for a uniform-mass field, mfac = m''): phi = -S0 mfac / 2^ms,
-    // grad phi = -S mfac / 2^ms
-    const double sp = f.mscale_inv * mfac, sg = sp;
-    F[0] = -acc[0] * sp;
-    F[1] = -acc[1] * sg;
-    F[2] = -acc[2] * sg;
-    F[3] = -acc[3] * sg;
-    if (f.replicated && f.mean_subtract) {
-        // remove the field of the replica's uniform mean density (Sec. 3.3)
-        const double lo[3] = {-0.5 * f.L, -0.5 * f.L, (double)rep * f.L};
-        const double hi[3] = {0.5 * f.L, 0.5 * f.L, (double)(rep + 1) * f.L};
-        double I[4];
-        prism_field<double>(lo, hi, p, I);
-        F[0] += f.rho_term * I[0];
-        F[1] += f.rho_term * I[1];
-        F[2] += f.rho_term * I[2];
-        F[3] += f.rho_term * I[3];
-    }
-}
-
-// d y / d lambda for y = (t, x1, x2, x3, dt/dl, dx1/dl, dx2/dl, dx3/dl):
-// d^2 x^a / dl^2 = -Gamma^a_bc u^b u^c with App. A's first-order symbols
-//   Gamma^t_tt = -a' phi / a^2,  Gamma^t_ti = phi_i / a,  Gamma^t_ii = a' (a + phi)
-//   Gamma^i_tt = phi_i / a^3,    Gamma^i_ti = a' (a + phi) / a^2,
-//   Gamma^i_jk = (-phi_k d_ij - phi_j d_ik + phi_i d_jk) / a
-// (christoffel = DERIVED replaces Gamma^t_ii by a' (a - 3 phi)).
-__device__ __forceinline__ void geodesic_rhs(const double y[8], const double F[4], double a, double ad,
-                                             int christoffel, double k[8])
-{
-    const double T = y[4], vx = y[5], vy = y[6], vz = y[7];
-    const double phi = F[0], gx = F[1], gy = F[2], gz = F[3];
-    const double ia = 1.0 / a;
-    const double gv = gx * vx + gy * vy + gz * vz;
-    const double v2 = vx * vx + vy * vy + vz * vz;
-    const double gtii = christoffel == RT3D_CHRISTOFFEL_DERIVED ? ad * (a - 3.0 * phi) : ad * (a + phi);
-    const double gitj = ad * (a + phi) * ia * ia;
-    k[0] = T;
-    k[1] = vx;
-    k[2] = vy;
-    k[3] = vz;
-    k[4] = ad * phi * ia * ia * T * T - 2.0 * ia * gv * T - gtii * v2;
-    const double tt = T * T * ia * ia * ia;
-    const double drag = 2.0 * gitj * T;
-    k[5] = -gx * tt - drag * vx - ia * (gx * v2 - 2.0 * vx * gv);
-    k[6] = -gy * tt - drag * vy - ia * (gy * v2 - 2.0 * vy * gv);
-    k[7] = -gz * tt - drag * vz - ia * (gz * v2 - 2.0 * vz * gv);
-}
-
 __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RayState rs, int S, int fp64,
                                               double mfac, const void *__restrict__ partials,
                                               const double *__restrict__ dlam,
@@ -250,64 +72,9 @@ __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RaySt
     __shared__ unsigned s_active;
     if (threadIdx.x == 0) s_active = 0;
     __syncthreads();
-    const int64_t n = rs.n_rays;
-    const bool valid = i < n;
-    const int g = step * 4 + stage;  // global stage index: replica buffers alternate on its parity
-    if (valid) {
-        const int64_t b = i / rs.nr;
-        const int rep = rs.rep[(g & 1) * rs.n_b + b];
-        double ys[8], y[8], k[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            ys[q] = rs.ys[q * n + i];
-            y[q] = rs.y[q * n + i];
-        }
-        double F[4];
-        gather_field(f, S, fp64 != 0, partials, n, i, rep, ys + 1, mfac, F);
-        const double a = cosmo_a(tp.cosmo, ys[0]);
-        const double ad = cosmo_adot(tp.cosmo, a);
-        if (step == 0 && stage == 0) {
-            // null condition of Eq. expandingmetric with psi = phi / a
-            const double vn = sqrt(ys[5] * ys[5] + ys[6] * ys[6] + ys[7] * ys[7]);
-            const double T = a * vn * sqrt((1.0 - 2.0 * F[0] / a) / (1.0 + 2.0 * F[0] / a));
-            ys[4] = T;
-            y[4] = T;
-            rs.y[4 * n + i] = T;
-        }
-        geodesic_rhs(ys, F, a, ad, tp.christoffel, k);
-        const double dl = dlam[step < tp.n_steps ? step : tp.n_steps - 1];
-        const int done = rs.done[i];
-        if (!done) atomicAdd(&s_active, 1u);
-        double nx[8];
-        if (stage < 3) {
-            const double c = stage == 2 ? dl : 0.5 * dl;
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                const double acc = stage == 0 ? k[q] : rs.ks[q * n + i] + 2.0 * k[q];
-                rs.ks[q * n + i] = acc;
-                nx[q] = y[q] + c * k[q];
-                rs.ys[q * n + i] = nx[q];
-            }
-        } else {
-#pragma unroll
-            for (int q = 0; q < 8; ++q) nx[q] = y[q] + dl / 6.0 * (rs.ks[q * n + i] + k[q]);
-            const double chi_s = misc[0];
-            if (!done && nx[3] >= chi_s) {
-                const double s = (chi_s - y[3]) / (nx[3] - y[3]);
-#pragma unroll
-                for (int q = 0; q < 8; ++q) rs.fin[q * n + i] = y[q] + s * (nx[q] - y[q]);
-                rs.done[i] = 1;
-                rs.steps[i] = step + 1;
-            } else if (!done) {
-                atomicAdd((unsigned long long *)&cnt[step & 1], 1ull);
-            }
-#pragma unroll
-            for (int q = 0; q < 8; ++q) {
-                rs.y[q * n + i] = nx[q];
-                rs.ys[q * n + i] = nx[q];
-            }
-        }
-        if (i % rs.nr == 0) rs.rep[((g + 1) & 1) * rs.n_b + b] = replica_of(f, nx[3]);
+    if (i < rs.n_rays) {
+        if (stage_ray(tp, f, rs, S, fp64 != 0, mfac, partials, dlam, misc[0], step, stage, cnt, i))
+            atomicAdd(&s_active, 1u);
     }
     __syncthreads();
     if (threadIdx.x == 0 && s_active) atomicAdd(&cnt[2], (unsigned long long)s_active);
@@ -357,60 +124,7 @@ __global__ void k_reduce(TraceParams tp, const double *__restrict__ theta, RaySt
 {
     const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (b >= rs.n_b) return;
-    const int64_t n = rs.n_rays;
-    const double chi_s = misc[0];
-    int flags = 0;
-    double x0 = 0, y0 = 0, tx0 = 0, ty0 = 0;
-    double M00 = 0, M01 = 0, M10 = 0, M11 = 0, N00 = 0, N01 = 0, N10 = 0, N11 = 0;
-    for (int k = 0; k < rs.nr; ++k) {
-        const int64_t i = b * rs.nr + k;
-        const int done = rs.done[i];
-        const double *src = done ? rs.fin : rs.y;
-        if (!done) flags |= RT3D_F_NOCROSS;
-        double st[8];
-#pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            st[q] = src[q * n + i];
-            if (!isfinite(st[q])) flags |= RT3D_F_NONFINITE;
-        }
-        if (rout)
-#pragma unroll
-            for (int q = 0; q < 8; ++q) rout[i * 8 + q] = st[q];
-        double tx, ty;
-        ray_theta(tp, theta, b, k, tx, ty);
-        if (k == 0) {
-            x0 = st[1];
-            y0 = st[2];
-            tx0 = tx;
-            ty0 = ty;
-        } else {
-            const double dbx = (st[1] - x0) / chi_s, dby = (st[2] - y0) / chi_s;
-            const double dtx = tx - tx0, dty = ty - ty0;
-            M00 += dbx * dtx;
-            M01 += dbx * dty;
-            M10 += dby * dtx;
-            M11 += dby * dty;
-            N00 += dtx * dtx;
-            N01 += dtx * dty;
-            N10 += dty * dtx;
-            N11 += dty * dty;
-        }
-    }
-    const double dn = N00 * N11 - N01 * N10;
-    const double i00 = N11 / dn, i01 = -N01 / dn, i10 = -N10 / dn, i11 = N00 / dn;
-    const double A00 = M00 * i00 + M01 * i10, A01 = M00 * i01 + M01 * i11;
-    const double A10 = M10 * i00 + M11 * i10, A11 = M10 * i01 + M11 * i11;
-    const double det = A00 * A11 - A01 * A10;
-    const double mu = 1.0 / det;
-    if (!isfinite(mu)) flags |= RT3D_F_NONFINITE;
-    if (mu < 0.0) flags |= RT3D_F_NEGPARITY;
-    double *o = bout + 6 * b;
-    o[0] = mu;
-    o[1] = 1.0 - 0.5 * (A00 + A11);
-    o[2] = 0.5 * (A11 - A00);
-    o[3] = -0.5 * (A01 + A10);
-    o[4] = 0.5 * (A01 - A10);
-    o[5] = (double)flags;
+    reduce_bundle(tp, theta, rs, misc[0], b, bout + 6 * b, rout);
 }
 
 cudaError_t launch_reduce(const TraceParams &tp, const double *d_theta, RayState rs, const double *d_misc,

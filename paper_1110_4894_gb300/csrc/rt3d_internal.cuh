@@ -169,9 +169,10 @@ struct RayState {
     double *fin;   // 8 x nr  state interpolated to x3 = chi_s
     int *done;     // nr
     int *steps;    // nr
-    int *rep;      // n_bundles: replica for the current stage
+    int *rep;      // 2 x n_bundles: replica of each bundle for even / odd stages
     int64_t n_rays, n_b;
     int nr;        // rays per bundle (1 + n_ring)
+    int64_t stride;  // component stride of y, ys, ks, fin (n_rays for a single trace)
 };
 
 struct TraceParams {
