@@ -18,6 +18,7 @@ namespace rt3d {
 cudaError_t dispatch_mixed(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
 cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
 cudaError_t dispatch_packed(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
+cudaError_t dispatch_bundle(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 struct BatchArgs;
 
 // ---------------------------------------------------------------------------
@@ -479,7 +480,10 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
 // ---------------------------------------------------------------------------
 // launch shape
 // ---------------------------------------------------------------------------
-static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_points, bool fp64)
+// group = rays per bundle for a trace (1 for arbitrary points).  Traces with
+// rings of 4 or 8 use the bundle-centric kernel (R = rays per bundle, NT =
+// bundles per block); other calls the packed kernel (R rays per thread).
+static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_points, bool fp64, int group = 1)
 {
     const int64_t n_particles = f.n;
     ForceShape sh;
@@ -488,6 +492,11 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
         sh.variant = 2;
         sh.R = 2;
         sh.NT = 128;
+    } else if (ctx->opt.variant == 0 && (group == 5 || group == 9)) {
+        sh.variant = 3;
+        sh.umass = f.uniform_mass ? 1 : 0;
+        sh.R = group;
+        sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : 128;
     } else {
         sh.variant = ctx->opt.variant == 1 ? 1 : 0;
         sh.umass = (sh.variant == 0 && f.uniform_mass) ? 1 : 0;
@@ -539,6 +548,7 @@ static cudaError_t run_force(rt3d_ctx *ctx, const DevField &f, const double *px,
     (void)fp64;
     if (sh.variant == 2) return dispatch_fp64(A, sh, st);
     if (sh.variant == 1) return dispatch_mixed(A, sh, st);
+    if (sh.variant == 3) return dispatch_bundle(A, sh, sh.umass != 0, st);
     return dispatch_packed(A, sh, sh.umass != 0, st);
 }
 
@@ -574,7 +584,7 @@ static ForceShape with_splits(ForceShape sh, int64_t n_points, int64_t n_particl
 static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, const double *py, const double *pz,
                        const int *rep, int group, int64_t n, bool fp64, cudaStream_t st, ForceShape &out)
 {
-    ForceShape base = choose_shape(ctx, fs.df, n, fp64);
+    ForceShape base = choose_shape(ctx, fs.df, n, fp64, group);
     if (!ctx->opt.autotune || ctx->opt.rays_per_thread > 0 || ctx->opt.threads_per_block > 0 || ctx->opt.splits > 0) {
         out = base;
         return RT3D_OK;
@@ -590,12 +600,14 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     std::vector<int> waves;
     const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
     const int rn64[][2] = {{2, 128}, {1, 128}};
-    const int nrn = fp64 ? 2 : 4;
+    const int rnb[][2] = {{group, 128}, {group, 64}, {group, 256}};
+    const int nrn = base.variant == 2 ? 2 : (base.variant == 3 ? 3 : 4);
     for (int c = 0; c < nrn; ++c)
         for (int w : {2, 3, 5, 8}) {
             ForceShape s = base;
-            s.R = fp64 ? rn64[c][0] : rn[c][0];
-            s.NT = fp64 ? rn64[c][1] : rn[c][1];
+            const int *p = base.variant == 2 ? rn64[c] : (base.variant == 3 ? rnb[c] : rn[c]);
+            s.R = p[0];
+            s.NT = p[1];
             cand.push_back(with_splits(s, n, fs.n, w));
             waves.push_back(w);
         }
@@ -694,7 +706,7 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     const bool fp64 = ctx->opt.precision == RT3D_FP64;
     const int nr = 1 + b->n_ring;
     const int64_t n_rays = n_b * nr;
-    ForceShape sh = choose_shape(ctx, fs.df, n_rays, fp64);
+    ForceShape sh = choose_shape(ctx, fs.df, n_rays, fp64, nr);
     int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
     if (rc) return rc;
     RayState rs = make_state(ctx, n_b, nr);
@@ -959,8 +971,10 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
 {
     auto &BS = ctx->batch;
     const int P = 2;
-    const int RB = 2 * P * NT;
     const int nr = 1 + b->n_ring;
+    // rays per block: NT bundles (bundle-centric kernel, rings of 4 or 8) or
+    // 2P rays per thread (packed kernel); both are multiples of 32
+    const int RB = (nr == 5 || nr == 9) ? NT * nr : 2 * P * NT;
     BatchPlan plan;
     int rc = plan_batch(ctx->fields.data(), n_cones, cones, nr, RB, per_item, b->max_extra, plan);
     if (rc) return fail(ctx, rc, "invalid cone list");
@@ -990,7 +1004,8 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     CK(cudaMemcpyAsync(BS.rb2cone, plan.rb2cone.data(), plan.rb2cone.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(BS.bar, 0, 4 * sizeof(unsigned), st));
     int grid = 0;
-    CK(batch_resident_blocks(P, NT, &grid));
+    const int MODE = nr == 5 ? 4 : (nr == 9 ? 8 : 0);
+    CK(batch_resident_blocks(NT, MODE, &grid));
     if (grid < 1) return fail(ctx, RT3D_ECUDA, "persistent kernel cannot be resident");
     BatchArgs A = make_batch_args(BS.cones, n_cones, BS.items, (int64_t)plan.items.size(), BS.rb2cone, T, RB,
                                   g_limit > 0 ? g_limit : plan.g_end, BS.bar, (int *)(BS.bar + 2),
@@ -1008,7 +1023,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
         }
         cudaGraph_t gr = nullptr;
         CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-        cudaError_t le = batch_launch(A, P, NT, grid, plan.max_steps, plan.n_b_total, st);
+        cudaError_t le = batch_launch(A, NT, MODE, grid, plan.max_steps, plan.n_b_total, st);
         cudaError_t ce = cudaStreamEndCapture(st, &gr);
         if (le != cudaSuccess || ce != cudaSuccess) {
             if (gr) cudaGraphDestroy(gr);
@@ -1027,7 +1042,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
         }
     }
     if (use_graph) CK(cudaGraphLaunch(BS.exec, st));
-    else CK(batch_launch(A, P, NT, grid, plan.max_steps, plan.n_b_total, st));
+    else CK(batch_launch(A, NT, MODE, grid, plan.max_steps, plan.n_b_total, st));
     CK(cudaEventRecord(ctx->ev1, st));
     CK(cudaEventSynchronize(ctx->ev1));
     float ms = 0.0f;
@@ -1040,7 +1055,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     ctx->stats.launches = 4;
     ctx->stats.force_launches = 1;
     ctx->stats.steps = plan.max_steps + b->max_extra;
-    ctx->stats.rays_per_thread = 2 * P;
+    ctx->stats.rays_per_thread = (nr == 5 || nr == 9) ? nr : 2 * P;
     ctx->stats.threads_per_block = NT;
     ctx->stats.splits = (int)per_item;
     ctx->stats.force_ms = ms;
@@ -1092,6 +1107,7 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
     for (int c = 0; c < n_cones; ++c) want_rays |= outs[c].ray_state != nullptr || outs[c].ray_steps != nullptr;
     // launch shape: block size and particles per work item (autotuned per size class)
     int NT = ctx->opt.threads_per_block == 64 || ctx->opt.threads_per_block == 256 ? ctx->opt.threads_per_block : 128;
+    if (NT == 256 && b->n_ring == 8) NT = 128;
     int64_t per_item = ctx->opt.splits > 0 ? (int64_t)ctx->opt.splits * kTile : 16 * kTile;
     if (ctx->opt.autotune && ctx->opt.threads_per_block <= 0 && ctx->opt.splits <= 0) {
         int64_t rays = 0;
@@ -1109,6 +1125,7 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
             float best = 1e30f;
             for (int nt : {128, 256, 64})
                 for (int tiles : {8, 16, 32}) {
+                    if (nt == 256 && b->n_ring == 8) continue;
                     float ms = 0.0f;
                     rc = batch_run(ctx, n_cones, cones, b, nt, (int64_t)tiles * kTile, 8, false, &ms);
                     if (rc) return rc;
@@ -1147,7 +1164,7 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
         // crossing steps: read each cone's done/steps view
         std::vector<int> steps;
         int64_t T = 0;
-        const int RB = 4 * NT;
+        const int RB = (nr == 5 || nr == 9) ? NT * nr : 4 * NT;
         for (int c = 0; c < n_cones; ++c) T += ((cones[c].n_bundles * nr + RB - 1) / RB) * RB;
         steps.resize((size_t)T);
         CK(cudaMemcpy(steps.data(), BS.ints + T, T * sizeof(int), cudaMemcpyDeviceToHost));

@@ -84,16 +84,38 @@ __global__ void k_batch_init(BatchArgs B)
     init_ray(C.tp, C.f, C.theta, C.rs, local);
 }
 
-template <int P, int NT>
+// MODE 4 / 8: bundle-centric kernel for rings of 4 / 8 rays; MODE 0: packed
+template <int P, int NT, int MODE>
 __device__ __forceinline__ void batch_item(const BatchCone &C, int4 item, int g, float4 *s_a, float4 *s_b,
                                            float2 *s_e)
 {
-    const int64_t base = (int64_t)item.y * (NT * 2 * P);
     const int64_t p0 = (int64_t)item.z * C.per_split;
     const int64_t p1 = min(C.f.n, p0 + C.per_split);
     const int64_t st = C.rs.stride;
     const double *px = C.rs.ys + st, *py = C.rs.ys + 2 * st, *pz = C.rs.ys + 3 * st;
     const int *rep = C.rs.rep + (g & 1) * C.rs.n_b;
+    if (MODE != 0) {  // bundle-centric: block = NT bundles
+        const int64_t b0 = (int64_t)item.y * NT;
+#define RT3D_BITEM(NRING_, R_, E_, U_)                                                                          \
+    bundle_block_sum<NT, NRING_, R_, E_, U_>(C.f, px, py, pz, rep, C.rs.n_b, C.rs.n_rays, b0, p0, p1, item.z,   \
+                                             C.partials, s_a, (float *)s_e)
+#define RT3D_BFLAGS(NRING_)                                          \
+    switch (C.flags) {                                               \
+    case 0: RT3D_BITEM(NRING_, false, false, false); break;          \
+    case 1: RT3D_BITEM(NRING_, true, false, false); break;           \
+    case 2: RT3D_BITEM(NRING_, false, true, false); break;           \
+    case 3: RT3D_BITEM(NRING_, true, true, false); break;            \
+    case 4: RT3D_BITEM(NRING_, false, false, true); break;           \
+    case 5: RT3D_BITEM(NRING_, true, false, true); break;            \
+    case 6: RT3D_BITEM(NRING_, false, true, true); break;            \
+    default: RT3D_BITEM(NRING_, true, true, true); break;            \
+    }
+        RT3D_BFLAGS(MODE == 8 ? 8 : 4)
+#undef RT3D_BFLAGS
+#undef RT3D_BITEM
+        return;
+    }
+    const int64_t base = (int64_t)item.y * (NT * 2 * P);
 #define RT3D_ITEM(R_, E_, U_)                                                                                   \
     packed_block_sum<P, NT, R_, E_, U_>(C.f, px, py, pz, rep, C.rs.nr, C.rs.n_rays, base, p0, p1, item.z,        \
                                         C.partials, s_a, s_b, s_e)
@@ -110,7 +132,7 @@ __device__ __forceinline__ void batch_item(const BatchCone &C, int4 item, int g,
 #undef RT3D_ITEM
 }
 
-template <int P, int NT>
+template <int P, int NT, int MODE>
 __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
 {
     __shared__ float4 s_a[kTile];
@@ -123,7 +145,7 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
             const int4 item = B.items[it];
             const BatchCone &C = B.cones[item.x];
             if (!cone_active(C, step)) continue;  // uniform across the block
-            batch_item<P, NT>(C, item, g, s_a, s_b, s_e);
+            batch_item<P, NT, MODE>(C, item, g, s_a, s_b, s_e);
         }
         if (!grid_sync(B)) return;
         for (int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x; r < B.T; r += nthreads) {
@@ -163,28 +185,42 @@ __global__ void k_batch_reduce(BatchArgs B, int64_t n_b_total)
 // ---------------------------------------------------------------------------
 // launch wrappers (the host orchestration lives in api.cu)
 // ---------------------------------------------------------------------------
-template <int P, int NT>
+template <int NT, int MODE>
 static cudaError_t batch_occupancy(int *blocks_per_sm)
 {
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_run<P, NT>, NT, 0);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_run<2, NT, MODE>, NT, 0);
 }
 
-cudaError_t batch_resident_blocks(int P, int NT, int *out)
+template <int NT, int MODE>
+static cudaError_t batch_coop(const cudaLaunchConfig_t &cfg, const BatchArgs &B)
+{
+    return cudaLaunchKernelEx(&cfg, k_batch_run<2, NT, MODE>, B);
+}
+
+#define RT3D_BATCH_SHAPES(F, ...)                                              \
+    if (NT == 128 && MODE == 4) e = F<128, 4>(__VA_ARGS__);                    \
+    else if (NT == 256 && MODE == 4) e = F<256, 4>(__VA_ARGS__);               \
+    else if (NT == 64 && MODE == 4) e = F<64, 4>(__VA_ARGS__);                 \
+    else if (NT == 128 && MODE == 8) e = F<128, 8>(__VA_ARGS__);               \
+    else if (NT == 64 && MODE == 8) e = F<64, 8>(__VA_ARGS__);                 \
+    else if (NT == 128 && MODE == 0) e = F<128, 0>(__VA_ARGS__);               \
+    else if (NT == 256 && MODE == 0) e = F<256, 0>(__VA_ARGS__);               \
+    else if (NT == 64 && MODE == 0) e = F<64, 0>(__VA_ARGS__);                 \
+    else e = cudaErrorInvalidConfiguration;
+
+cudaError_t batch_resident_blocks(int NT, int MODE, int *out)
 {
     int dev = 0, sms = 0, per = 0;
     cudaError_t e;
     if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
     if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-    if (P == 2 && NT == 128) e = batch_occupancy<2, 128>(&per);
-    else if (P == 2 && NT == 256) e = batch_occupancy<2, 256>(&per);
-    else if (P == 2 && NT == 64) e = batch_occupancy<2, 64>(&per);
-    else return cudaErrorInvalidConfiguration;
+    RT3D_BATCH_SHAPES(batch_occupancy, &per)
     if (e != cudaSuccess) return e;
     *out = per * sms;
     return cudaSuccess;
 }
 
-cudaError_t batch_launch(const BatchArgs &B, int P, int NT, int grid, int max_sched_steps, int64_t n_b_total,
+cudaError_t batch_launch(const BatchArgs &B, int NT, int MODE, int grid, int max_sched_steps, int64_t n_b_total,
                          cudaStream_t st)
 {
     cudaError_t e;
@@ -206,13 +242,11 @@ cudaError_t batch_launch(const BatchArgs &B, int P, int NT, int grid, int max_sc
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    if (P == 2 && NT == 128) e = cudaLaunchKernelEx(&cfg, k_batch_run<2, 128>, B);
-    else if (P == 2 && NT == 256) e = cudaLaunchKernelEx(&cfg, k_batch_run<2, 256>, B);
-    else if (P == 2 && NT == 64) e = cudaLaunchKernelEx(&cfg, k_batch_run<2, 64>, B);
-    else e = cudaErrorInvalidConfiguration;
+    RT3D_BATCH_SHAPES(batch_coop, cfg, B)
     if (e != cudaSuccess) return e;
     k_batch_reduce<<<(unsigned)((n_b_total + 127) / 128), 128, 0, st>>>(B, n_b_total);
     return cudaGetLastError();
 }
+#undef RT3D_BATCH_SHAPES
 
 }  // namespace rt3d

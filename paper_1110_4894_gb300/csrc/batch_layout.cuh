@@ -55,8 +55,9 @@ inline BatchArgs make_batch_args(void *cones, int n_cones, const int4 *items, in
     return A;
 }
 
-cudaError_t batch_resident_blocks(int P, int NT, int *out);
-cudaError_t batch_launch(const BatchArgs &B, int P, int NT, int grid, int max_sched_steps, int64_t n_b_total,
+// MODE: 4 or 8 = bundle-centric pair sum for rings of that size, 0 = packed
+cudaError_t batch_resident_blocks(int NT, int MODE, int *out);
+cudaError_t batch_launch(const BatchArgs &B, int NT, int MODE, int grid, int max_sched_steps, int64_t n_b_total,
                          cudaStream_t st);
 
 }  // namespace rt3d

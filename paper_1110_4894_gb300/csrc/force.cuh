@@ -346,6 +346,196 @@ __global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
                                                (float2 *)A.out, s_a, s_b, s_e);
 }
 
+// Bundle-centric variant: one thread per bundle (central ray + NRING rays).
+// Each satellite's offset from a particle is formed from the central ray's,
+//   d_k = (p - r_c) + (r_c - r_k),
+// with r_c - r_k taken in FP64 and rounded once.  The large, rounded
+// quantities (the particle's and the central ray's offsets from the block
+// anchor) are then common to every ray of the bundle and cancel from the
+// bundle's differential deflection, which sets the magnification: its
+// position error is ulp(|d|), not ulp(|anchor distance|).  The central ray
+// runs in scalar FP32, the satellites in f32x2 pairs.  Particles are staged
+// once, (x, y, z, m), plus eps^2 when it varies per particle.
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>
+__device__ __forceinline__ void bundle_block_sum(const DevField &f, const double *__restrict__ px,
+                                                 const double *__restrict__ py, const double *__restrict__ pz,
+                                                 const int *__restrict__ rep, int64_t n_b, int64_t n_rays,
+                                                 int64_t b0, int64_t p0, int64_t p1, int split,
+                                                 float2 *__restrict__ out, float4 *s_p, float *s_e)
+{
+    constexpr int NR = NRING + 1, PP = NRING / 2;
+    const int tid = threadIdx.x;
+    const int64_t b = b0 + tid;
+    const bool valid = b < n_b;
+    const int64_t ic = b * NR;  // central ray
+    __shared__ int s_rmin, s_rmax;
+    if (tid == 0) {
+        s_rmin = INT_MAX;
+        s_rmax = INT_MIN;
+    }
+    __syncthreads();
+    const int myrep = valid ? (rep ? rep[b] : 0) : -1;
+    if (valid) {
+        atomicMin(&s_rmin, myrep);
+        atomicMax(&s_rmax, myrep);
+    }
+    __syncthreads();
+    const int rmin = s_rmin, rmax = s_rmax;
+
+    // satellite offsets r_c - r_k (FP64 difference, one rounding)
+    float2 ex[PP], ey[PP], ez[PP];
+#pragma unroll
+    for (int p = 0; p < PP; ++p) {
+        float v[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+        if (valid) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t ik = ic + 1 + 2 * p + h;
+                v[h][0] = (float)(px[ic] - px[ik]);
+                v[h][1] = (float)(py[ic] - py[ik]);
+                v[h][2] = (float)(pz[ic] - pz[ik]);
+            }
+        }
+        ex[p] = make_float2(v[0][0], v[1][0]);
+        ey[p] = make_float2(v[0][1], v[1][1]);
+        ez[p] = make_float2(v[0][2], v[1][2]);
+    }
+    float c_phi = 0.f, c_hx = 0.f, c_hy = 0.f, c_hz = 0.f, c_lx = 0.f, c_ly = 0.f, c_lz = 0.f;
+    float2 phi[PP], hx[PP], hy[PP], hz[PP], lx[PP], ly[PP], lz[PP];
+#pragma unroll
+    for (int p = 0; p < PP; ++p) phi[p] = hx[p] = hy[p] = hz[p] = lx[p] = ly[p] = lz[p] = make_float2(0.f, 0.f);
+    const float dlt = (float)f.delta;
+    const int64_t ia = b0 * NR;  // anchor: the block's first central ray
+    for (int j = rmin; j <= rmax; ++j) {
+        double o[3];
+        frame_origin(f, j, o);
+        const long long ax = __double2ll_rn((px[ia] - o[0]) * f.inv_delta);
+        const long long ay = __double2ll_rn((py[ia] - o[1]) * f.inv_delta);
+        const long long az = __double2ll_rn((pz[ia] - o[2]) * f.inv_delta);
+        float nx = -1e30f, ny = -1e30f, nz = -1e30f;  // far sentinel
+        if (valid && myrep == j) {
+            nx = -(float)(((px[ic] - o[0]) * f.inv_delta - (double)ax) * f.delta);
+            ny = -(float)(((py[ic] - o[1]) * f.inv_delta - (double)ay) * f.delta);
+            nz = -(float)(((pz[ic] - o[2]) * f.inv_delta - (double)az) * f.delta);
+        }
+        for (int64_t t0 = p0; t0 < p1; t0 += kTile) {
+            __syncthreads();
+            for (int q = tid; q < kTile; q += NT) {
+                const int64_t pi = t0 + q;
+                float4 v = make_float4(1e18f, 1e18f, 1e18f, 0.0f);
+                float e2 = 0.0f;
+                if (pi < p1) {
+                    const int4 pr = f.part[pi];
+                    long long qq[3] = {pr.x, pr.y, pr.z};
+                    if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
+                    v = make_float4((float)(qq[0] - ax) * dlt, (float)(qq[1] - ay) * dlt, (float)(qq[2] - az) * dlt,
+                                    __int_as_float(pr.w));
+                    if (PEPS) e2 = f.eps2[pi];
+                }
+                s_p[q] = v;
+                if (PEPS) s_e[q] = e2;
+            }
+            __syncthreads();
+            for (int c0 = 0; c0 < kTile; c0 += kChunk) {
+                float ccx = 0.f, ccy = 0.f, ccz = 0.f;
+                float2 cx[PP], cy[PP], cz[PP];
+#pragma unroll
+                for (int p = 0; p < PP; ++p) cx[p] = cy[p] = cz[p] = make_float2(0.f, 0.f);
+#pragma unroll 2
+                for (int jj = c0; jj < c0 + kChunk; ++jj) {
+                    const float4 a = s_p[jj];
+                    const float e2 = PEPS ? s_e[jj] : f.eps2u;
+                    // central ray (scalar)
+                    const float dx = a.x + nx, dy = a.y + ny, dz = a.z + nz;
+                    const float r2 = fmaf(dx, dx, fmaf(dy, dy, fmaf(dz, dz, e2)));
+                    const float inv = rsqrt_mufu(r2);
+                    const float i2 = inv * inv;
+                    float mi3;
+                    if (UMASS) {
+                        c_phi += inv;
+                        mi3 = inv * i2;
+                    } else {
+                        const float mi = a.w * inv;
+                        c_phi += mi;
+                        mi3 = mi * i2;
+                    }
+                    ccx = fmaf(dx, mi3, ccx);
+                    ccy = fmaf(dy, mi3, ccy);
+                    ccz = fmaf(dz, mi3, ccz);
+                    // satellites in pairs: d_k = d_c + (r_c - r_k)
+                    const float2 DX = make_float2(dx, dx), DY = make_float2(dy, dy), DZ = make_float2(dz, dz);
+                    const float2 E2 = make_float2(e2, e2);
+#pragma unroll
+                    for (int p = 0; p < PP; ++p) {
+                        const float2 qx = __fadd2_rn(DX, ex[p]);
+                        const float2 qy = __fadd2_rn(DY, ey[p]);
+                        const float2 qz = __fadd2_rn(DZ, ez[p]);
+                        float2 s2 = __ffma2_rn(qz, qz, E2);
+                        s2 = __ffma2_rn(qy, qy, s2);
+                        s2 = __ffma2_rn(qx, qx, s2);
+                        const float2 w = make_float2(rsqrt_mufu(s2.x), rsqrt_mufu(s2.y));
+                        const float2 w2 = __fmul2_rn(w, w);
+                        float2 m3;
+                        if (UMASS) {
+                            phi[p] = __fadd2_rn(phi[p], w);
+                            m3 = __fmul2_rn(w, w2);
+                        } else {
+                            const float2 mw = __fmul2_rn(make_float2(a.w, a.w), w);
+                            phi[p] = __fadd2_rn(phi[p], mw);
+                            m3 = __fmul2_rn(mw, w2);
+                        }
+                        cx[p] = __ffma2_rn(qx, m3, cx[p]);
+                        cy[p] = __ffma2_rn(qy, m3, cy[p]);
+                        cz[p] = __ffma2_rn(qz, m3, cz[p]);
+                    }
+                }
+                two_sum_into(c_hx, c_lx, ccx);
+                two_sum_into(c_hy, c_ly, ccy);
+                two_sum_into(c_hz, c_lz, ccz);
+#pragma unroll
+                for (int p = 0; p < PP; ++p) {
+                    two_sum2_into(hx[p], lx[p], cx[p]);
+                    two_sum2_into(hy[p], ly[p], cy[p]);
+                    two_sum2_into(hz[p], lz[p], cz[p]);
+                }
+            }
+        }
+    }
+    if (!valid) return;
+    const int64_t sn = (int64_t)split * 4;
+    out[(sn + 0) * n_rays + ic] = make_float2(c_phi, 0.f);
+    out[(sn + 1) * n_rays + ic] = make_float2(c_hx, c_lx);
+    out[(sn + 2) * n_rays + ic] = make_float2(c_hy, c_ly);
+    out[(sn + 3) * n_rays + ic] = make_float2(c_hz, c_lz);
+#pragma unroll
+    for (int p = 0; p < PP; ++p)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t i = ic + 1 + 2 * p + h;
+            out[(sn + 0) * n_rays + i] = make_float2(h ? phi[p].y : phi[p].x, 0.f);
+            out[(sn + 1) * n_rays + i] = h ? make_float2(hx[p].y, lx[p].y) : make_float2(hx[p].x, lx[p].x);
+            out[(sn + 2) * n_rays + i] = h ? make_float2(hy[p].y, ly[p].y) : make_float2(hy[p].x, ly[p].x);
+            out[(sn + 3) * n_rays + i] = h ? make_float2(hz[p].y, lz[p].y) : make_float2(hz[p].x, lz[p].x);
+        }
+}
+
+// ForceArgs for the bundle kernel: n = rays, group = rays per bundle; rep is
+// the per-bundle replica array.
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>
+__global__ void __launch_bounds__(NT) k_force_bundle(ForceArgs A)
+{
+    if (A.gate && *A.gate == 0ull) return;
+    __shared__ float4 s_p[kTile];
+    __shared__ float s_e[PEPS ? kTile : 1];
+    const int64_t n_b = A.n / (NRING + 1);
+    const int64_t b0 = (int64_t)blockIdx.x * NT;
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * A.per_split;
+    const int64_t p1 = min(A.f.n, p0 + A.per_split);
+    bundle_block_sum<NT, NRING, REPL, PEPS, UMASS>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
+                                                   (float2 *)A.out, s_p, s_e);
+}
+
 // FP64 twin (the all-FP64 path): same staging, FP64 arithmetic, plain sums.
 template <int R, int NT, bool REPL, bool PEPS>
 __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
