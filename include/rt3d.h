@@ -74,7 +74,9 @@ typedef struct {
     int autotune;          /* 1: time candidate launch shapes once per size bucket */
     double watchdog_s;     /* limit for the persistent kernel's waits; 0 = 10 s */
     int time_kernels;      /* 1: bracket every pair-sum launch with CUDA events (stats.force_ms) */
-    int variant;           /* pair-sum kernel: 0 = packed FP32x2 (default), 1 = scalar FP32 */
+    int variant;           /* pair-sum kernel: 0 = automatic (bundle-centric FP32x2 for traces),
+                              1 = scalar FP32, 2 = packed FP32x2 per ray, 3 = one bundle per thread,
+                              4 = two bundles per thread (rings of 4) */
 } rt3d_options;
 
 /* Mass distribution layout.

@@ -19,7 +19,11 @@ cudaError_t dispatch_mixed(const ForceArgs &A, const ForceShape &sh, cudaStream_
 cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t st);
 cudaError_t dispatch_packed(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 cudaError_t dispatch_bundle(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
+cudaError_t dispatch_bundle2(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 struct BatchArgs;
+
+// rays covered by one block of the pair-sum kernel of shape sh
+inline int64_t rays_per_block(const ForceShape &sh) { return (int64_t)sh.R * sh.NT * (sh.variant == 4 ? 2 : 1); }
 
 // ---------------------------------------------------------------------------
 // particle staging (S2): FP64 input -> integer grid + scaled masses
@@ -492,18 +496,21 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
         sh.variant = 2;
         sh.R = 2;
         sh.NT = 128;
-    } else if (ctx->opt.variant == 0 && (group == 5 || group == 9)) {
-        sh.variant = 3;
+    } else if ((ctx->opt.variant == 0 || ctx->opt.variant >= 3) && (group == 5 || group == 9)) {
+        // bundle-centric: two bundles per thread for rings of 4 (variant 4),
+        // one per thread otherwise (variant 3)
+        sh.variant = (group == 5 && ctx->opt.variant != 3) ? 4 : 3;
         sh.umass = f.uniform_mass ? 1 : 0;
         sh.R = group;
-        sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : 128;
+        sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : (sh.variant == 4 ? 64 : 128);
+        if (sh.variant == 4 && sh.NT > 128) sh.NT = 128;
     } else {
         sh.variant = ctx->opt.variant == 1 ? 1 : 0;
         sh.umass = (sh.variant == 0 && f.uniform_mass) ? 1 : 0;
         sh.R = ctx->opt.rays_per_thread > 0 ? ctx->opt.rays_per_thread : 4;
         sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : 128;
     }
-    const int64_t per_block = (int64_t)sh.R * sh.NT;
+    const int64_t per_block = rays_per_block(sh);
     const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
     int S;
     if (ctx->opt.splits > 0) {
@@ -549,6 +556,7 @@ static cudaError_t run_force(rt3d_ctx *ctx, const DevField &f, const double *px,
     if (sh.variant == 2) return dispatch_fp64(A, sh, st);
     if (sh.variant == 1) return dispatch_mixed(A, sh, st);
     if (sh.variant == 3) return dispatch_bundle(A, sh, sh.umass != 0, st);
+    if (sh.variant == 4) return dispatch_bundle2(A, sh, sh.umass != 0, st);
     return dispatch_packed(A, sh, sh.umass != 0, st);
 }
 
@@ -570,7 +578,7 @@ static int ilog2(int64_t v)
 
 static ForceShape with_splits(ForceShape sh, int64_t n_points, int64_t n_particles, int waves)
 {
-    const int64_t per_block = (int64_t)sh.R * sh.NT;
+    const int64_t per_block = rays_per_block(sh);
     const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
     const int64_t slots = 152 * std::max(1, 640 / sh.NT);
     int S = (int)std::max<int64_t>(1, (waves * slots + nrb - 1) / nrb);
@@ -600,14 +608,22 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     std::vector<int> waves;
     const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
     const int rn64[][2] = {{2, 128}, {1, 128}};
-    const int rnb[][2] = {{group, 128}, {group, 64}, {group, 256}};
-    const int nrn = base.variant == 2 ? 2 : (base.variant == 3 ? 3 : 4);
+    // bundle shapes: {variant, bundles per block}
+    const int rnb[][3] = {{3, group, 128}, {3, group, 64}, {3, group, 256}, {4, group, 64}, {4, group, 128}};
+    const bool bundles = base.variant == 3 || base.variant == 4;
+    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 5 : 3) : 4);
     for (int c = 0; c < nrn; ++c)
         for (int w : {2, 3, 5, 8}) {
             ForceShape s = base;
-            const int *p = base.variant == 2 ? rn64[c] : (base.variant == 3 ? rnb[c] : rn[c]);
-            s.R = p[0];
-            s.NT = p[1];
+            if (bundles) {
+                s.variant = rnb[c][0];
+                s.R = rnb[c][1];
+                s.NT = rnb[c][2];
+            } else {
+                const int *p = base.variant == 2 ? rn64[c] : rn[c];
+                s.R = p[0];
+                s.NT = p[1];
+            }
             cand.push_back(with_splits(s, n, fs.n, w));
             waves.push_back(w);
         }

@@ -46,13 +46,14 @@ def _cloud(n, seed, centre=(0.0, 0.0, 800.0), scale=0.3, per_particle_soft=False
     return pos, mass, soft
 
 
-PRECISIONS = ["fp64", "mixed", "mixed-scalar"]
+PRECISIONS = ["fp64", "mixed", "mixed-scalar", "mixed-packed", "mixed-bundle1"]
+VARIANT = {"mixed": 0, "mixed-scalar": 1, "mixed-packed": 2, "mixed-bundle1": 3}
 
 
 def ctx_prec(P, precision, **kw):
     if precision == "fp64":
         return ctx_for(P, P.FP64, **kw)
-    return ctx_for(P, P.MIXED, variant=1 if precision == "mixed-scalar" else 0, **kw)
+    return ctx_for(P, P.MIXED, variant=VARIANT[precision], **kw)
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
