@@ -34,7 +34,10 @@ FLOPS_PER_INTERACTION = 20  # direct N-body convention (3 sub, 6 fma/mul for r^2
 N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6  # FLOP/s at the maximum SM clock
 HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
-PROFILED_DRAM_BYTES = 2130432  # dram__bytes_read.sum + dram__bytes_write.sum of one k_force_packed launch
+KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2"}
+# dram__bytes_read.sum + dram__bytes_write.sum of one pair-sum launch on this
+# workload, per kernel, from the ncu captures summarised under profiles/
+PROFILED_DRAM_BYTES = {"k_force_packed": 2130432}
 
 
 def workload(full=True):
@@ -321,10 +324,10 @@ def run_ours(args):
         avg_launch_s = force_ms / 1e3 / max(1, force_launches)
         achieved = FLOPS_PER_INTERACTION * per_launch / avg_launch_s if avg_launch_s > 0 else 0.0
         shape = ctx.stats()
-        # DRAM bytes per pair-sum launch from the ncu capture summarised in
-        # profiles/k_force_packed_nfw_1e5p_4096b.md (particles and positions;
-        # the split partials stay in L2); reported for the kernel as captured
-        traffic = PROFILED_DRAM_BYTES if not args.small else None
+        kname = KERNEL_NAMES.get(shape["variant"], "k_force")
+        # DRAM bytes per pair-sum launch from the ncu capture of this kernel
+        # (profiles/); null when the launched kernel was not captured
+        traffic = None if args.small else PROFILED_DRAM_BYTES.get(kname)
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -333,12 +336,12 @@ def run_ours(args):
                           "rk4_steps": cfg["n_steps"], "z_s": cfg["z_s"],
                           "precision": "fp32 pair sums (chunked TwoSum), fp64 ray state",
                           "l2": "256 MB buffer written between timed steps",
-                          "launch_shape": {"rays_per_thread": ctx.stats()["rays_per_thread"],
-                                           "threads_per_block": ctx.stats()["threads_per_block"],
-                                           "splits": ctx.stats()["splits"]}},
+                          "launch_shape": {"rays_per_thread": shape["rays_per_thread"],
+                                           "threads_per_block": shape["threads_per_block"],
+                                           "splits": shape["splits"], "kernel": kname}},
                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK / 1e12,
                             "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": traffic,
-                            "kernel": "k_force_packed", "flops_per_interaction": FLOPS_PER_INTERACTION,
+                            "kernel": kname, "flops_per_interaction": FLOPS_PER_INTERACTION,
                             "interactions_per_launch": per_launch, "avg_launch_ms": avg_launch_s * 1e3,
                             "peak_basis": "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived)"},
                "clocks": clocks,

@@ -135,6 +135,7 @@ typedef struct {
     int64_t force_launches;
     int steps;            /* RK4 steps issued */
     int rays_per_thread, threads_per_block, splits; /* force launch shape used */
+    int variant;          /* pair-sum kernel used: 0 packed, 1 scalar, 2 FP64, 3 bundle, 4 two bundles per thread */
 } rt3d_stats;
 
 /* One light cone of a batch (Sec. 5): its field, source redshift, bundles and steps. */

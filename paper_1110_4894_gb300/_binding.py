@@ -58,7 +58,8 @@ class Hist(C.Structure):
 class Stats(C.Structure):
     _fields_ = [("interactions", C.c_double), ("device_ms", C.c_double), ("force_ms", C.c_double),
                 ("launches", C.c_int64), ("force_launches", C.c_int64), ("steps", C.c_int),
-                ("rays_per_thread", C.c_int), ("threads_per_block", C.c_int), ("splits", C.c_int)]
+                ("rays_per_thread", C.c_int), ("threads_per_block", C.c_int), ("splits", C.c_int),
+                ("variant", C.c_int)]
 
 
 class Cone(C.Structure):

@@ -776,6 +776,7 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     ctx->stats.rays_per_thread = sh.R;
     ctx->stats.threads_per_block = sh.NT;
     ctx->stats.splits = sh.splits;
+    ctx->stats.variant = sh.variant;
     ctx->last_npart = (double)fs.n;
     ctx->stats_pending = true;
     return RT3D_OK;
@@ -1073,6 +1074,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     ctx->stats.steps = plan.max_steps + b->max_extra;
     ctx->stats.rays_per_thread = (nr == 5 || nr == 9) ? nr : 2 * P;
     ctx->stats.threads_per_block = NT;
+    ctx->stats.variant = (nr == 5 || nr == 9) ? 3 : 0;
     ctx->stats.splits = (int)per_item;
     ctx->stats.force_ms = ms;
     ctx->stats_pending = false;

@@ -60,20 +60,34 @@ cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *
 // integrator stage (Eq. geodesiceqn with the App. A symbols, classical RK4,
 // termination on x3 with linear interpolation: Sec. 3.4)
 // ---------------------------------------------------------------------------
+// A block of 256 threads serves 64 rays: first every thread reduces one
+// output of one ray's split partials (mixed precision: four threads per ray,
+// which keeps four times more loads in flight), then one thread per ray runs
+// the FP64 stage update with whole warps active.
+constexpr int kStageRays = 64;
+
 __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RayState rs, int S, int fp64,
                                               double mfac, const void *__restrict__ partials,
                                               const double *__restrict__ dlam,
                                               const double *__restrict__ misc, int step, int stage,
                                               unsigned long long *cnt)
 {
-    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (stage == 0 && blockIdx.x == 0 && threadIdx.x == 0) cnt[step & 1] = 0ull;
     if (step >= tp.n_steps && cnt[(step - 1) & 1] == 0ull) return;  // every ray is across
+    __shared__ double s_acc[kStageRays][4];
     __shared__ unsigned s_active;
     if (threadIdx.x == 0) s_active = 0;
+    const int64_t r0 = (int64_t)blockIdx.x * kStageRays;
+    if (!fp64) {
+        const int local = threadIdx.x >> 2, o = threadIdx.x & 3;
+        const int64_t i = r0 + local;
+        if (i < rs.n_rays) s_acc[local][o] = reduce_partials_mixed((const float2 *)partials, S, rs.n_rays, i, o);
+    }
     __syncthreads();
-    if (i < rs.n_rays) {
-        if (stage_ray(tp, f, rs, S, fp64 != 0, mfac, partials, dlam, misc[0], step, stage, cnt, i))
+    if (threadIdx.x < kStageRays) {
+        const int64_t i = r0 + threadIdx.x;
+        if (i < rs.n_rays && stage_ray(tp, f, rs, S, fp64 != 0, mfac, partials, dlam, misc[0], step, stage, cnt, i,
+                                       fp64 ? nullptr : s_acc[threadIdx.x]))
             atomicAdd(&s_active, 1u);
     }
     __syncthreads();
@@ -84,10 +98,8 @@ cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, 
                          const void *d_partials, const double *d_dlam, const double *d_misc, int step, int stage,
                          unsigned long long *d_counters, cudaStream_t st)
 {
-    // small blocks spread the FP64 work of a few thousand rays over every SM
-    const int bs = rs.n_rays >= 152 * 256 ? 256 : 64;
-    const int64_t blocks = (rs.n_rays + bs - 1) / bs;
-    k_stage<<<(unsigned)blocks, bs, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
+    const int64_t blocks = (rs.n_rays + kStageRays - 1) / kStageRays;
+    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
                                              d_partials, d_dlam, d_misc, step, stage, d_counters);
     return cudaGetLastError();
 }

@@ -131,6 +131,48 @@ __device__ __forceinline__ void init_ray(const TraceParams &tp, const DevField &
 // integrator stage (Eq. geodesiceqn with the App. A symbols, classical RK4,
 // termination on x3 with linear interpolation: Sec. 3.4)
 // ---------------------------------------------------------------------------
+// phi and grad phi from the reduced pair sums, plus the mean subtraction.
+// The sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with d = particle -
+// point and m'' = mu_G m 2^ms (or the same sums without m'' for a uniform-mass
+// field, mfac = m''): phi = -S0 mfac / 2^ms, grad phi = -S mfac / 2^ms.
+__device__ __forceinline__ void field_from_sums(const DevField &f, const double acc[4], int rep, const double p[3],
+                                                double mfac, double F[4])
+{
+    const double sp = f.mscale_inv * mfac, sg = sp;
+    F[0] = -acc[0] * sp;
+    F[1] = -acc[1] * sg;
+    F[2] = -acc[2] * sg;
+    F[3] = -acc[3] * sg;
+    if (f.replicated && f.mean_subtract) {
+        // remove the field of the replica's uniform mean density (Sec. 3.3)
+        const double lo[3] = {-0.5 * f.L, -0.5 * f.L, (double)rep * f.L};
+        const double hi[3] = {0.5 * f.L, 0.5 * f.L, (double)(rep + 1) * f.L};
+        double I[4];
+        prism_field<double>(lo, hi, p, I);
+        F[0] += f.rho_term * I[0];
+        F[1] += f.rho_term * I[1];
+        F[2] += f.rho_term * I[2];
+        F[3] += f.rho_term * I[3];
+    }
+}
+
+// One output of one ray's split partials, as a double-float sum in FP32
+// (TwoSum on the high parts, low parts carried), converted once to FP64.
+__device__ __forceinline__ double reduce_partials_mixed(const float2 *__restrict__ pm, int S, int64_t n, int64_t i,
+                                                        int o)
+{
+    float hi = 0.0f, lo = 0.0f;
+    for (int s = 0; s < S; ++s) {
+        const float2 v = pm[((int64_t)s * 4 + o) * n + i];
+        const float t = hi + v.x;
+        const float bb = t - hi;
+        const float err = (hi - (t - bb)) + (v.x - bb);
+        hi = t;
+        lo += err + v.y;
+    }
+    return (double)hi + (double)lo;
+}
+
 // Reduce the pair-sum partials of one ray and add the mean subtraction:
 // F = (phi, dphi/dx1, dphi/dx2, dphi/dx3) at the ray's stage position.
 __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64, const void *partials, int64_t n,
@@ -161,26 +203,7 @@ __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64
 #pragma unroll
         for (int o = 0; o < 4; ++o) acc[o] = (double)hi[o] + (double)lo[o];
     }
-    // partial sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with
-    // d = particle - point and m'' = mu_G m 2^ms (or the same sums without m''
-    // for a uniform-mass field, mfac = m''): phi = -S0 mfac / 2^ms,
-    // grad phi = -S mfac / 2^ms
-    const double sp = f.mscale_inv * mfac, sg = sp;
-    F[0] = -acc[0] * sp;
-    F[1] = -acc[1] * sg;
-    F[2] = -acc[2] * sg;
-    F[3] = -acc[3] * sg;
-    if (f.replicated && f.mean_subtract) {
-        // remove the field of the replica's uniform mean density (Sec. 3.3)
-        const double lo[3] = {-0.5 * f.L, -0.5 * f.L, (double)rep * f.L};
-        const double hi[3] = {0.5 * f.L, 0.5 * f.L, (double)(rep + 1) * f.L};
-        double I[4];
-        prism_field<double>(lo, hi, p, I);
-        F[0] += f.rho_term * I[0];
-        F[1] += f.rho_term * I[1];
-        F[2] += f.rho_term * I[2];
-        F[3] += f.rho_term * I[3];
-    }
+    field_from_sums(f, acc, rep, p, mfac, F);
 }
 
 // d y / d lambda for y = (t, x1, x2, x3, dt/dl, dx1/dl, dx2/dl, dx3/dl):
@@ -220,7 +243,7 @@ __device__ __forceinline__ void geodesic_rhs(const double y[8], const double F[4
 __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField &f, const RayState &rs, int S,
                                           bool fp64, double mfac, const void *__restrict__ partials,
                                           const double *__restrict__ dlam, double chi_s, int step, int stage,
-                                          unsigned long long *cnt, int64_t i)
+                                          unsigned long long *cnt, int64_t i, const double *pre = nullptr)
 {
     const int64_t st = rs.stride;
     const int64_t b = i / rs.nr;
@@ -233,7 +256,8 @@ __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField 
         y[q] = rs.y[q * st + i];
     }
     double F[4];
-    gather_field(f, S, fp64, partials, rs.n_rays, i, rep, ys + 1, mfac, F);
+    if (pre) field_from_sums(f, pre, rep, ys + 1, mfac, F);
+    else gather_field(f, S, fp64, partials, rs.n_rays, i, rep, ys + 1, mfac, F);
     const double a = cosmo_a(tp.cosmo, ys[0]);
     const double ad = cosmo_adot(tp.cosmo, a);
     if (step == 0 && stage == 0) {
