@@ -36,8 +36,10 @@ FP32_PEAK = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6  # FLOP/s at the maximum SM
 HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
 KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2"}
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-sum launch on this
-# workload, per kernel, from the ncu captures summarised under profiles/
-PROFILED_DRAM_BYTES = {"k_force_packed": 2130432}
+# workload, per (kernel, threads per block, splits), from the ncu captures
+# summarised under profiles/
+PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31): 2130432,
+                       ("k_force_bundle2", 128, 196): 2169600 + 68610304}
 
 
 def workload(full=True):
@@ -327,7 +329,8 @@ def run_ours(args):
         kname = KERNEL_NAMES.get(shape["variant"], "k_force")
         # DRAM bytes per pair-sum launch from the ncu capture of this kernel
         # (profiles/); null when the launched kernel was not captured
-        traffic = None if args.small else PROFILED_DRAM_BYTES.get(kname)
+        traffic = None if args.small else PROFILED_DRAM_BYTES.get(
+            (kname, shape["threads_per_block"], shape["splits"]))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
