@@ -24,6 +24,17 @@ class Cosmo(C.Structure):
     _fields_ = [("omega_m", C.c_double), ("omega_l", C.c_double), ("h", C.c_double)]
 
 
+class Grid(C.Structure):
+    _fields_ = [
+        ("n", C.c_int),
+        ("lo", C.c_double * 3),
+        ("h", C.c_double),
+        ("n_int", C.c_int),
+        ("val", C.POINTER(C.c_double)),
+        ("y2", C.POINTER(C.c_double)),
+    ]
+
+
 class Field(C.Structure):
     _fields_ = [
         ("n", C.c_int64),
@@ -37,6 +48,7 @@ class Field(C.Structure):
         ("rot", C.POINTER(C.c_int32)),
         ("shift", C.POINTER(C.c_double)),
         ("mean_subtract", C.c_int),
+        ("grid", C.POINTER(Grid)),
     ]
 
 
@@ -94,6 +106,12 @@ def lib():
         L.orc_histogram.argtypes = [C.c_int64, _dp, C.POINTER(C.c_int32), C.POINTER(HistOpts),
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _dp]
         L.orc_histogram.restype = C.c_int
+        L.orc_spline_y2.argtypes = [C.c_int, _dp, C.c_int64, _dp]
+        L.orc_spline_y2.restype = None
+        L.orc_grid_y2.argtypes = [C.c_int, _dp, _dp]
+        L.orc_grid_y2.restype = None
+        L.orc_grid_eval.argtypes = [C.POINTER(Grid), _dp, _dp]
+        L.orc_grid_eval.restype = None
         _lib = L
     return _lib
 
@@ -147,7 +165,7 @@ class MassField:
     """A particle mass distribution as the oracle sees it (Sec. 3.3, 5.2)."""
 
     def __init__(self, pos, mass, soft, replicated=False, L=0.0, rot=None, shift=None,
-                 mean_subtract=False):
+                 mean_subtract=False, grid=None):
         self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
         n = self.pos.shape[0]
         self.mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, np.float64), (n,)))
@@ -168,7 +186,8 @@ class MassField:
         self.f = Field(n, _p(self.pos), _p(self.mass),
                        _p(self.soft) if self.soft is not None else None, self.soft_scalar,
                        int(self.replicated), self.L, self.n_rep, _p(self.rot, C.c_int32), _p(self.shift),
-                       int(self.mean_subtract))
+                       int(self.mean_subtract), C.pointer(grid.g) if grid is not None else None)
+        self.grid = grid  # keeps the node arrays alive
 
 
 def potential(field, pts, rep=None, nthreads=None):

@@ -300,6 +300,10 @@ static void prep_free(prep_field *pf)
 static void field_eval(const orc_field *f, const prep_field *pf, int rep, const double *r,
                        double out[4], double *npairs)
 {
+    if (f->grid) {  /* grid path: the field interpolated from the nodes (App. B) */
+        orc_grid_eval(f->grid, r, out);
+        return;
+    }
     const double *w = pf->w[f->replicated ? rep : 0];
     nsum ph = {0, 0}, gx = {0, 0}, gy = {0, 0}, gz = {0, 0};
     for (int64_t i = 0; i < pf->n; ++i) {
@@ -334,6 +338,81 @@ static void field_eval(const orc_field *f, const prep_field *pf, int rep, const 
     }
 }
 
+/* ------------------------------------------------------------------------ */
+/* gridded field (Sec. 3.3 grid path; App. B "three-dimensional bicubic    */
+/* spline"): natural cubic splines with unit node spacing.                  */
+/* ------------------------------------------------------------------------ */
+void orc_spline_y2(int n, const double *y, int64_t stride, double *y2)
+{
+    /* y2[0] = y2[n-1] = 0;  y2[i-1] + 4 y2[i] + y2[i+1] = 6 (y[i+1] - 2 y[i] + y[i-1]) */
+    for (int i = 0; i < n; ++i) y2[i * stride] = 0.0;
+    if (n < 3) return;
+    double cp[4096], dp[4096];
+    if (n - 2 >= 4096) return;
+    cp[0] = 0.0;
+    dp[0] = 0.0;  /* y2[0] = 0 enters the first row as a known value */
+    for (int i = 1; i <= n - 2; ++i) {
+        double d = 6.0 * (y[(i + 1) * stride] - 2.0 * y[i * stride] + y[(i - 1) * stride]);
+        double den = 4.0 - cp[i - 1];
+        cp[i] = 1.0 / den;
+        dp[i] = (d - dp[i - 1]) / den;
+    }
+    y2[(n - 2) * stride] = dp[n - 2];
+    for (int i = n - 3; i >= 1; --i) y2[i * stride] = dp[i] - cp[i] * y2[(i + 1) * stride];
+}
+
+void orc_grid_y2(int n, const double *val, double *y2)
+{
+    const int64_t lines = 4 * (int64_t)n * n;
+    for (int64_t l = 0; l < lines; ++l) orc_spline_y2(n, val + l * n, 1, y2 + l * n);
+}
+
+/* cubic-spline value at u in [0, m-1] from values y and second derivatives y2 */
+static double splint_unit(int m, const double *y, const double *y2, double u)
+{
+    int k = (int)floor(u);
+    if (k > m - 2) k = m - 2;
+    if (k < 0) k = 0;
+    double A = (double)(k + 1) - u, B = u - (double)k;
+    return A * y[k] + B * y[k + 1] + ((A * A * A - A) * y2[k] + (B * B * B - B) * y2[k + 1]) / 6.0;
+}
+
+void orc_grid_eval(const orc_grid *g, const double r[3], double out[4])
+{
+    const int n = g->n, w = 2 * g->n_int;
+    double u[3];
+    int s[3];
+    for (int f = 0; f < 4; ++f) out[f] = 0.0;
+    if (w < 2 || w > 16 || n < w) return;
+    for (int d = 0; d < 3; ++d) {
+        u[d] = (r[d] - g->lo[d]) / g->h;
+        if (!(u[d] >= 0.0 && u[d] <= (double)(n - 1))) return;  /* outside the nodes: no field */
+        s[d] = (int)floor(u[d]) - g->n_int + 1;
+        if (s[d] > n - w) s[d] = n - w;
+        if (s[d] < 0) s[d] = 0;
+    }
+    const int64_t n3 = (int64_t)n * n * n;
+    for (int f = 0; f < 4; ++f) {
+        const double *v = g->val + f * n3, *y2 = g->y2 + f * n3;
+        double v1[16][16], v2[16], t[16], t2[16];
+        /* step 1: along x3 on every (x1, x2) node of the window, global spline */
+        for (int a = 0; a < w; ++a)
+            for (int b = 0; b < w; ++b) {
+                const int64_t line = ((int64_t)(s[0] + a) * n + (s[1] + b)) * n;
+                v1[a][b] = splint_unit(n, v + line, y2 + line, u[2]);
+            }
+        /* steps 2-3: along x1, one local spline per x2 node */
+        for (int b = 0; b < w; ++b) {
+            for (int a = 0; a < w; ++a) t[a] = v1[a][b];
+            orc_spline_y2(w, t, 1, t2);
+            v2[b] = splint_unit(w, t, t2, u[0] - (double)s[0]);
+        }
+        /* steps 4-5: along x2 */
+        orc_spline_y2(w, v2, 1, t2);
+        out[f] = splint_unit(w, v2, t2, u[1] - (double)s[1]);
+    }
+}
+
 static int rep_of(const orc_field *f, double x3)
 {
     if (!f->replicated) return 0;
@@ -346,6 +425,7 @@ static int rep_of(const orc_field *f, double x3)
 int orc_potential(const orc_field *f, int64_t n, const double *pts, const int32_t *rep,
                   double *out, int nthreads)
 {
+    if (f->grid && f->replicated) return -1;
     prep_field pf;
     if (prep_make(f, &pf) != 0) { prep_free(&pf); return -2; }
     for (int64_t i = 0; i < n; ++i)
@@ -442,6 +522,7 @@ int orc_trace(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b,
               double *bundle_out, int32_t *steps_out, double *n_pairs, int nthreads)
 {
     if (o->n_ring < 2 || o->n_steps < 1 || !(z_s > 0.0)) return -1;
+    if (f->grid && f->replicated) return -1;
     const int nr = 1 + o->n_ring;
     const double chi_s = orc_chi(c, z_s);
     double *dlam = (double *)malloc(sizeof(double) * (size_t)o->n_steps);

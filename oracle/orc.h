@@ -62,7 +62,33 @@ typedef struct {
     const int32_t *rot;   /* n_rep * 9 row-major signed permutation matrices */
     const double *shift;  /* n_rep * 3 shifts in [0, L) */
     int mean_subtract;    /* subtract the field of the replica's uniform mean */
+    const struct orc_grid *grid; /* non-NULL: phi and grad phi come from this
+                                    gridded field (isolated fields only) */
 } orc_field;
+
+/* ---- gridded field (Sec. 3.3 grid path, App. B interpolation) ---------- */
+/* phi and grad phi on the nodes x = lo + h (i1, i2, i3), i = 0..n-1, stored
+ * [f][i1][i2][i3] with f = (phi, dphi/dx1, dphi/dx2, dphi/dx3) and i3
+ * fastest; y2 holds the natural-spline second derivatives of every line
+ * along x3 in index units (App. B: computed once per mass distribution). */
+typedef struct orc_grid {
+    int n;
+    double lo[3];
+    double h;
+    int n_int;          /* App. B: n_int nodes on either side per dimension */
+    const double *val;  /* 4 n^3 */
+    const double *y2;   /* 4 n^3 */
+} orc_grid;
+
+/* second derivatives of the natural cubic spline through y[0..n-1] (unit
+ * spacing, y'' = 0 at both ends); y and y2 strided by `stride` */
+void orc_spline_y2(int n, const double *y, int64_t stride, double *y2);
+
+/* y2 of every x3 line of val (4 n^3) */
+void orc_grid_y2(int n, const double *val, double *y2);
+
+/* App. B evaluation at r: out = (phi, grad phi); zero outside the node range */
+void orc_grid_eval(const orc_grid *g, const double r[3], double out[4]);
 
 /* phi and grad phi (Eqs. psi, derivs, phicotophys, as a Plummer-softened
  * direct sum) at n points; rep[i] selects the replica for point i (ignored

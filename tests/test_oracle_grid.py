@@ -1,0 +1,154 @@
+"""Pins of the oracle's grid path (Sec. 3.3 CIC + zero-padded FFT convolution,
+App. B spline interpolation) against definitions, library routines and
+special cases that do not share its code."""
+import numpy as np
+import pytest
+
+import oracle
+import oracle.grid as G
+
+
+def test_cic_special_cases_and_moments():
+    lo, h, n = np.zeros(3), 0.5, 6
+    # a particle on a node puts all its mass there
+    M = G.cic([[1.0, 1.5, 2.0]], [3.0], lo, h, n)
+    assert M[2, 3, 4] == 3.0 and M.sum() == 3.0
+    # a particle at a cell centre splits its mass equally over the 8 corners
+    M = G.cic([[1.25, 1.75, 0.25]], [8.0], lo, h, n)
+    assert np.allclose(M[2:4, 3:5, 0:2], 1.0) and M.sum() == pytest.approx(8.0)
+    # CIC keeps the mass and the centre of mass of particles inside the grid
+    g = np.random.default_rng(3)
+    pos = g.uniform(0.0, (n - 1) * h, (200, 3))
+    m = g.uniform(1.0, 2.0, 200)
+    M = G.cic(pos, m, lo, h, n)
+    assert M.sum() == pytest.approx(m.sum(), rel=1e-14)
+    idx = np.stack(np.meshgrid(*[np.arange(n) * h] * 3, indexing="ij"), -1)
+    com = np.einsum("ijk,ijkc->c", M, idx) / M.sum()
+    assert np.allclose(com, (m[:, None] * pos).sum(0) / m.sum(), rtol=1e-13)
+
+
+def test_cic_drops_mass_outside_the_grid():
+    M = G.cic([[-0.75, 0.2, 0.2], [0.2, 0.2, 0.2]], [5.0, 1.0], np.zeros(3), 0.5, 4)
+    assert M.sum() == pytest.approx(1.0)
+
+
+@pytest.mark.parametrize("eps", [0.0, 0.07])
+def test_fft_convolution_equals_the_node_double_sum(eps):
+    g = np.random.default_rng(7)
+    n, h = 5, 0.3
+    M = g.uniform(-1.0, 2.0, (n, n, n)) * 1e11
+    fft = G.convolve(M, h, eps)
+    ref = G.direct_node_sum(M, h, eps)
+    assert np.max(np.abs(fft - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_single_mass_on_a_node_gives_the_plummer_field_on_the_nodes():
+    n, h, eps = 8, 0.25, 0.1
+    M = np.zeros((n, n, n))
+    M[3, 4, 2] = 2e12
+    val = G.convolve(M, h, eps)
+    mu = oracle.mu_G()
+    i = np.array([6, 1, 7])
+    d = (i - np.array([3, 4, 2])) * h
+    r2 = d @ d + eps * eps
+    assert val[0][tuple(i)] == pytest.approx(-mu * 2e12 / np.sqrt(r2), rel=1e-12)
+    assert np.allclose(val[1:, i[0], i[1], i[2]], mu * 2e12 * d / r2 ** 1.5, rtol=1e-11)
+
+
+def test_spline_second_derivatives_match_scipy_natural_spline():
+    interp = pytest.importorskip("scipy.interpolate")
+    g = np.random.default_rng(11)
+    for n in (2, 3, 4, 9, 40):
+        y = g.normal(size=n)
+        ref = interp.CubicSpline(np.arange(n), y, bc_type="natural")(np.arange(n), 2)
+        assert np.allclose(G.spline_y2(y), ref, atol=1e-12)
+
+
+def _grid_from(fun, n=12, h=0.2, lo=(1.0, -1.0, 0.5), n_int=2):
+    lo = np.asarray(lo, np.float64)
+    x = [lo[d] + h * np.arange(n) for d in range(3)]
+    X = np.meshgrid(*x, indexing="ij")
+    val = np.stack([fun(*X, f) for f in range(4)])
+    return G.GridField(None, None, 0.0, lo, h, n, n_int=n_int, val=val), lo, h, n
+
+
+def test_grid_eval_reproduces_nodes_and_linear_fields():
+    gf, lo, h, n = _grid_from(lambda x, y, z, f: 1.0 + (f + 1) * x - 2.0 * y + 0.5 * f * z)
+    g = np.random.default_rng(5)
+    nodes = lo + h * g.integers(0, n, (20, 3))
+    pts = lo + h * g.uniform(0, n - 1, (50, 3))
+    for p in (nodes, pts):
+        out = gf.eval(p)
+        want = np.stack([1.0 + (f + 1) * p[:, 0] - 2.0 * p[:, 1] + 0.5 * f * p[:, 2] for f in range(4)], 1)
+        assert np.allclose(out, want, atol=1e-12)
+
+
+def test_grid_eval_along_x3_is_the_global_natural_spline():
+    interp = pytest.importorskip("scipy.interpolate")
+    gf, lo, h, n = _grid_from(lambda x, y, z, f: np.sin(3.0 * z + f) + 0.0 * x)
+    zs = lo[2] + h * np.arange(n)
+    p = np.array([[lo[0] + 0.37, lo[1] + 0.91, z] for z in np.linspace(lo[2], zs[-1], 33)])
+    out = gf.eval(p)
+    for f in range(4):
+        cs = interp.CubicSpline(np.arange(n), np.sin(3.0 * zs + f), bc_type="natural")
+        assert np.allclose(out[:, f], cs((p[:, 2] - lo[2]) / h), atol=1e-12)
+
+
+@pytest.mark.parametrize("n_int", [1, 2, 3])
+def test_grid_eval_along_x1_is_the_local_natural_spline(n_int):
+    interp = pytest.importorskip("scipy.interpolate")
+    gf, lo, h, n = _grid_from(lambda x, y, z, f: np.cos(2.0 * x - f), n_int=n_int)
+    xs = lo[0] + h * np.arange(n)
+    for u in (0.0, 0.3, 2.5, 5.99, 9.2, n - 1.0):
+        p = np.array([[lo[0] + u * h, lo[1] + 0.33, lo[2] + 1.1]])
+        s = min(max(int(np.floor(u)) - n_int + 1, 0), n - 2 * n_int)
+        win = np.arange(s, s + 2 * n_int)
+        out = gf.eval(p)[0]
+        for f in range(4):
+            cs = interp.CubicSpline(win, np.cos(2.0 * xs[win] - f), bc_type="natural")
+            assert out[f] == pytest.approx(float(cs(u)), abs=1e-12)
+
+
+def test_grid_eval_is_zero_outside_the_nodes():
+    gf, lo, h, n = _grid_from(lambda x, y, z, f: 1.0 + x * 0.0)
+    out = gf.eval([[lo[0] - 1e-9, lo[1] + 0.5, lo[2] + 0.5], [lo[0] + 0.5, lo[1] + 0.5, lo[2] + (n - 1) * h + 1e-9]])
+    assert np.all(out == 0.0)
+
+
+def test_grid_field_converges_to_the_direct_sum():
+    # a Plummer-softened particle: the grid field between the nodes approaches
+    # the direct sum as the node spacing shrinks (App. B, Figs. nfwtests2)
+    p0 = np.array([[0.5, 0.5, 0.5]])
+    m0 = np.array([1e12])
+    eps = 0.08
+    pts = np.array([[0.71, 0.43, 0.62], [0.35, 0.58, 0.33], [0.52, 0.27, 0.55]])
+    ref = oracle.potential(oracle.MassField(p0, m0, eps), pts)
+    errs = []
+    for n in (11, 21, 41):
+        h = 1.0 / (n - 1)
+        gf = G.GridField(p0, m0, eps, np.zeros(3), h, n, n_int=2)
+        errs.append(np.max(np.abs(gf.eval(pts) - ref) / np.abs(ref).max(axis=0)))
+    assert errs[2] < errs[1] < errs[0]
+    assert errs[2] < 2e-3
+
+
+def test_grid_trace_matches_direct_sum_for_a_smooth_lens(cosmo):
+    # the whole trace through a gridded Plummer lens tends to the direct-sum trace
+    import inputs
+    cfg = inputs.config_c1(n_bundles=4, x_lo=2.0, x_hi=4.0, n_steps=400, extra_images=False)
+    chi_l = cfg["chi_l"]
+    eps = 3.0 * cfg["theta_E"] * chi_l
+    pos, mass = cfg["pos"], cfg["mass"]
+    kw = dict(n_ring=4, theta_r=cfg["theta_r"], schedule=1, n_steps=400, lens_chi=chi_l, asinh_s=eps)
+    ref = oracle.trace(cosmo, oracle.MassField(pos, mass, eps), cfg["z_s"], cfg["theta"], **kw)
+    n = 41
+    half = 12.0 * eps
+    h = 2.0 * half / (n - 1)
+    lo = pos[0] - half
+    gf = G.GridField(pos, mass, eps, lo, h, n, n_int=2)
+    got = oracle.trace(cosmo, gf.field(), cfg["z_s"], cfg["theta"], **kw)
+    assert np.all(got.flags == 0)
+    # the grid holds the lens only within +-12 eps: the deflection outside is
+    # missing, so compare the magnification, which is set near the lens
+    assert np.max(np.abs(got.mu / ref.mu - 1)) < 2e-2
+    assert np.max(np.abs(got.mu - 1) / np.abs(ref.mu - 1)) > 0.5
