@@ -34,7 +34,8 @@ FLOPS_PER_INTERACTION = 20  # direct N-body convention (3 sub, 6 fma/mul for r^2
 N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 FP32_PEAK = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6  # FLOP/s at the maximum SM clock
 HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
-KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2"}
+KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2",
+                5: "k_force_bundle2x"}
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-sum launch on this
 # workload, per (kernel, threads per block, splits), from the ncu captures
 # summarised under profiles/
@@ -70,7 +71,7 @@ def run_cones(args):
 
     import paper_1110_4894_gb300 as P
     cfg, name = cones_workload(args.cones, args.cone_steps)
-    ctx = P.Context(0, precision=P.MIXED, autotune=1)
+    ctx = P.Context(0, precision=P.MIXED, autotune=1, variant=args.variant)
     ctx.set_cosmology(*cfg["cosmo"])
     cones = []
     npart = 0
@@ -122,6 +123,96 @@ def run_cones(args):
                                         "speedup_of_mixed_batched": value / (i64 / t64),
                                         "max_rel_dmu_vs_mixed": dmu},
            "clocks": clocks}
+    print(json.dumps(out))
+    return 0
+
+
+def run_grid(args):
+    """The grid path (Sec. 3.3, App. B) on the NFW workload: the halo's
+    particles on an n^3 node grid spanning +-2.2 r200 (comoving), App. B
+    interpolation with n_int = 2.  One step = one full trace of every bundle
+    (rt3d_trace_device + histogram).  Reported beside it: the grid build time,
+    and |mu_grid / mu_direct - 1| against the direct-sum trace of the same
+    bundles (the grid's smoothing, not a parity figure)."""
+    import torch
+
+    import paper_1110_4894_gb300 as P
+    dev = torch.device("cuda", 0)
+    cfg, name = workload(full=not args.small)
+    n = args.grid_n
+    r200c = cfg["info"]["r200_phys"] * (1 + cfg["z_l"])
+    half = 2.2 * r200c
+    h = 2 * half / (n - 1)
+    lo = [-half, -half, cfg["chi_l"] - half]
+    kw = trace_kw(cfg)
+    nb = cfg["theta"].shape[0]
+    ctx = P.Context(0, precision=P.MIXED, time_kernels=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    t0 = time.perf_counter()
+    ctx.load_grid(0, cfg["pos"], cfg["mass"], cfg["soft"], lo, h, n, n_int=2)
+    build_s = time.perf_counter() - t0
+    d_theta = torch.from_numpy(np.ascontiguousarray(cfg["theta"])).to(dev)
+    d_bout = torch.zeros(nb * 6, dtype=torch.float64, device=dev)
+    d_counts = torch.zeros(HIST["bins"], dtype=torch.int64, device=dev)
+    d_wfix = torch.zeros(HIST["bins"], dtype=torch.int64, device=dev)
+    d_scal = torch.zeros(8, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def step():
+        ctx.trace_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), d_bout.data_ptr(), **kw)
+        ctx.histogram_device(sp, nb, d_bout.data_ptr(), d_counts.data_ptr(), d_wfix.data_ptr(), d_scal.data_ptr(),
+                             **HIST)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    eval_ms, eval_launches, evals, launches = 0.0, 0, 0.0, 0
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            flush.zero_()
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            st = ctx.stats()
+            eval_ms += st["force_ms"]
+            eval_launches += st["force_launches"]
+            evals += st["interactions"]  # ray-stage field evaluations on the grid path
+            launches += st["launches"] + 2
+    clocks = clk.summary()
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    mu_grid = d_bout.view(nb, 6)[:, 0].cpu().numpy()
+    # the direct sum on the same bundles, for the grid's smoothing error
+    cd = P.Context(0, precision=P.MIXED, autotune=1)
+    cd.set_cosmology(*cfg["cosmo"])
+    cd.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"])
+    mu_dir = cd.trace(0, cfg["z_s"], cfg["theta"], **kw)["mu"]
+    dmu = np.abs(mu_grid / mu_dir - 1)
+    per_launch_s = eval_ms / 1e3 / max(1, eval_launches)
+    w = 4  # 2 n_int nodes per axis
+    bytes_per_launch = nb * (1 + cfg["n_ring"]) * 4 * w * w * 4 * 8  # (val, y2) x (k, k+1) per x3 spline
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    out = {"metric": "ray bundles/s (grid path)", "value": nb * args.steps / dev_s, "unit": "bundles/s",
+           "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": name + "_grid%d" % n, "grid_n": n, "node_spacing_mpc": h, "n_int": 2,
+                      "bundles": nb, "rk4_steps": cfg["n_steps"], "l2": "256 MB buffer written between timed steps"},
+           "grid_build_s": build_s,
+           "field_evals_per_s": evals / dev_s,
+           "roofline": {"bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": bytes_per_launch / per_launch_s / 1e9 / hbm, "traffic": None,
+                        "kernel": "k_grid_eval", "avg_launch_ms": per_launch_s * 1e3,
+                        "note": "algorithmic bytes = spline reads along x3 per ray and field; most hit L1/L2"},
+           "grid_vs_direct_sum": {"median_abs_dmu_over_mu": float(np.median(dmu)),
+                                  "max_abs_dmu_over_mu": float(np.max(dmu))},
+           "clocks": clocks, "gpu_launches": int(launches)}
     print(json.dumps(out))
     return 0
 
@@ -251,7 +342,7 @@ def run_ours(args):
     nr = 1 + cfg["n_ring"]
     npart = len(cfg["mass"])
 
-    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=1)
+    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=1, variant=args.variant)
     ctx.set_cosmology(*cfg["cosmo"])
     ctx.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"])
     d_theta = torch.from_numpy(np.ascontiguousarray(cfg["theta"])).to(dev)
@@ -370,16 +461,21 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
-    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones"])
+    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid"])
+    ap.add_argument("--grid-n", type=int, default=256, help="nodes per side of the grid workload")
     ap.add_argument("--cones", type=int, default=512)
     ap.add_argument("--cone-steps", type=int, default=8)
     ap.add_argument("--fp64-cones", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--variant", type=int, default=0,
+                    help="pair-sum kernel (0: the autotuner picks among all; 3, 4, 5: that kernel's shapes only)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
     if args.workload == "cones":
         return run_cones(args)
+    if args.workload == "grid":
+        return run_grid(args)
     return run_ours(args)
 
 

@@ -74,9 +74,11 @@ typedef struct {
     int autotune;          /* 1: time candidate launch shapes once per size bucket */
     double watchdog_s;     /* limit for the persistent kernel's waits; 0 = 10 s */
     int time_kernels;      /* 1: bracket every pair-sum launch with CUDA events (stats.force_ms) */
-    int variant;           /* pair-sum kernel: 0 = automatic (bundle-centric FP32x2 for traces),
+    int variant;           /* pair-sum kernel: 0 = automatic (bundle-centric FP32x2 for traces:
+                              5 for rings of 4, 3 otherwise; with autotune, the fastest of 3, 4, 5),
                               1 = scalar FP32, 2 = packed FP32x2 per ray, 3 = one bundle per thread,
-                              4 = two bundles per thread (rings of 4) */
+                              4 = two bundles per thread (rings of 4), 5 = as 4 with the ring
+                              separations expanded about the central ray */
 } rt3d_options;
 
 /* Mass distribution layout.
@@ -135,7 +137,8 @@ typedef struct {
     int64_t force_launches;
     int steps;            /* RK4 steps issued */
     int rays_per_thread, threads_per_block, splits; /* force launch shape used */
-    int variant;          /* pair-sum kernel used: 0 packed, 1 scalar, 2 FP64, 3 bundle, 4 two bundles per thread */
+    int variant;          /* pair-sum kernel used: 0 packed, 1 scalar, 2 FP64, 3 bundle, 4 two bundles
+                             per thread, 5 two bundles per thread, expanded separations */
 } rt3d_stats;
 
 /* One light cone of a batch (Sec. 5): its field, source redshift, bundles and steps. */
@@ -164,6 +167,41 @@ int rt3d_set_cosmology(rt3d_ctx *ctx, double omega_m, double omega_l, double h);
 int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos,
                         const double *mass, const double *soft, int soft_per_particle,
                         const rt3d_volume *vol);
+
+/* ---- grid path (Sec. 3.3 and App. B) --------------------------------------
+ * The paper's own force path: the particle masses are assigned to a regular
+ * node grid by cloud-in-cell, phi and grad phi are found on the nodes by a
+ * zero-padded FFT convolution (no periodic images) with the kernels
+ *   K_phi(d) = -mu_G (|d|^2 + soft^2)^(-1/2),  K_g(d) = mu_G d (|d|^2 + soft^2)^(-3/2)
+ * (soft = 0: the d = 0 term is zero), and at every RK4 stage each ray reads
+ * the field by App. B's interpolation: along x3 with the natural cubic spline
+ * of the whole node line (second derivatives computed once at load), then
+ * along x1 and x2 with natural cubic splines through the 2 n_int nodes
+ * around the ray.  Outside the node range the field is zero.  Mass on nodes
+ * outside the grid is dropped. */
+typedef struct {
+    int n;              /* nodes per side, 2 n_int .. 1024 */
+    double lo[3];       /* position of node (0, 0, 0), comoving Mpc */
+    double h;           /* node spacing, comoving Mpc (> 0) */
+    int n_int;          /* interpolation nodes on either side, 1 .. 4 */
+    int mean_subtract;  /* 1: subtract the mean node mass before the convolution */
+} rt3d_grid_opts;
+
+/* Build a gridded field in slot field_id from n particles (pos n*3, mass n,
+ * one softening length soft for the kernels).  The library copies the
+ * inputs; the grid (8 n^3 doubles: node values and x3 spline second
+ * derivatives) stays on the device until the slot is reloaded or the context
+ * destroyed.  The build needs (2n)^3 doubles and two (2n)^2 (n+1) complex
+ * FFT buffers of temporary device memory.  Traces, rt3d_potential and
+ * rt3d_grid_nodes on the slot then use the grid; rt3d_trace_batch rejects
+ * grid slots (RT3D_ENOTIMPL).  Errors: RT3D_EINVAL for a bad option or a
+ * non-finite input, RT3D_ENOMEM, RT3D_ECUDA (including a cuFFT failure). */
+int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
+                   double soft, const rt3d_grid_opts *g);
+
+/* Copy a grid slot's node values to out (host, 4 n^3 doubles, [f][i1][i2][i3]
+ * with i3 fastest, f = phi, dphi/dx1, dphi/dx2, dphi/dx3). */
+int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out);
 
 /* Trace n_bundles bundles with centres theta (n_bundles*2, tangent-plane
  * angles: direction (theta_x, theta_y, 1)) from the observer to the plane

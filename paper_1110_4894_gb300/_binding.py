@@ -62,6 +62,11 @@ class Stats(C.Structure):
                 ("variant", C.c_int)]
 
 
+class GridOpts(C.Structure):
+    _fields_ = [("n", C.c_int), ("lo", C.c_double * 3), ("h", C.c_double), ("n_int", C.c_int),
+                ("mean_subtract", C.c_int)]
+
+
 class Cone(C.Structure):
     _fields_ = [("field_id", C.c_int), ("z_s", C.c_double), ("n_bundles", C.c_int64), ("theta", _dp),
                 ("n_steps", C.c_int)]
@@ -100,6 +105,8 @@ def lib(build=True):
         "rt3d_histogram": ([vp, C.c_int64, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)], C.c_int),
         "rt3d_histogram_device": ([vp, vp, C.c_int64, vp, C.POINTER(HistOpts), vp, vp, vp], C.c_int),
         "rt3d_potential": ([vp, C.c_int, C.c_int64, _dp, _ip, _dp], C.c_int),
+        "rt3d_load_grid": ([vp, C.c_int, C.c_int64, _dp, _dp, C.c_double, C.POINTER(GridOpts)], C.c_int),
+        "rt3d_grid_nodes": ([vp, C.c_int, _dp], C.c_int),
         "rt3d_schedule": ([vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp], C.c_int),
         "rt3d_get_stats": ([vp, C.POINTER(Stats)], C.c_int),
         "rt3d_status_string": ([C.c_int], C.c_char_p),
@@ -164,6 +171,23 @@ class Context:
             vol = Volume(1, float(box_length), rot.shape[0], _p(rot, C.c_int32), _p(shift), int(bool(mean_subtract)))
         self._check(self.L.rt3d_load_particles(self.h, int(field_id), n, _p(pos), _p(mass), _p(soft), int(pp),
                                                C.byref(vol) if vol is not None else None))
+
+    def load_grid(self, field_id, pos, mass, soft, lo, h, n, n_int=2, mean_subtract=False):
+        """rt3d_load_grid: the grid path's field (CIC, zero-padded FFT, App. B splines)."""
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        npart = pos.shape[0]
+        mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, np.float64), (npart,)))
+        g = GridOpts(int(n), (C.c_double * 3)(*[float(v) for v in lo]), float(h), int(n_int), int(bool(mean_subtract)))
+        self._grid_n = getattr(self, "_grid_n", {})
+        self._grid_n[int(field_id)] = int(n)
+        self._check(self.L.rt3d_load_grid(self.h, int(field_id), npart, _p(pos), _p(mass), float(soft), C.byref(g)))
+
+    def grid_nodes(self, field_id):
+        """rt3d_grid_nodes: phi and grad phi on the nodes, (4, n, n, n)."""
+        n = self._grid_n[int(field_id)]
+        out = np.zeros((4, n, n, n))
+        self._check(self.L.rt3d_grid_nodes(self.h, int(field_id), _p(out)))
+        return out
 
     @staticmethod
     def bundle_opts(n_ring=4, theta_r=1e-6, phase=0.0, schedule=SCHED_UNIFORM, n_steps=1000, lens_chi=0.0,

@@ -1,7 +1,8 @@
 """Build librt3d.so (the sm_103a CUDA library behind include/rt3d.h) in-tree.
 
 Each .cu is compiled by nvcc in parallel for sm_103a only, then linked into
-one shared library with the CUDA runtime linked statically.
+one shared library with the CUDA runtime linked statically and cuFFT (the
+grid path's FFTs) dynamically from the toolkit.
 """
 import concurrent.futures as cf
 import os
@@ -23,6 +24,20 @@ def nvcc():
         if c and (os.path.isabs(c) and os.path.exists(c) or not os.path.isabs(c)):
             return c
     return "nvcc"
+
+
+def cuda_libdir():
+    """the toolkit's library directory (cuFFT is linked dynamically from it)"""
+    import shutil
+    exe = nvcc()
+    path = exe if os.path.isabs(exe) else shutil.which(exe)
+    if not path:
+        return None
+    root = os.path.dirname(os.path.dirname(os.path.realpath(path)))
+    for d in ("lib64", "lib"):
+        if os.path.exists(os.path.join(root, d, "libcufft.so")):
+            return os.path.join(root, d)
+    return None
 
 
 def sources():
@@ -66,7 +81,10 @@ def build(force=False, verbose=False):
             if log:
                 print(log)
     tmp = OUT + ".tmp.%d" % os.getpid()
-    cmd = [nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in res] + ["-lcudart_static", "-lrt", "-ldl", "-lpthread"]
+    libdir = cuda_libdir()
+    cmd = ([nvcc()] + ARCH + ["-shared", "-o", tmp] + [o for o, _ in res] +
+           ["-lcudart_static", "-lcufft", "-lrt", "-ldl", "-lpthread"] +
+           (["-L", libdir, "-Xlinker", "-rpath", "-Xlinker", libdir] if libdir else []))
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError("link failed:\n%s\n%s" % (r.stdout, r.stderr))

@@ -20,10 +20,14 @@ cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t
 cudaError_t dispatch_packed(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 cudaError_t dispatch_bundle(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 cudaError_t dispatch_bundle2(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
+cudaError_t dispatch_bundle2x(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 struct BatchArgs;
 
 // rays covered by one block of the pair-sum kernel of shape sh
-inline int64_t rays_per_block(const ForceShape &sh) { return (int64_t)sh.R * sh.NT * (sh.variant == 4 ? 2 : 1); }
+inline int64_t rays_per_block(const ForceShape &sh)
+{
+    return (int64_t)sh.R * sh.NT * ((sh.variant == 4 || sh.variant == 5) ? 2 : 1);
+}
 
 // ---------------------------------------------------------------------------
 // particle staging (S2): FP64 input -> integer grid + scaled masses
@@ -121,6 +125,8 @@ struct FieldSlot {
     double *d_m64 = nullptr, *d_eps2_64 = nullptr;
     int *d_rot = nullptr, *d_shift = nullptr;
     int64_t n = 0;
+    bool is_grid = false;  // grid path: phi and grad phi interpolated from nodes
+    GridDev gd;
 };
 
 struct rt3d_ctx {
@@ -212,6 +218,7 @@ static void free_field(FieldSlot &s)
     cudaFree(s.d_eps2_64);
     cudaFree(s.d_rot);
     cudaFree(s.d_shift);
+    grid_free(s.gd);
     s = FieldSlot{};
 }
 
@@ -497,13 +504,14 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
         sh.R = 2;
         sh.NT = 128;
     } else if ((ctx->opt.variant == 0 || ctx->opt.variant >= 3) && (group == 5 || group == 9)) {
-        // bundle-centric: two bundles per thread for rings of 4 (variant 4),
-        // one per thread otherwise (variant 3)
-        sh.variant = (group == 5 && ctx->opt.variant != 3) ? 4 : 3;
+        // bundle-centric: two bundles per thread for rings of 4 (variant 5,
+        // the expanded separations, or 4), one per thread otherwise (3)
+        sh.variant = group == 5 ? (ctx->opt.variant == 3 || ctx->opt.variant == 4 ? ctx->opt.variant : 5) : 3;
         sh.umass = f.uniform_mass ? 1 : 0;
         sh.R = group;
-        sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : (sh.variant == 4 ? 64 : 128);
-        if (sh.variant == 4 && sh.NT > 128) sh.NT = 128;
+        const bool two = sh.variant == 4 || sh.variant == 5;
+        sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : (two ? 64 : 128);
+        if (two && sh.NT > 128) sh.NT = 128;
     } else {
         sh.variant = ctx->opt.variant == 1 ? 1 : 0;
         sh.umass = (sh.variant == 0 && f.uniform_mass) ? 1 : 0;
@@ -557,6 +565,7 @@ static cudaError_t run_force(rt3d_ctx *ctx, const DevField &f, const double *px,
     if (sh.variant == 1) return dispatch_mixed(A, sh, st);
     if (sh.variant == 3) return dispatch_bundle(A, sh, sh.umass != 0, st);
     if (sh.variant == 4) return dispatch_bundle2(A, sh, sh.umass != 0, st);
+    if (sh.variant == 5) return dispatch_bundle2x(A, sh, sh.umass != 0, st);
     return dispatch_packed(A, sh, sh.umass != 0, st);
 }
 
@@ -609,12 +618,15 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
     const int rn64[][2] = {{2, 128}, {1, 128}};
     // bundle shapes: {variant, bundles per block}
-    const int rnb[][3] = {{3, group, 128}, {3, group, 64}, {3, group, 256}, {4, group, 64}, {4, group, 128}};
-    const bool bundles = base.variant == 3 || base.variant == 4;
-    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 5 : 3) : 4);
+    const int rnb[][3] = {{3, group, 128}, {3, group, 64}, {3, group, 256}, {4, group, 64},
+                          {4, group, 128}, {5, group, 64}, {5, group, 128}};
+    const bool bundles = base.variant >= 3;
+    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 7 : 3) : 4);
     for (int c = 0; c < nrn; ++c)
         for (int w : {2, 3, 5, 8}) {
             ForceShape s = base;
+            // a requested bundle kernel is tuned over its own shapes only
+            if (bundles && ctx->opt.variant >= 3 && rnb[c][0] != base.variant) continue;
             if (bundles) {
                 s.variant = rnb[c][0];
                 s.R = rnb[c][1];
@@ -627,6 +639,10 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
             cand.push_back(with_splits(s, n, fs.n, w));
             waves.push_back(w);
         }
+    if (cand.empty()) {
+        out = base;
+        return RT3D_OK;
+    }
     size_t need = 0;
     for (auto &s : cand) need = std::max(need, partials_bytes(s, n, fp64));
     CK(grow(*(char **)&ctx->scr.partials, ctx->scr.partials_bytes, need));
@@ -716,17 +732,30 @@ static RayState make_state(rt3d_ctx *ctx, int64_t n_b, int nr)
 }
 
 // enqueue one full trace on st: schedule, init, RK4 stages, reduce
+// force shape of a grid-path trace: one "split" of interpolated values, no
+// mass factor (variant 6 names the grid path in the statistics)
+static ForceShape grid_shape()
+{
+    ForceShape sh;
+    sh.R = 1;
+    sh.NT = 128;
+    sh.splits = 1;
+    sh.variant = 6;
+    sh.umass = 0;
+    return sh;
+}
+
 static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t n_b, const double *d_theta,
                          const rt3d_bundle_opts *b, double *d_bout, double *d_rout, cudaStream_t st, bool timed)
 {
     const bool fp64 = ctx->opt.precision == RT3D_FP64;
     const int nr = 1 + b->n_ring;
     const int64_t n_rays = n_b * nr;
-    ForceShape sh = choose_shape(ctx, fs.df, n_rays, fp64, nr);
+    ForceShape sh = fs.is_grid ? grid_shape() : choose_shape(ctx, fs.df, n_rays, fp64, nr);
     int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
     if (rc) return rc;
     RayState rs = make_state(ctx, n_b, nr);
-    bool tune_pending = ctx->opt.autotune != 0;
+    bool tune_pending = ctx->opt.autotune != 0 && !fs.is_grid;
     TraceParams tp;
     tp.cosmo = ctx->cosmo;
     tp.chi_s = 0.0;
@@ -760,8 +789,12 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
                 e1 = timing_event(ctx);
                 if (e0) CK(cudaEventRecord(e0, st));
             }
-            CK(run_force(ctx, fs.df, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, rs.rep + (g & 1) * n_b,
-                         nr, n_rays, sh, fp64, s.partials, gate, st));
+            if (fs.is_grid)
+                CK(launch_grid_eval(fs.gd, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, n_rays,
+                                    fp64 ? 1 : 0, s.partials, gate, st));
+            else
+                CK(run_force(ctx, fs.df, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays,
+                             rs.rep + (g & 1) * n_b, nr, n_rays, sh, fp64, s.partials, gate, st));
             if (e1) CK(cudaEventRecord(e1, st));
             CK(launch_stage(tp, fs.df, rs, sh, fp64, s.partials, s.dlam, s.misc, step, stage, s.counters, st));
             launches += 2;
@@ -777,7 +810,8 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     ctx->stats.threads_per_block = sh.NT;
     ctx->stats.splits = sh.splits;
     ctx->stats.variant = sh.variant;
-    ctx->last_npart = (double)fs.n;
+    // grid path: one field evaluation per ray and stage counts as one
+    ctx->last_npart = fs.is_grid ? 1.0 : (double)fs.n;
     ctx->stats_pending = true;
     return RT3D_OK;
 }
@@ -1099,6 +1133,8 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
         const rt3d_cone &k = cones[c];
         if (k.field_id < 0 || k.field_id >= RT3D_MAX_FIELDS || !ctx->fields[k.field_id].loaded)
             return fail(ctx, RT3D_ENOFIELD, "cone field not loaded");
+        if (ctx->fields[k.field_id].is_grid)
+            return fail(ctx, RT3D_ENOTIMPL, "the batched trace takes particle fields, not grid fields");
         if (!(k.z_s > 0.0) || k.z_s > 20.0 || k.n_bundles < 1 || !k.theta || k.n_steps < 1 || k.n_steps > 10000000)
             return fail(ctx, RT3D_EINVAL, "cone needs z_s in (0, 20], n_bundles >= 1, theta, n_steps >= 1");
         if (!outs[c].mu) return fail(ctx, RT3D_EINVAL, "null mu output");
@@ -1273,6 +1309,64 @@ extern "C" int rt3d_histogram_device(rt3d_ctx *ctx, void *stream, int64_t n, con
     return RT3D_OK;
 }
 
+extern "C" int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
+                              double soft, const rt3d_grid_opts *g)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS) return fail(ctx, RT3D_EINVAL, "field id out of range");
+    if (!g) return fail(ctx, RT3D_EINVAL, "null grid options");
+    if (g->n_int < 1 || g->n_int > 4) return fail(ctx, RT3D_EINVAL, "n_int must be 1..4");
+    if (g->n < 2 * g->n_int || g->n > 1024) return fail(ctx, RT3D_EINVAL, "grid n must be in [2 n_int, 1024]");
+    if (!(g->h > 0.0) || !isfinite(g->h) || !isfinite(g->lo[0]) || !isfinite(g->lo[1]) || !isfinite(g->lo[2]))
+        return fail(ctx, RT3D_EINVAL, "grid needs h > 0 and a finite origin");
+    if (!(soft >= 0.0) || !isfinite(soft)) return fail(ctx, RT3D_EINVAL, "softening must be >= 0");
+    if (n < 0 || (n > 0 && (!pos || !mass))) return fail(ctx, RT3D_EINVAL, "null particle arrays");
+    for (int64_t i = 0; i < n; ++i) {
+        if (!isfinite(pos[3 * i]) || !isfinite(pos[3 * i + 1]) || !isfinite(pos[3 * i + 2]))
+            return fail(ctx, RT3D_EINVAL, "non-finite particle position");
+        if (!(mass[i] > 0.0) || !isfinite(mass[i])) return fail(ctx, RT3D_EINVAL, "particle masses must be > 0");
+    }
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    FieldSlot &fs = ctx->fields[field_id];
+    free_field(fs);
+    fs.gd.n = g->n;
+    fs.gd.n_int = g->n_int;
+    fs.gd.h = g->h;
+    for (int d = 0; d < 3; ++d) fs.gd.lo[d] = g->lo[d];
+    int rc = grid_build(fs.gd, n, pos, mass, soft, g->mean_subtract ? 1 : 0, ctx->stream, ctx->err);
+    if (rc != RT3D_OK) {
+        free_field(fs);
+        return rc;
+    }
+    DevField &df = fs.df;
+    df = DevField{};
+    df.n = n;
+    df.n_rep = 1;
+    df.mscale_inv = 1.0;
+    df.delta = 1.0;
+    df.inv_delta = 1.0;
+    fs.n = n;
+    fs.is_grid = true;
+    fs.loaded = true;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS || !ctx->fields[field_id].loaded)
+        return fail(ctx, RT3D_ENOFIELD, "field not loaded");
+    const FieldSlot &fs = ctx->fields[field_id];
+    if (!fs.is_grid) return fail(ctx, RT3D_EINVAL, "not a grid field");
+    if (!out) return fail(ctx, RT3D_EINVAL, "null output");
+    CK(cudaSetDevice(ctx->device));
+    const size_t m = 4 * (size_t)fs.gd.n * fs.gd.n * fs.gd.n;
+    CK(cudaMemcpyAsync(out, fs.gd.val, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    return RT3D_OK;
+}
+
 extern "C" int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const double *pts, const int32_t *rep,
                               double *out)
 {
@@ -1300,8 +1394,12 @@ extern "C" int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const doub
     cudaStream_t st = ctx->stream;
     CK(cudaMemcpyAsync(d_pts, soa.data(), 3 * n * sizeof(double), cudaMemcpyHostToDevice, st));
     if (rep) CK(cudaMemcpyAsync(d_rep, rep, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
-    CK(run_force(ctx, fs.df, d_pts, d_pts + n, d_pts + 2 * n, d_rep, 1, n, sh, fp64, s.partials, nullptr, st));
-    CK(launch_stage_field(fs.df, sh, fp64, s.partials, d_pts, d_rep, n, d_out, st));
+    if (fs.is_grid) {
+        CK(launch_grid_eval(fs.gd, d_pts, d_pts + n, d_pts + 2 * n, n, 2, d_out, nullptr, st));
+    } else {
+        CK(run_force(ctx, fs.df, d_pts, d_pts + n, d_pts + 2 * n, d_rep, 1, n, sh, fp64, s.partials, nullptr, st));
+        CK(launch_stage_field(fs.df, sh, fp64, s.partials, d_pts, d_rep, n, d_out, st));
+    }
     CK(cudaMemcpyAsync(out, d_out, 4 * n * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return RT3D_OK;
@@ -1377,6 +1475,8 @@ extern "C" int rt3d_potential_device_noalloc(rt3d_ctx *ctx, void *stream, int fi
     if (!ctx) return RT3D_EINVAL;
     if (field_id < 0 || field_id >= RT3D_MAX_FIELDS || !ctx->fields[field_id].loaded)
         return fail(ctx, RT3D_ENOFIELD, "field not loaded");
+    if (ctx->fields[field_id].is_grid)
+        return fail(ctx, RT3D_ENOTIMPL, "the no-allocation entry point takes particle fields, not grid fields");
     if (n < 1 || !d_pts || !d_out) return fail(ctx, RT3D_EINVAL, "need n >= 1 points and device arrays");
     const int64_t max_points = (int64_t)(RT3D_NOALLOC_SCRATCH_BYTES / 32);
     if (n > max_points) return fail(ctx, RT3D_EINVAL, "rt3d_potential_device_noalloc: at most 1048576 points per call");

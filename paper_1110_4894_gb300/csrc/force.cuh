@@ -712,6 +712,241 @@ __global__ void __launch_bounds__(NT, 384 / NT) k_force_bundle2(ForceArgs A)
                                                     (float2 *)A.out, s_a, s_b, s_e, s_hl);
 }
 
+// Two bundles per thread with the ring separations expanded about the
+// central ray.  With d_c = p - r_c and e_k = r_c - r_k the ring ray's
+// separation is d_k = d_c + e_k, so
+//   |d_k|^2 + eps^2 = (|d_c|^2 + eps^2) + (2 e_k . d_c + |e_k|^2)
+//   sum m d_k / r_k^3 = sum m d_c / r_k^3 + e_k sum m / r_k^3.
+// The central ray's softened squared distance is shared by the ring, each
+// ring ray adds a three-FMA correction (its own rounding is one add), and the
+// ring gradient splits into a sum along d_c plus e_k times a positive scalar
+// sum S_k, combined once per block.  Per particle and pair of bundles this is
+// 56 f32x2 operations for 10 interactions (the unexpanded kernel: 60).
+// (Taking 1/r^2 from MUFU rcp instead of rsqrt^2 saves 5 more but was
+// measured 26 % slower: the MUFU pipe then limits.)
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>
+__device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const double *__restrict__ px,
+                                                   const double *__restrict__ py, const double *__restrict__ pz,
+                                                   const int *__restrict__ rep, int64_t n_b, int64_t n_rays,
+                                                   int64_t b0, int64_t p0, int64_t p1, int split,
+                                                   float2 *__restrict__ out, float4 *s_a, float4 *s_b, float *s_e,
+                                                   float2 *s_hl)
+{
+    constexpr int NR = NRING + 1;
+    constexpr int NQ = NR * 3 + NRING;  // compensated sums per bundle: G (3 per ray) and S (ring)
+    const int tid = threadIdx.x;
+    int64_t bb[2] = {b0 + tid, b0 + NT + tid};
+    bool valid[2] = {bb[0] < n_b, bb[1] < n_b};
+    __shared__ int s_rmin, s_rmax;
+    if (tid == 0) {
+        s_rmin = INT_MAX;
+        s_rmax = INT_MIN;
+    }
+    __syncthreads();
+    int myrep[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        myrep[h] = valid[h] ? (rep ? rep[bb[h]] : 0) : -1;
+        if (valid[h]) {
+            atomicMin(&s_rmin, myrep[h]);
+            atomicMax(&s_rmax, myrep[h]);
+        }
+    }
+    __syncthreads();
+    const int rmin = s_rmin, rmax = s_rmax;
+    // 2 e_k (exact doubling of the once-rounded FP64 offset) and |e_k|^2, paired (A, B)
+    float2 fx[NRING], fy[NRING], fz[NRING], ee[NRING];
+#pragma unroll
+    for (int k = 0; k < NRING; ++k) {
+        float v[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            if (valid[h]) {
+                const int64_t ic = bb[h] * NR, ik = ic + 1 + k;
+                v[h][0] = (float)(px[ic] - px[ik]);
+                v[h][1] = (float)(py[ic] - py[ik]);
+                v[h][2] = (float)(pz[ic] - pz[ik]);
+            }
+        fx[k] = make_float2(2.f * v[0][0], 2.f * v[1][0]);
+        fy[k] = make_float2(2.f * v[0][1], 2.f * v[1][1]);
+        fz[k] = make_float2(2.f * v[0][2], 2.f * v[1][2]);
+        ee[k] = make_float2(fmaf(v[0][0], v[0][0], fmaf(v[0][1], v[0][1], v[0][2] * v[0][2])),
+                            fmaf(v[1][0], v[1][0], fmaf(v[1][1], v[1][1], v[1][2] * v[1][2])));
+    }
+    // (hi, lo) per bundle pair: q = 3 g + o for G of ray g, 3 NR + k for S_k
+    float2 *s_hi = s_hl, *s_lo = s_hl + NQ * NT;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s_hi[q * NT + tid] = s_lo[q * NT + tid] = make_float2(0.f, 0.f);
+    float2 phi[NR];
+#pragma unroll
+    for (int g = 0; g < NR; ++g) phi[g] = make_float2(0.f, 0.f);
+    const float dlt = (float)f.delta;
+    const float2 E2u = make_float2(f.eps2u, f.eps2u);
+    const int64_t ia = b0 * NR;  // anchor: the block's first central ray
+    for (int j = rmin; j <= rmax; ++j) {
+        double o[3];
+        frame_origin(f, j, o);
+        const long long ax = __double2ll_rn((px[ia] - o[0]) * f.inv_delta);
+        const long long ay = __double2ll_rn((py[ia] - o[1]) * f.inv_delta);
+        const long long az = __double2ll_rn((pz[ia] - o[2]) * f.inv_delta);
+        float nc[2][3];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            nc[h][0] = nc[h][1] = nc[h][2] = -1e30f;  // far sentinel
+            if (valid[h] && myrep[h] == j) {
+                const int64_t ic = bb[h] * NR;
+                nc[h][0] = -(float)(((px[ic] - o[0]) * f.inv_delta - (double)ax) * f.delta);
+                nc[h][1] = -(float)(((py[ic] - o[1]) * f.inv_delta - (double)ay) * f.delta);
+                nc[h][2] = -(float)(((pz[ic] - o[2]) * f.inv_delta - (double)az) * f.delta);
+            }
+        }
+        const float2 NX = make_float2(nc[0][0], nc[1][0]), NY = make_float2(nc[0][1], nc[1][1]),
+                     NZ = make_float2(nc[0][2], nc[1][2]);
+        for (int64_t t0 = p0; t0 < p1; t0 += kTile) {
+            __syncthreads();
+            for (int q = tid; q < kTile; q += NT) {
+                const int64_t pi = t0 + q;
+                float x = 1e18f, y = 1e18f, z = 1e18f, m = 0.0f, e2 = 0.0f;
+                if (pi < p1) {
+                    const int4 pr = f.part[pi];
+                    long long qq[3] = {pr.x, pr.y, pr.z};
+                    if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
+                    x = (float)(qq[0] - ax) * dlt;
+                    y = (float)(qq[1] - ay) * dlt;
+                    z = (float)(qq[2] - az) * dlt;
+                    m = __int_as_float(pr.w);
+                    if (PEPS) e2 = f.eps2[pi];
+                }
+                s_a[q] = make_float4(x, x, y, y);
+                s_b[q] = make_float4(z, z, m, m);
+                if (PEPS) s_e[q] = e2;
+            }
+            __syncthreads();
+            for (int c0 = 0; c0 < kTile; c0 += kChunk2) {
+                float2 cx[NR], cy[NR], cz[NR], cs[NRING];
+#pragma unroll
+                for (int g = 0; g < NR; ++g) cx[g] = cy[g] = cz[g] = make_float2(0.f, 0.f);
+#pragma unroll
+                for (int k = 0; k < NRING; ++k) cs[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+                for (int jj = c0; jj < c0 + kChunk2; ++jj) {
+                    const float4 a = s_a[jj];
+                    const float4 b = s_b[jj];
+                    const float2 E2 = PEPS ? make_float2(s_e[jj], s_e[jj]) : E2u;
+                    const float2 M2 = make_float2(b.z, b.w);
+                    const float2 DX = __fadd2_rn(make_float2(a.x, a.y), NX);
+                    const float2 DY = __fadd2_rn(make_float2(a.z, a.w), NY);
+                    const float2 DZ = __fadd2_rn(make_float2(b.x, b.y), NZ);
+                    float2 R2 = __ffma2_rn(DZ, DZ, E2);
+                    R2 = __ffma2_rn(DY, DY, R2);
+                    R2 = __ffma2_rn(DX, DX, R2);
+#pragma unroll
+                    for (int g = 0; g < NR; ++g) {
+                        float2 s2 = R2;
+                        if (g > 0) {
+                            float2 t = __ffma2_rn(fz[g - 1], DZ, ee[g - 1]);
+                            t = __ffma2_rn(fy[g - 1], DY, t);
+                            t = __ffma2_rn(fx[g - 1], DX, t);
+                            s2 = __fadd2_rn(R2, t);
+                        }
+                        const float2 w = make_float2(rsqrt_mufu(s2.x), rsqrt_mufu(s2.y));
+                        const float2 u = __fmul2_rn(w, w);
+                        float2 m3;
+                        if (UMASS) {
+                            phi[g] = __fadd2_rn(phi[g], w);
+                            m3 = __fmul2_rn(w, u);
+                        } else {
+                            const float2 mw = __fmul2_rn(M2, w);
+                            phi[g] = __fadd2_rn(phi[g], mw);
+                            m3 = __fmul2_rn(mw, u);
+                        }
+                        if (g > 0) cs[g - 1] = __fadd2_rn(cs[g - 1], m3);
+                        cx[g] = __ffma2_rn(DX, m3, cx[g]);
+                        cy[g] = __ffma2_rn(DY, m3, cy[g]);
+                        cz[g] = __ffma2_rn(DZ, m3, cz[g]);
+                    }
+                }
+#pragma unroll
+                for (int g = 0; g < NR; ++g) {
+                    const float2 cc[3] = {cx[g], cy[g], cz[g]};
+#pragma unroll
+                    for (int oo = 0; oo < 3; ++oo) {
+                        const int q = (g * 3 + oo) * NT + tid;
+                        float2 hi = s_hi[q], lo = s_lo[q];
+                        two_sum2_into(hi, lo, cc[oo]);
+                        s_hi[q] = hi;
+                        s_lo[q] = lo;
+                    }
+                }
+#pragma unroll
+                for (int k = 0; k < NRING; ++k) {
+                    const int q = (NR * 3 + k) * NT + tid;
+                    float2 hi = s_hi[q], lo = s_lo[q];
+                    two_sum2_into(hi, lo, cs[k]);
+                    s_hi[q] = hi;
+                    s_lo[q] = lo;
+                }
+            }
+        }
+    }
+    // gradient of ring ray k: G_k + e_k S_k, as an FP32 (hi, lo) pair (the
+    // product's rounding error recovered by an FMA, the sum by TwoSum)
+    const int64_t sn = (int64_t)split * 4;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!valid[h]) continue;
+        const int64_t ic = bb[h] * NR;
+#pragma unroll
+        for (int g = 0; g < NR; ++g) {
+            const int64_t i = ic + g;
+            out[(sn + 0) * n_rays + i] = make_float2(h ? phi[g].y : phi[g].x, 0.f);
+            float shi = 0.f, slo = 0.f;
+            if (g > 0) {
+                const float2 a = s_hi[(NR * 3 + g - 1) * NT + tid], c = s_lo[(NR * 3 + g - 1) * NT + tid];
+                shi = h ? a.y : a.x;
+                slo = h ? c.y : c.x;
+            }
+#pragma unroll
+            for (int oo = 0; oo < 3; ++oo) {
+                const int q = (g * 3 + oo) * NT + tid;
+                const float2 a = s_hi[q], c = s_lo[q];
+                float hi = h ? a.y : a.x, lo = h ? c.y : c.x;
+                if (g > 0) {
+                    const float2 f2 = oo == 0 ? fx[g - 1] : (oo == 1 ? fy[g - 1] : fz[g - 1]);
+                    const float e = 0.5f * (h ? f2.y : f2.x);
+                    const float p = e * shi;
+                    const float pe = fmaf(e, shi, -p);
+                    const float s = hi + p;
+                    const float bv = s - hi;
+                    const float err = (hi - (s - bv)) + (p - bv);
+                    lo = lo + (err + fmaf(e, slo, pe));
+                    hi = s;
+                }
+                out[(sn + 1 + oo) * n_rays + i] = make_float2(hi, lo);
+            }
+        }
+    }
+}
+
+// TPSM: resident threads per SM the register allocation is bounded for (384:
+// 168 registers, with some spilling; 256: no spills)
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM>
+__global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
+{
+    if (A.gate && *A.gate == 0ull) return;
+    __shared__ float4 s_a[kTile];
+    __shared__ float4 s_b[kTile];
+    __shared__ float s_e[PEPS ? kTile : 1];
+    __shared__ float2 s_hl[2 * ((NRING + 1) * 3 + NRING) * NT];
+    const int64_t n_b = A.n / (NRING + 1);
+    const int64_t b0 = (int64_t)blockIdx.x * 2 * NT;
+    const int split = blockIdx.y;
+    const int64_t p0 = (int64_t)split * A.per_split;
+    const int64_t p1 = min(A.f.n, p0 + A.per_split);
+    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
+                                                     (float2 *)A.out, s_a, s_b, s_e, s_hl);
+}
+
 // ForceArgs for the bundle kernel: n = rays, group = rays per bundle; rep is
 // the per-bundle replica array.
 template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>

@@ -241,6 +241,25 @@ cudaError_t launch_stage_field(const DevField &f, const ForceShape &sh, bool fp6
                                const double *d_pts, const int *d_rep, int64_t n, double *d_out,
                                cudaStream_t st);
 
+// gridded field (Sec. 3.3 grid path, App. B): node values and x3 spline
+// second derivatives, 4 n^3 doubles each, [f][i1][i2][i3] with i3 fastest
+struct GridDev {
+    int n = 0, n_int = 0;
+    double lo[3] = {0.0, 0.0, 0.0};
+    double h = 0.0;
+    double *val = nullptr, *y2 = nullptr;
+};
+// build g.val and g.y2 (allocated here) from host particles; returns an
+// rt3d status and sets err on failure
+int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, double soft, int mean_subtract,
+               cudaStream_t st, std::string &err);
+void grid_free(GridDev &g);
+// App. B evaluation at n points (SoA px, py, pz).  mode 0: -F as (hi, lo)
+// FP32 pairs in the pair-sum partial layout (one split); 1: -F as FP64
+// partials; 2: F at out[4 i + f]
+cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
+                             int mode, void *out, const unsigned long long *gate, cudaStream_t st);
+
 int force_max_splits(const ForceShape &sh, int64_t n_particles);
 size_t partials_bytes(const ForceShape &sh, int64_t n_rays, bool fp64);
 

@@ -46,8 +46,8 @@ def _cloud(n, seed, centre=(0.0, 0.0, 800.0), scale=0.3, per_particle_soft=False
     return pos, mass, soft
 
 
-PRECISIONS = ["fp64", "mixed", "mixed-scalar", "mixed-packed", "mixed-bundle1"]
-VARIANT = {"mixed": 0, "mixed-scalar": 1, "mixed-packed": 2, "mixed-bundle1": 3}
+PRECISIONS = ["fp64", "mixed", "mixed-scalar", "mixed-packed", "mixed-bundle1", "mixed-bundle2"]
+VARIANT = {"mixed": 0, "mixed-scalar": 1, "mixed-packed": 2, "mixed-bundle1": 3, "mixed-bundle2": 4}
 
 
 def ctx_prec(P, precision, **kw):
