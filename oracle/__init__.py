@@ -106,6 +106,9 @@ def lib():
         L.orc_histogram.argtypes = [C.c_int64, _dp, C.POINTER(C.c_int32), C.POINTER(HistOpts),
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _dp]
         L.orc_histogram.restype = C.c_int
+        L.orc_shear_histogram.argtypes = [C.c_int64, _dp, _dp, _dp, C.POINTER(C.c_int32), C.POINTER(HistOpts),
+                                          C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _dp]
+        L.orc_shear_histogram.restype = C.c_int
         L.orc_spline_y2.argtypes = [C.c_int, _dp, C.c_int64, _dp]
         L.orc_spline_y2.restype = None
         L.orc_grid_y2.argtypes = [C.c_int, _dp, _dp]
@@ -293,5 +296,22 @@ def histogram(mu, flags=None, bins=200, mu_min=0.5, mu_max=5.0):
                              _p(counts, C.c_uint64), _p(wfix, C.c_uint64), _p(sc))
     if rc != 0:
         raise ValueError("orc_histogram failed: %d" % rc)
+    keys = ("n_used", "n_under", "n_over", "n_neg", "n_bad", "W_total", "mean_w", "sigma_w")
+    return counts, wfix, dict(zip(keys, sc))
+
+
+def shear_histogram(mu, gamma1, gamma2, flags=None, bins=200, g_min=1e-4, g_max=1.0):
+    """shear PDF: bins in log10|gamma|, weight 1/|mu| (see orc.h)"""
+    mu, g1, g2 = (np.ascontiguousarray(a, np.float64) for a in (mu, gamma1, gamma2))
+    n = mu.shape[0]
+    fl = None if flags is None else np.ascontiguousarray(flags, np.int32)
+    counts = np.zeros(bins, np.uint64)
+    wfix = np.zeros(bins, np.uint64)
+    sc = np.zeros(8)
+    o = HistOpts(bins, g_min, g_max)
+    rc = lib().orc_shear_histogram(n, _p(mu), _p(g1), _p(g2), _p(fl, C.c_int32) if fl is not None else None,
+                                   C.byref(o), _p(counts, C.c_uint64), _p(wfix, C.c_uint64), _p(sc))
+    if rc != 0:
+        raise ValueError("orc_shear_histogram failed: %d" % rc)
     keys = ("n_used", "n_under", "n_over", "n_neg", "n_bad", "W_total", "mean_w", "sigma_w")
     return counts, wfix, dict(zip(keys, sc))

@@ -146,6 +146,15 @@ int orc_histogram(int64_t n, const double *mu, const int32_t *flags,
                   const orc_hist_opts *o, uint64_t *counts, uint64_t *wfix,
                   double *scalars);
 
+/* shear PDF (Sec. 5.4, Fig. RBMvsMudShear): as orc_histogram, but bins are
+ * uniform in log10|gamma|, |gamma| = sqrt(gamma1^2 + gamma2^2), over
+ * [o->mu_min, o->mu_max] read as the |gamma| range; each bundle still
+ * carries the source-plane weight 1/|mu|; the moments are those of |gamma|
+ * under that weight.  |gamma| = 0 counts as underflow. */
+int orc_shear_histogram(int64_t n, const double *mu, const double *g1, const double *g2,
+                        const int32_t *flags, const orc_hist_opts *o, uint64_t *counts,
+                        uint64_t *wfix, double *scalars);
+
 #ifdef __cplusplus
 }
 #endif

@@ -95,3 +95,49 @@ def test_flux_conservation_weighting():
     mu = np.array([0.9, 0.95, 1.0, 1.2, 2.0])
     _, _, sc = oracle.histogram(mu, None, 20, 0.5, 5.0)
     assert abs(sc["mean_w"] - len(mu) / np.sum(1 / mu)) < 1e-15
+
+
+def test_shear_histogram_against_brute_force():
+    # shear PDF (Sec. 5.4): |gamma| binned in log10, weight 1/|mu|, checked
+    # against 50-digit edges and exact integer weights
+    g = inputs.rng(43)
+    n, bins, g_min, g_max = 4000, 120, 1e-3, 0.5
+    gam = np.exp(g.uniform(math.log(3e-4), math.log(0.9), n))
+    ang = g.uniform(0, 2 * math.pi, n)
+    g1, g2 = gam * np.cos(ang), gam * np.sin(ang)
+    mu = np.exp(g.uniform(math.log(0.5), math.log(3.0), n))
+    mu[::11] *= -1.0
+    g1[4], g2[4] = 0.0, 0.0          # no shear: underflow
+    flags = np.zeros(n, np.int32)
+    flags[9] = oracle.F_NONFINITE
+    getcontext().prec = 50
+    _, edges = _edges(g_min, g_max, bins)
+    gabs = [Decimal(float(a)) ** 2 + Decimal(float(b)) ** 2 for a, b in zip(g1, g2)]
+    gabs = [x.sqrt() for x in gabs]
+    keep = np.array([x == 0 or min(abs(x / e - 1) for e in edges) > Decimal("1e-9") for x in gabs])
+    mu, g1, g2, flags = mu[keep], g1[keep], g2[keep], flags[keep]
+    gabs = [x for x, k in zip(gabs, keep) if k]
+    counts, wfix, sc = oracle.shear_histogram(mu, g1, g2, flags, bins, g_min, g_max)
+    ref_c, ref_w = [0] * bins, [0] * bins
+    under = over = neg = used = bad = 0
+    W, S1 = [], []
+    for m, x, fl in zip(mu, gabs, flags):
+        if fl:
+            bad += 1
+            continue
+        used += 1
+        neg += m < 0
+        w = 1.0 / abs(float(m))
+        W.append(w)
+        S1.append(w * float(x))
+        if x < edges[0]:
+            under += 1
+        elif x >= edges[-1]:
+            over += 1
+        else:
+            k = max(i for i in range(bins) if edges[i] <= x)
+            ref_c[k] += 1
+            ref_w[k] += round(Fraction(2 ** 32) / Fraction(abs(float(m))))
+    assert counts.tolist() == ref_c and wfix.tolist() == ref_w
+    assert (sc["n_used"], sc["n_under"], sc["n_over"], sc["n_neg"], sc["n_bad"]) == (used, under, over, neg, bad)
+    assert abs(sc["mean_w"] / (math.fsum(S1) / math.fsum(W)) - 1) < 1e-13
