@@ -40,7 +40,8 @@ KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "
 # workload, per (kernel, threads per block, splits), from the ncu captures
 # summarised under profiles/
 PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31): 2130432,
-                       ("k_force_bundle2", 128, 196): 2169600 + 68610304}
+                       ("k_force_bundle2", 128, 196): 2169600 + 68610304,
+                       ("k_force_bundle2x", 64, 131): 2154752 + 34375680}
 
 
 def workload(full=True):
@@ -464,7 +465,7 @@ def main():
     ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid"])
     ap.add_argument("--grid-n", type=int, default=256, help="nodes per side of the grid workload")
     ap.add_argument("--cones", type=int, default=512)
-    ap.add_argument("--cone-steps", type=int, default=8)
+    ap.add_argument("--cone-steps", type=int, default=16)
     ap.add_argument("--fp64-cones", type=int, default=8)
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", type=int, default=0,

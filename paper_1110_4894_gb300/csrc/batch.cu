@@ -4,7 +4,8 @@
 // The persistent kernel is a cooperative launch of one resident grid.  For
 // every global RK4 stage it runs two phases separated by grid barriers:
 //   force phase: every (cone, ray block, particle split) work item of the
-//                cones still in flight, statically strided over the blocks;
+//                cones still in flight, taken from a work queue (an atomic
+//                counter) by whichever block is free, largest items first;
 //   stage phase: the FP64 integrator stage of every ray of those cones.
 // Cones whose rays have all crossed their source plane drop out; cones with
 // fewer steps simply finish earlier.  The barrier waits are bounded by a
@@ -138,10 +139,22 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
     __shared__ float4 s_a[kTile];
     __shared__ float4 s_b[kTile];
     __shared__ float2 s_e[kTile];
+    __shared__ unsigned s_it;
     const int64_t nthreads = (int64_t)gridDim.x * NT;
     for (int g = 0; g < B.g_end; ++g) {
         const int step = g >> 2, stage = g & 3;
-        for (int64_t it = blockIdx.x; it < B.n_items; it += gridDim.x) {
+        // work queue of this stage's force items (largest first, as planned):
+        // each block takes the next item when it is free.  The counter of the
+        // next stage is the one stage g-1 used, finished before the barriers
+        // that ended it, so it is reset here.
+        unsigned *queue = B.bar + 4;
+        if (blockIdx.x == 0 && threadIdx.x == 0) queue[(g + 1) & 1] = 0u;
+        for (;;) {
+            if (threadIdx.x == 0) s_it = atomicAdd(&queue[g & 1], 1u);
+            __syncthreads();
+            const int64_t it = s_it;
+            __syncthreads();
+            if (it >= B.n_items) break;
             const int4 item = B.items[it];
             const BatchCone &C = B.cones[item.x];
             if (!cone_active(C, step)) continue;  // uniform across the block

@@ -29,7 +29,7 @@ struct BatchArgs {
     int64_t T;             // padded ray count
     int RB;                // rays per block
     int g_end;             // global stages to run
-    unsigned *bar;         // grid barrier: count, generation
+    unsigned *bar;         // [0] barrier count, [1] generation, [2] error word, [4], [5] work queues
     int *err;              // watchdog / error word
     unsigned long long limit_ns;
     double *bout;

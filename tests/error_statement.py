@@ -59,17 +59,25 @@ def _sample(n, k):
 
 
 def _points(cfg, theta, n_pts, chi_s, seed=7):
-    """points on the unperturbed lines of sight of the given bundles, with the
-    replica index the bundle's central ray would select there"""
+    """stage-like points: a run of neighbouring bundles (grid order) on their
+    unperturbed lines of sight at each of a few comoving distances, so that
+    consecutive points are neighbours as the rays of one RK4 stage are; with
+    the replica index the bundle's central ray would select there"""
     g = np.random.default_rng(seed)
-    b = g.integers(0, len(theta), n_pts)
+    k = 8
+    per = max(1, n_pts // k)
     if cfg.get("replicated"):
-        chi = g.uniform(0.0, chi_s, n_pts)
+        chis = np.sort(g.uniform(0.02 * chi_s, 0.98 * chi_s, k))
     else:
         lc = cfg.get("lens_chi", 0.5 * chi_s)
-        chi = lc + g.normal(0.0, 2.0, n_pts)
-    pts = np.stack([theta[b, 0] * chi, theta[b, 1] * chi, chi], axis=1)
-    rep = np.floor(chi / cfg["L"]).astype(np.int32) if cfg.get("replicated") else None
+        chis = lc + np.linspace(-2.0, 2.0, k)
+    pts = []
+    for chi in chis:
+        b0 = int(g.integers(0, max(1, len(theta) - per)))
+        th = theta[b0:b0 + per]
+        pts.append(np.stack([th[:, 0] * chi, th[:, 1] * chi, np.full(len(th), chi)], axis=1))
+    pts = np.concatenate(pts)
+    rep = np.floor(pts[:, 2] / cfg["L"]).astype(np.int32) if cfg.get("replicated") else None
     return pts, rep
 
 
@@ -149,6 +157,11 @@ def _rel_alpha(rays, res, idx=None):
     return (np.linalg.norm(a_g - a_o, axis=-1) / np.linalg.norm(a_o, axis=-1)).ravel()
 
 
+def _abs_alpha(rays, res):
+    a_g = res.ray_theta() - rays[:, :, 1:3] / res.chi_s
+    return np.linalg.norm(a_g - res.alpha(), axis=-1).ravel()
+
+
 def _round_fp32(cfg):
     """the field with positions (about the field's centre) and masses rounded to FP32"""
     pos = np.asarray(cfg["pos"], np.float64)
@@ -189,7 +202,7 @@ def phase_compare(args):
         cosmo = oracle.Cosmology(*cfg["cosmo"])
         row = {}
         if name == "c4_cones":
-            dm, da, dm64, dmc, dac = [], [], [], [], []
+            dm, da, dar, dm64, dmc, dac = [], [], [], [], [], []
             for i, c in enumerate(cfg["cones"]):
                 mu_g, mu_f = d[f"{name}/{i}/mixed/mu"], d[f"{name}/{i}/fp64/mu"]
                 dm64.append(np.abs(mu_g / mu_f - 1))
@@ -200,6 +213,7 @@ def phase_compare(args):
                                  theta_r=cfg["theta_r"], schedule=0, n_steps=c["n_steps"])
                 dm.append(np.abs(mu_g[idx] / o.mu - 1))
                 da.append(_rel_alpha(d[f"{name}/{i}/mixed/rays_s"], o))
+                dar.append(_abs_alpha(d[f"{name}/{i}/mixed/rays_s"], o) / np.sqrt(np.mean(np.sum(o.alpha() ** 2, -1))))
                 if i < 4 and n_ctl:
                     j = idx[:n_ctl]
                     oc = oracle.trace(cosmo, _field(_round_fp32(cc)), c["z_s"], c["theta"][j], n_ring=cfg["n_ring"],
@@ -208,6 +222,7 @@ def phase_compare(args):
                     dac.append(np.linalg.norm(oc.alpha() - o.alpha()[:len(j)], axis=-1).ravel()
                                / np.linalg.norm(o.alpha()[:len(j)], axis=-1).ravel())
             row = dict(mu=_stat(np.concatenate(dm)), alpha=_stat(np.concatenate(da)),
+                       alpha_rms=_stat(np.concatenate(dar)),
                        mu_vs_gpu_fp64=_stat(np.concatenate(dm64)),
                        control_mu=_stat(np.concatenate(dmc)) if dmc else None,
                        control_alpha=_stat(np.concatenate(dac)) if dac else None,
@@ -223,6 +238,7 @@ def phase_compare(args):
         o = oracle.trace(cosmo, field, cfg["z_s"], theta[idx], **_trace_kw(cfg))
         row["mu"] = _stat(np.abs(mu_g[idx] / o.mu - 1))
         row["alpha"] = _stat(_rel_alpha(rays_g[idx], o))
+        row["alpha_rms"] = _stat(_abs_alpha(rays_g[idx], o) / np.sqrt(np.mean(np.sum(o.alpha() ** 2, -1))))
         row["flags_equal"] = bool(np.array_equal(d[f"{name}/flags"][idx], o.flags))
         row["steps_equal"] = bool(np.array_equal(d[f"{name}/steps"][idx], o.steps))
         pts = d[f"{name}/pts"]
@@ -252,15 +268,16 @@ def _fmt(s, key="max"):
 
 
 def _print_table(rows):
-    print("| workload | RK4 steps | bundles GPU / oracle | max / p99.9 \\|Δα/α\\| | max / p99.9 \\|Δμ/μ\\| "
-          "| \\|Δμ/μ\\| vs GPU FP64 (max) | \\|Δ∇φ\\|/\\|∇φ\\| max / p99.9 | control \\|Δμ/μ\\| / \\|Δα/α\\| (max) |")
-    print("|---|---|---|---|---|---|---|---|")
+    print("| workload | RK4 steps | bundles GPU / oracle | max / p99.9 \\|Δα/α\\| | max \\|Δα\\|/rms α "
+          "| max / p99.9 \\|Δμ/μ\\| | \\|Δμ/μ\\| vs GPU FP64 (max) | \\|Δ∇φ\\|/\\|∇φ\\| max / p99.9 "
+          "| control \\|Δμ/μ\\| / \\|Δα/α\\| (max) |")
+    print("|---|---|---|---|---|---|---|---|---|")
     for name, r in rows.items():
         nb = "%s / %s" % (r.get("bundles_gpu"), r.get("bundles_oracle", r.get("mu", {}).get("n") if r.get("mu") else "—"))
-        print("| %s | %s | %s | %s / %s | %s / %s | %s | %s / %s | %s / %s |" % (
-            name, r["steps"], nb, _fmt(r["alpha"]), _fmt(r["alpha"], "p999"), _fmt(r["mu"]), _fmt(r["mu"], "p999"),
-            _fmt(r.get("mu_vs_gpu_fp64")), _fmt(r.get("grad_phi")), _fmt(r.get("grad_phi"), "p999"),
-            _fmt(r.get("control_mu")), _fmt(r.get("control_alpha"))))
+        print("| %s | %s | %s | %s / %s | %s | %s / %s | %s | %s / %s | %s / %s |" % (
+            name, r["steps"], nb, _fmt(r["alpha"]), _fmt(r["alpha"], "p999"), _fmt(r.get("alpha_rms")),
+            _fmt(r["mu"]), _fmt(r["mu"], "p999"), _fmt(r.get("mu_vs_gpu_fp64")), _fmt(r.get("grad_phi")),
+            _fmt(r.get("grad_phi"), "p999"), _fmt(r.get("control_mu")), _fmt(r.get("control_alpha"))))
 
 
 def main():
