@@ -231,6 +231,17 @@ int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones,
 int rt3d_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const int32_t *flags,
                    const rt3d_hist_opts *o, rt3d_hist *out);
 
+/* Shear PDF (Sec. 5.4, Fig. RBMvsMudShear) of n bundles: bins uniform in
+ * log10|gamma|, |gamma| = sqrt(gamma1^2 + gamma2^2), over [o->mu_min,
+ * o->mu_max] read as the |gamma| range; every bundle keeps the source-plane
+ * weight round(2^32/|mu|) of the muPDF; |gamma| = 0 counts as underflow; the
+ * scalars are the 1/|mu|-weighted mean and spread of |gamma|.  Exclusions
+ * as rt3d_histogram (and non-finite gamma).  The paper does not state its
+ * shear-PDF weighting; this is the muPDF's. */
+int rt3d_shear_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const double *gamma1,
+                         const double *gamma2, const int32_t *flags, const rt3d_hist_opts *o,
+                         rt3d_hist *out);
+
 /* phi and grad phi (comoving, with mean subtraction when enabled) at n
  * points: out = n*4 (phi, dphi/dx1, dphi/dx2, dphi/dx3).  rep: replica per
  * point (replicated fields; NULL = 0).  Uses the context's precision. */

@@ -103,6 +103,8 @@ def lib(build=True):
         "rt3d_trace_batch": ([vp, C.c_int, C.POINTER(Cone), C.POINTER(BundleOpts), C.POINTER(BundleResult)],
                              C.c_int),
         "rt3d_histogram": ([vp, C.c_int64, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)], C.c_int),
+        "rt3d_shear_histogram": ([vp, C.c_int64, _dp, _dp, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)],
+                                 C.c_int),
         "rt3d_histogram_device": ([vp, vp, C.c_int64, vp, C.POINTER(HistOpts), vp, vp, vp], C.c_int),
         "rt3d_potential": ([vp, C.c_int, C.c_int64, _dp, _ip, _dp], C.c_int),
         "rt3d_load_grid": ([vp, C.c_int, C.c_int64, _dp, _dp, C.c_double, C.POINTER(GridOpts)], C.c_int),
@@ -249,6 +251,20 @@ class Context:
         h = Hist(_p(counts, C.c_uint64), _p(wfix, C.c_uint64))
         o = HistOpts(bins, mu_min, mu_max)
         self._check(self.L.rt3d_histogram(self.h, mu.shape[0], _p(mu), _p(fl, C.c_int32), C.byref(o), C.byref(h)))
+        sc = dict(n_used=h.n_used, n_under=h.n_under, n_over=h.n_over, n_neg=h.n_neg, n_bad=h.n_bad,
+                  W_total=h.W_total, mean_w=h.mean_w, sigma_w=h.sigma_w)
+        return counts, wfix, sc
+
+    def shear_histogram(self, mu, gamma1, gamma2, flags=None, bins=200, g_min=1e-4, g_max=1.0):
+        """rt3d_shear_histogram: |gamma| in log10 bins, weight 1/|mu|."""
+        mu, g1, g2 = (np.ascontiguousarray(a, np.float64) for a in (mu, gamma1, gamma2))
+        fl = None if flags is None else np.ascontiguousarray(flags, np.int32)
+        counts = np.zeros(bins, np.uint64)
+        wfix = np.zeros(bins, np.uint64)
+        h = Hist(_p(counts, C.c_uint64), _p(wfix, C.c_uint64))
+        o = HistOpts(bins, g_min, g_max)
+        self._check(self.L.rt3d_shear_histogram(self.h, mu.shape[0], _p(mu), _p(g1), _p(g2), _p(fl, C.c_int32),
+                                                C.byref(o), C.byref(h)))
         sc = dict(n_used=h.n_used, n_under=h.n_under, n_over=h.n_over, n_neg=h.n_neg, n_bad=h.n_bad,
                   W_total=h.W_total, mean_w=h.mean_w, sigma_w=h.sigma_w)
         return counts, wfix, sc

@@ -171,7 +171,7 @@ struct rt3d_ctx {
         size_t partials_n = 0;
         unsigned long long *cnt = nullptr;
         size_t cnt_n = 0;
-        unsigned *bar = nullptr;  // [0] count, [1] generation, [2] error word
+        unsigned *bar = nullptr;  // [0] count, [1] generation, [2] error word, [4], [5] work queues
         double *bout = nullptr;
         size_t bout_n = 0;
         double *rout = nullptr;
@@ -911,6 +911,7 @@ struct BatchPlan {
     std::vector<int64_t> ray_base, b_base, dlam_off, part_off, per_split;
     std::vector<int> S;
     std::vector<int4> items;
+    std::vector<int64_t> cost;  // rays x particles of each item (planning order)
     std::vector<int> rb2cone;
     size_t cone_bytes(int n) const { return sizeof(BatchCone) * (size_t)n; }
 };
@@ -941,12 +942,26 @@ static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *con
             p.rb2cone.push_back(c);
         }
         p.T += nrb * RB;
+        for (int64_t rb = 0; rb < nrb; ++rb) {
+            const int64_t rays = std::min<int64_t>(RB, n_rays - rb * RB);
+            for (int64_t s = 0; s < S; ++s) {
+                const int64_t parts = std::min<int64_t>(tps * kTile, N - s * tps * kTile);
+                p.cost.push_back(rays * std::max<int64_t>(parts, 1));
+            }
+        }
         p.n_b_total += nb;
         p.dlam_total += cones[c].n_steps;
         p.partials_total += S * 4 * n_rays;
         p.max_steps = std::max(p.max_steps, cones[c].n_steps);
         p.g_end = std::max(p.g_end, 4 * (cones[c].n_steps + max_extra));
     }
+    // the work queue hands out items in this order: largest first
+    std::vector<size_t> order(p.items.size());
+    for (size_t i = 0; i < order.size(); ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](size_t a, size_t b) { return p.cost[a] > p.cost[b]; });
+    std::vector<int4> sorted(p.items.size());
+    for (size_t i = 0; i < order.size(); ++i) sorted[i] = p.items[order[i]];
+    p.items.swap(sorted);
     return RT3D_OK;
 }
 
@@ -1039,8 +1054,8 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     CK(grow(BS.dlam, BS.dlam_n, (size_t)plan.dlam_total));
     CK(grow(BS.partials, BS.partials_n, (size_t)plan.partials_total));
     CK(grow(BS.cnt, BS.cnt_n, (size_t)(3 * n_cones)));
-    size_t bar_n = BS.bar ? 4 : 0;
-    CK(grow(BS.bar, bar_n, 4));
+    size_t bar_n = BS.bar ? 8 : 0;
+    CK(grow(BS.bar, bar_n, 8));
     CK(grow(BS.bout, BS.bout_n, (size_t)(6 * plan.n_b_total)));
     if (want_rays) CK(grow(BS.rout, BS.rout_n, (size_t)(8 * nr * plan.n_b_total)));
     std::vector<unsigned char> table;
@@ -1053,7 +1068,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     CK(cudaMemcpyAsync(BS.cones, table.data(), table.size(), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(BS.items, plan.items.data(), plan.items.size() * sizeof(int4), cudaMemcpyHostToDevice, st));
     CK(cudaMemcpyAsync(BS.rb2cone, plan.rb2cone.data(), plan.rb2cone.size() * sizeof(int), cudaMemcpyHostToDevice, st));
-    CK(cudaMemsetAsync(BS.bar, 0, 4 * sizeof(unsigned), st));
+    CK(cudaMemsetAsync(BS.bar, 0, 8 * sizeof(unsigned), st));
     int grid = 0;
     const int MODE = nr == 5 ? 4 : (nr == 9 ? 8 : 0);
     CK(batch_resident_blocks(NT, MODE, &grid));
@@ -1274,6 +1289,48 @@ extern "C" int rt3d_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const 
     if (flags && n > 0) CK(cudaMemcpyAsync(d_fl, flags, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
     unsigned long long *cnt = ctx->d_hist_u64, *wf = cnt + o->bins, *sc = wf + o->bins;
     CK(launch_histogram(n, d_mu, 1, d_fl, nullptr, o->bins, o->mu_min, o->mu_max, cnt, wf, sc, ctx->d_hist_f64, st));
+    double o8[8];
+    CK(cudaMemcpyAsync(out->counts, cnt, o->bins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(out->wfix, wf, o->bins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaMemcpyAsync(o8, ctx->d_hist_f64, sizeof o8, cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    out->n_used = (int64_t)o8[0];
+    out->n_under = (int64_t)o8[1];
+    out->n_over = (int64_t)o8[2];
+    out->n_neg = (int64_t)o8[3];
+    out->n_bad = (int64_t)o8[4];
+    out->W_total = o8[5];
+    out->mean_w = o8[6];
+    out->sigma_w = o8[7];
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_shear_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const double *gamma1,
+                                    const double *gamma2, const int32_t *flags, const rt3d_hist_opts *o,
+                                    rt3d_hist *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    int rc = check_hist(ctx, o);
+    if (rc) return rc;
+    if (n < 0 || (n > 0 && (!mu || !gamma1 || !gamma2)) || !out || !out->counts || !out->wfix)
+        return fail(ctx, RT3D_EINVAL, "null arrays");
+    CK(cudaSetDevice(ctx->device));
+    rc = ensure_hist(ctx, o->bins);
+    if (rc) return rc;
+    cudaStream_t st = ctx->stream;
+    const int64_t m = std::max<int64_t>(n, 1);
+    CK(grow(ctx->d_io, ctx->d_io_n, (size_t)(4 * m)));
+    double *d_mu = ctx->d_io, *d_g1 = ctx->d_io + m, *d_g2 = ctx->d_io + 2 * m;
+    int *d_fl = flags ? (int *)(ctx->d_io + 3 * m) : nullptr;
+    if (n > 0) {
+        CK(cudaMemcpyAsync(d_mu, mu, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_g1, gamma1, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(d_g2, gamma2, n * sizeof(double), cudaMemcpyHostToDevice, st));
+        if (flags) CK(cudaMemcpyAsync(d_fl, flags, n * sizeof(int32_t), cudaMemcpyHostToDevice, st));
+    }
+    unsigned long long *cnt = ctx->d_hist_u64, *wf = cnt + o->bins, *sc = wf + o->bins;
+    CK(launch_histogram(n, d_mu, 1, d_fl, nullptr, o->bins, o->mu_min, o->mu_max, cnt, wf, sc, ctx->d_hist_f64, st,
+                        d_g1, d_g2));
     double o8[8];
     CK(cudaMemcpyAsync(out->counts, cnt, o->bins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));
     CK(cudaMemcpyAsync(out->wfix, wf, o->bins * sizeof(uint64_t), cudaMemcpyDeviceToHost, st));

@@ -152,30 +152,46 @@ cudaError_t launch_reduce(const TraceParams &tp, const double *d_theta, RayState
 // by atomics (order-independent, so bit-reproducible), moments by one block
 // in a fixed order.
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ bool hist_take(int64_t i, const double *mu, int stride, const int *fl, const double *fld,
-                                          double &m)
+// value binned and weight base of entry i: v = |mu| (muPDF) or, with a shear
+// pair, v = |gamma| = sqrt(g1^2 + g2^2) (shear PDF, Sec. 5.4, products and sum
+// rounded separately as in the FP64 definition); the weight is 1/|mu| in both
+struct HistIn {
+    const double *mu;
+    int stride;
+    const int *fl;
+    const double *fld;
+    const double *g1, *g2;  // shear PDF; null for the muPDF
+};
+
+__device__ __forceinline__ bool hist_take(const HistIn &h, int64_t i, double &m, double &v)
 {
-    m = mu[i * stride];
-    int f = fl ? fl[i] : (fld ? (int)fld[i * stride] : 0);
+    m = h.mu[i * h.stride];
+    int f = h.fl ? h.fl[i] : (h.fld ? (int)h.fld[i * h.stride] : 0);
     if ((f & (RT3D_F_NOCROSS | RT3D_F_NONFINITE)) || !isfinite(m) || m == 0.0) return false;
+    if (h.g1) {
+        const double a = h.g1[i], b = h.g2[i];
+        v = sqrt(__dadd_rn(__dmul_rn(a, a), __dmul_rn(b, b)));
+        if (!isfinite(v)) return false;
+    } else {
+        v = fabs(m);
+    }
     return true;
 }
 
-__global__ void k_hist_bins(int64_t n, const double *__restrict__ mu, int stride, const int *__restrict__ fl,
-                            const double *__restrict__ fld, int bins, double lmin, double dl,
-                            unsigned long long *counts, unsigned long long *wfix, unsigned long long *scal)
+__global__ void k_hist_bins(int64_t n, HistIn h, int bins, double lmin, double dl, unsigned long long *counts,
+                            unsigned long long *wfix, unsigned long long *scal)
 {
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
-    double m;
-    if (!hist_take(i, mu, stride, fl, fld, m)) {
+    double m, v;
+    if (!hist_take(h, i, m, v)) {
         atomicAdd(&scal[4], 1ull);
         return;
     }
     atomicAdd(&scal[0], 1ull);
     if (m < 0.0) atomicAdd(&scal[3], 1ull);
     m = fabs(m);
-    const double bb = floor((log10(m) - lmin) / dl);
+    const double bb = floor((log10(v) - lmin) / dl);
     if (bb < 0.0) {
         atomicAdd(&scal[1], 1ull);
     } else if (bb >= (double)bins) {
@@ -187,27 +203,25 @@ __global__ void k_hist_bins(int64_t n, const double *__restrict__ mu, int stride
     }
 }
 
-__global__ void __launch_bounds__(1024) k_hist_moments(int64_t n, const double *__restrict__ mu, int stride,
-                                                       const int *__restrict__ fl, const double *__restrict__ fld,
+__global__ void __launch_bounds__(1024) k_hist_moments(int64_t n, HistIn h,
                                                        const unsigned long long *__restrict__ scal, double *out8)
 {
     __shared__ double sw[1024], s1[1024];
     double w = 0.0, a1 = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        double m;
-        if (!hist_take(i, mu, stride, fl, fld, m)) continue;
-        m = fabs(m);
-        const double iw = 1.0 / m;
+        double m, v;
+        if (!hist_take(h, i, m, v)) continue;
+        const double iw = 1.0 / fabs(m);
         w += iw;
-        a1 += iw * m;
+        a1 += iw * v;
     }
     sw[threadIdx.x] = w;
     s1[threadIdx.x] = a1;
     __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) {
-            sw[threadIdx.x] += sw[threadIdx.x + h];
-            s1[threadIdx.x] += s1[threadIdx.x + h];
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) {
+            sw[threadIdx.x] += sw[threadIdx.x + k];
+            s1[threadIdx.x] += s1[threadIdx.x + k];
         }
         __syncthreads();
     }
@@ -215,16 +229,15 @@ __global__ void __launch_bounds__(1024) k_hist_moments(int64_t n, const double *
     __syncthreads();
     double a2 = 0.0;
     for (int64_t i = threadIdx.x; i < n; i += blockDim.x) {
-        double m;
-        if (!hist_take(i, mu, stride, fl, fld, m)) continue;
-        m = fabs(m);
-        const double d = m - mean;
-        a2 += d * d / m;
+        double m, v;
+        if (!hist_take(h, i, m, v)) continue;
+        const double d = v - mean;
+        a2 += d * d / fabs(m);
     }
     sw[threadIdx.x] = a2;
     __syncthreads();
-    for (int h = blockDim.x / 2; h > 0; h >>= 1) {
-        if (threadIdx.x < h) sw[threadIdx.x] += sw[threadIdx.x + h];
+    for (int k = blockDim.x / 2; k > 0; k >>= 1) {
+        if (threadIdx.x < k) sw[threadIdx.x] += sw[threadIdx.x + k];
         __syncthreads();
     }
     if (threadIdx.x == 0) {
@@ -238,21 +251,21 @@ __global__ void __launch_bounds__(1024) k_hist_moments(int64_t n, const double *
 cudaError_t launch_histogram(int64_t n, const double *d_mu, int mu_stride, const int *d_flags, const double *d_flagsd,
                              int bins, double mu_min, double mu_max, unsigned long long *d_counts,
                              unsigned long long *d_wfix, unsigned long long *d_scal, double *d_out8,
-                             cudaStream_t st)
+                             cudaStream_t st, const double *d_g1, const double *d_g2)
 {
     const double lmin = log10(mu_min);
     const double dl = (log10(mu_max) - lmin) / (double)bins;
+    HistIn h{d_mu, mu_stride, d_flags, d_flagsd, d_g1, d_g2};
     cudaError_t e;
     if ((e = cudaMemsetAsync(d_counts, 0, sizeof(unsigned long long) * bins, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_wfix, 0, sizeof(unsigned long long) * bins, st)) != cudaSuccess) return e;
     if ((e = cudaMemsetAsync(d_scal, 0, sizeof(unsigned long long) * 5, st)) != cudaSuccess) return e;
     if (n > 0) {
         const int64_t blocks = (n + 255) / 256;
-        k_hist_bins<<<(unsigned)blocks, 256, 0, st>>>(n, d_mu, mu_stride, d_flags, d_flagsd, bins, lmin, dl,
-                                                       d_counts, d_wfix, d_scal);
+        k_hist_bins<<<(unsigned)blocks, 256, 0, st>>>(n, h, bins, lmin, dl, d_counts, d_wfix, d_scal);
         if ((e = cudaGetLastError()) != cudaSuccess) return e;
     }
-    k_hist_moments<<<1, 1024, 0, st>>>(n, d_mu, mu_stride, d_flags, d_flagsd, d_scal, d_out8);
+    k_hist_moments<<<1, 1024, 0, st>>>(n, h, d_scal, d_out8);
     return cudaGetLastError();
 }
 

@@ -233,7 +233,8 @@ cudaError_t launch_reduce(const TraceParams &tp, const double *d_theta, RayState
 cudaError_t launch_histogram(int64_t n, const double *d_mu, int mu_stride, const int *d_flags,
                              const double *d_flagsd, int bins, double mu_min, double mu_max,
                              unsigned long long *d_counts, unsigned long long *d_wfix,
-                             unsigned long long *d_scal, double *d_out8, cudaStream_t st);
+                             unsigned long long *d_scal, double *d_out8, cudaStream_t st,
+                             const double *d_g1 = nullptr, const double *d_g2 = nullptr);
 cudaError_t launch_potential(const DevField &f, bool fp64, const double *d_pts, const int *d_rep,
                              int64_t n, const ForceShape &sh, void *d_partials, double *d_out,
                              cudaStream_t st);

@@ -222,6 +222,29 @@ def test_histogram_bit_exact(P):
             assert abs(s_g[k] / s_o[k] - 1) < 1e-12
 
 
+def test_shear_histogram_bit_exact(P):
+    g = inputs.rng(18)
+    n = 20000
+    gam = np.exp(g.uniform(np.log(1e-4), np.log(0.8), n))
+    ang = g.uniform(0, 2 * np.pi, n)
+    g1, g2 = gam * np.cos(ang), gam * np.sin(ang)
+    g1[::97], g2[::97] = 0.0, 0.0
+    mu = np.exp(g.uniform(np.log(0.4), np.log(6.0), n))
+    mu[::13] *= -1
+    flags = np.zeros(n, np.int32)
+    flags[::211] = oracle.F_NONFINITE
+    g1[5] = np.nan
+    ctx = ctx_for(P, P.MIXED)
+    for bins, lo, hi in ((200, 1e-3, 0.5), (23, 0.01, 0.2), (1, 1e-5, 1.0)):
+        c_g, w_g, s_g = ctx.shear_histogram(mu, g1, g2, flags, bins, lo, hi)
+        c_o, w_o, s_o = oracle.shear_histogram(mu, g1, g2, flags, bins, lo, hi)
+        assert np.array_equal(c_g, c_o) and np.array_equal(w_g, w_o)
+        for k in ("n_used", "n_under", "n_over", "n_neg", "n_bad"):
+            assert s_g[k] == s_o[k]
+        for k in ("W_total", "mean_w", "sigma_w"):
+            assert abs(s_g[k] / s_o[k] - 1) < 1e-12
+
+
 def test_errors_are_reported(P):
     ctx = P.Context(0)
     with pytest.raises(P.Rt3dError) as e:
