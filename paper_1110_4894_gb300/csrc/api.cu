@@ -176,6 +176,8 @@ struct rt3d_ctx {
         size_t bout_n = 0;
         double *rout = nullptr;
         size_t rout_n = 0;
+        double *prism = nullptr;
+        size_t prism_n = 0;
         cudaGraphExec_t exec = nullptr;
         std::vector<long long> key;
         std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // (cones, log2 rays, log2 pairs) -> (NT, items)
@@ -290,6 +292,7 @@ extern "C" int rt3d_destroy(rt3d_ctx *ctx)
     cudaFree(s.theta);
     cudaFree(s.bout);
     cudaFree(s.rout);
+    cudaFree(s.prism);
     cudaFree(ctx->d_hist_u64);
     cudaFree(ctx->d_hist_f64);
     cudaFree(ctx->d_io);
@@ -309,6 +312,7 @@ extern "C" int rt3d_destroy(rt3d_ctx *ctx)
         cudaFree(B.bar);
         cudaFree(B.bout);
         cudaFree(B.rout);
+        cudaFree(B.prism);
     }
     if (ctx->ev0) cudaEventDestroy(ctx->ev0);
     if (ctx->ev1) cudaEventDestroy(ctx->ev1);
@@ -778,6 +782,10 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
         if (rc) return rc;
         rs = make_state(ctx, n_b, nr);
     }
+    // mean-subtracted boxes: the prism field once per bundle and stage (value,
+    // gradient, Hessian), expanded to the bundle's other rays
+    const bool use_prism = !fs.is_grid && fs.df.replicated && fs.df.mean_subtract;
+    if (use_prism) CK(grow(s.prism, s.prism_n, (size_t)(kPrismRec * n_b)));
     const int total = b->n_steps + b->max_extra;
     for (int step = 0; step < total; ++step) {
         for (int stage = 0; stage < 4; ++stage) {
@@ -796,7 +804,12 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
                 CK(run_force(ctx, fs.df, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays,
                              rs.rep + (g & 1) * n_b, nr, n_rays, sh, fp64, s.partials, gate, st));
             if (e1) CK(cudaEventRecord(e1, st));
-            CK(launch_stage(tp, fs.df, rs, sh, fp64, s.partials, s.dlam, s.misc, step, stage, s.counters, st));
+            if (use_prism) {
+                CK(launch_prism(tp, fs.df, rs, step, stage, s.counters, s.prism, st));
+                ++launches;
+            }
+            CK(launch_stage(tp, fs.df, rs, sh, fp64, s.partials, s.dlam, s.misc, step, stage, s.counters, st,
+                            use_prism ? s.prism : nullptr));
             launches += 2;
             flaunch += gate ? 0 : 1;
         }
@@ -919,8 +932,8 @@ struct BatchPlan {
 // Layout of a batch: each cone's rays padded to whole ray blocks of RB, its
 // particles split into whole tiles of about per_item particles, one work item
 // per (cone, ray block, split).
-static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *cones, int nr, int RB, int64_t per_item,
-                      int max_extra, BatchPlan &p)
+static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *cones, int nr, int RB, int NT,
+                      int64_t per_item, int max_extra, BatchPlan &p)
 {
     p = BatchPlan{};
     for (int c = 0; c < n_cones; ++c) {
@@ -942,6 +955,16 @@ static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *con
             p.rb2cone.push_back(c);
         }
         p.T += nrb * RB;
+        const FieldSlot &fs = fields[cones[c].field_id];
+        if (fs.df.replicated && fs.df.mean_subtract) {
+            // prism records: one item per block of NT bundles, costed as the
+            // FP64 closed form (about 24 000 pair interactions per bundle)
+            const int64_t nbb = (nb + NT - 1) / NT;
+            for (int64_t q = 0; q < nbb; ++q) {
+                p.items.push_back(make_int4(c, (int)q, -1, 0));
+                p.cost.push_back(24000 * std::min<int64_t>(NT, nb - q * NT));
+            }
+        }
         for (int64_t rb = 0; rb < nrb; ++rb) {
             const int64_t rays = std::min<int64_t>(RB, n_rays - rb * RB);
             for (int64_t s = 0; s < S; ++s) {
@@ -968,7 +991,7 @@ static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *con
 static void fill_cone_table(const FieldSlot *fields, const Cosmo &cosmo, int christoffel, int n_cones,
                             const rt3d_cone *cones, const rt3d_bundle_opts *b, const BatchPlan &p, double *state,
                             int *ints, double *theta, double *dlam, float2 *partials, unsigned long long *cnt,
-                            double *rout, std::vector<unsigned char> &table)
+                            double *rout, double *prism, std::vector<unsigned char> &table)
 {
     table.assign(p.cone_bytes(n_cones), 0);
     BatchCone *T = (BatchCone *)table.data();
@@ -1002,6 +1025,7 @@ static void fill_cone_table(const FieldSlot *fields, const Cosmo &cosmo, int chr
         C.partials = partials + p.part_off[c];
         C.cnt = cnt + 3 * c;
         C.rout = rout ? rout + 8 * nr * p.b_base[c] : nullptr;
+        C.prism = (f.replicated && f.mean_subtract) ? prism + kPrismRec * p.b_base[c] : nullptr;
         C.chi_s = 0.0;
         C.z_s = cones[c].z_s;
         C.chi_l = b->lens_chi;
@@ -1042,7 +1066,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     // 2P rays per thread (packed kernel); both are multiples of 32
     const int RB = (nr == 5 || nr == 9) ? NT * nr : 2 * P * NT;
     BatchPlan plan;
-    int rc = plan_batch(ctx->fields.data(), n_cones, cones, nr, RB, per_item, b->max_extra, plan);
+    int rc = plan_batch(ctx->fields.data(), n_cones, cones, nr, RB, NT, per_item, b->max_extra, plan);
     if (rc) return fail(ctx, rc, "invalid cone list");
     const int64_t T = plan.T;
     CK(grow(*(char **)&BS.cones, BS.cones_n, plan.cone_bytes(n_cones)));
@@ -1059,8 +1083,9 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     CK(grow(BS.bout, BS.bout_n, (size_t)(6 * plan.n_b_total)));
     if (want_rays) CK(grow(BS.rout, BS.rout_n, (size_t)(8 * nr * plan.n_b_total)));
     std::vector<unsigned char> table;
+    CK(grow(BS.prism, BS.prism_n, (size_t)(kPrismRec * plan.n_b_total)));
     fill_cone_table(ctx->fields.data(), ctx->cosmo, ctx->opt.christoffel, n_cones, cones, b, plan, BS.state, BS.ints,
-                    BS.theta, BS.dlam, BS.partials, BS.cnt, want_rays ? BS.rout : nullptr, table);
+                    BS.theta, BS.dlam, BS.partials, BS.cnt, want_rays ? BS.rout : nullptr, BS.prism, table);
     cudaStream_t st = ctx->stream;
     for (int c = 0; c < n_cones; ++c)
         CK(cudaMemcpyAsync(BS.theta + 2 * plan.b_base[c], cones[c].theta, 2 * cones[c].n_bundles * sizeof(double),
@@ -1079,7 +1104,8 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     // the graph is keyed by everything its launches capture
     std::vector<long long> key = {n_cones, T, (long long)plan.items.size(), A.g_end, NT, per_item, grid,
                                   plan.max_steps, plan.n_b_total, (long long)(intptr_t)BS.cones,
-                                  (long long)(intptr_t)BS.items, (long long)(intptr_t)BS.bout};
+                                  (long long)(intptr_t)BS.items, (long long)(intptr_t)BS.bout,
+                                  (long long)(intptr_t)BS.prism};
     CK(cudaEventRecord(ctx->ev0, st));
     bool use_graph = g_limit == 0;
     if (use_graph && (BS.key != key || !BS.exec)) {

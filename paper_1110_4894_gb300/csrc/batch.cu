@@ -158,6 +158,11 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
             const int4 item = B.items[it];
             const BatchCone &C = B.cones[item.x];
             if (!cone_active(C, step)) continue;  // uniform across the block
+            if (item.z < 0) {  // the prism records of NT bundles (FP64)
+                const int64_t b = (int64_t)item.y * NT + threadIdx.x;
+                if (b < C.rs.n_b) bundle_prism(C.f, C.rs, g, b, C.prism);
+                continue;
+            }
             batch_item<P, NT, MODE>(C, item, g, s_a, s_b, s_e);
         }
         if (!grid_sync(B)) return;
@@ -170,7 +175,7 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
                 if (stage == 0 && local == 0) C.cnt[step & 1] = 0ull;
                 if (cone_active(C, step))
                     act = stage_ray(C.tp, C.f, C.rs, C.S, false, C.mfac, C.partials, C.dlam, C.chi_s, step, stage,
-                                    C.cnt, local);
+                                    C.cnt, local, nullptr, C.prism);
             }
             // ray blocks are multiples of 32 rays, so a warp never spans two cones
             const unsigned m = __ballot_sync(0xffffffffu, act);

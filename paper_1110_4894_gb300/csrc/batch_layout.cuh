@@ -14,6 +14,7 @@ struct BatchCone {
     float2 *partials;      // S * 4 * n_rays split partials
     unsigned long long *cnt;  // [0], [1] rays in flight after even / odd steps; [2] active ray-stages
     double *rout;          // optional per-ray final states (compact)
+    double *prism;         // mean-subtracted cones: kPrismRec doubles per bundle, else null
     double chi_s;          // written by the schedule kernel
     double z_s, chi_l, s_asinh, mfac;
     int64_t per_split, ray_base, b_base;
@@ -23,7 +24,8 @@ struct BatchCone {
 struct BatchArgs {
     BatchCone *cones;
     int n_cones;
-    const int4 *items;     // (cone, ray block, split, -)
+    const int4 *items;     // (cone, ray block, split, -); split -1: the prism records of a
+                           // block of NT bundles
     int64_t n_items;
     const int *rb2cone;    // cone of each padded ray block
     int64_t T;             // padded ray count

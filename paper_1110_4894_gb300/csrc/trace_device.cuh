@@ -135,8 +135,49 @@ __device__ __forceinline__ void init_ray(const TraceParams &tp, const DevField &
 // The sums hold sum m'' / |d| and sum m'' d / |d|^3 (Mpc) with d = particle -
 // point and m'' = mu_G m 2^ms (or the same sums without m'' for a uniform-mass
 // field, mfac = m''): phi = -S0 mfac / 2^ms, grad phi = -S mfac / 2^ms.
+// Bundle prism record (kPrismRec doubles per bundle): the central ray's stage
+// position, and the replica prism's I, grad I and Hessian there.
+// A ray whose offset e from its bundle's central ray is below 1/kPrismNear of
+// the central ray's distance to every face of the prism takes I and grad I
+// from the second-order Taylor expansion about the central ray; the
+// remainder is O(|e|^3 / d) in I and O(|e|^2 / d) in grad I, d the face
+// distance (the prism's third derivatives fall off as 1/d inside), i.e. a
+// relative 1/(2 kPrismNear) of the tidal term H e.  Other rays use the
+// closed form.
+constexpr double kPrismNear = 1000.0;
+
+__device__ __forceinline__ void prism_of_ray(const DevField &f, int rep, const double p[3],
+                                             const double *__restrict__ rec, double I[4])
+{
+    const double lo[3] = {-0.5 * f.L, -0.5 * f.L, (double)rep * f.L};
+    const double hi[3] = {0.5 * f.L, 0.5 * f.L, (double)(rep + 1) * f.L};
+    if (rec) {
+        const double e[3] = {p[0] - rec[0], p[1] - rec[1], p[2] - rec[2]};
+        const double en = sqrt(e[0] * e[0] + e[1] * e[1] + e[2] * e[2]);
+        double d = rec[0] - lo[0];
+        d = fmin(d, hi[0] - rec[0]);
+        d = fmin(d, rec[1] - lo[1]);
+        d = fmin(d, hi[1] - rec[1]);
+        d = fmin(d, rec[2] - lo[2]);
+        d = fmin(d, hi[2] - rec[2]);
+        if (d > kPrismNear * en) {
+            const double *g = rec + 3, *h = rec + 7;  // g = (I, grad I)
+            const double he[3] = {h[0] * e[0] + h[1] * e[1] + h[2] * e[2], h[1] * e[0] + h[3] * e[1] + h[4] * e[2],
+                                  h[2] * e[0] + h[4] * e[1] + h[5] * e[2]};
+            I[0] = g[0] + (g[1] * e[0] + g[2] * e[1] + g[3] * e[2]) +
+                   0.5 * (e[0] * he[0] + e[1] * he[1] + e[2] * he[2]);
+            I[1] = g[1] + he[0];
+            I[2] = g[2] + he[1];
+            I[3] = g[3] + he[2];
+            return;
+        }
+    }
+    prism_field<double>(lo, hi, p, I);
+}
+
+// rec: the bundle's prism record, or null (closed form at p)
 __device__ __forceinline__ void field_from_sums(const DevField &f, const double acc[4], int rep, const double p[3],
-                                                double mfac, double F[4])
+                                                double mfac, double F[4], const double *rec = nullptr)
 {
     const double sp = f.mscale_inv * mfac, sg = sp;
     F[0] = -acc[0] * sp;
@@ -145,15 +186,34 @@ __device__ __forceinline__ void field_from_sums(const DevField &f, const double 
     F[3] = -acc[3] * sg;
     if (f.replicated && f.mean_subtract) {
         // remove the field of the replica's uniform mean density (Sec. 3.3)
-        const double lo[3] = {-0.5 * f.L, -0.5 * f.L, (double)rep * f.L};
-        const double hi[3] = {0.5 * f.L, 0.5 * f.L, (double)(rep + 1) * f.L};
         double I[4];
-        prism_field<double>(lo, hi, p, I);
+        prism_of_ray(f, rep, p, rec, I);
         F[0] += f.rho_term * I[0];
         F[1] += f.rho_term * I[1];
         F[2] += f.rho_term * I[2];
         F[3] += f.rho_term * I[3];
     }
+}
+
+// the prism record of bundle b at its central ray's stage position
+__device__ __forceinline__ void bundle_prism(const DevField &f, const RayState &rs, int g, int64_t b,
+                                             double *__restrict__ rec)
+{
+    const int64_t ic = b * rs.nr, st = rs.stride;
+    const int rep = rs.rep[(g & 1) * rs.n_b + b];
+    const double p[3] = {rs.ys[st + ic], rs.ys[2 * st + ic], rs.ys[3 * st + ic]};
+    const double lo[3] = {-0.5 * f.L, -0.5 * f.L, (double)rep * f.L};
+    const double hi[3] = {0.5 * f.L, 0.5 * f.L, (double)(rep + 1) * f.L};
+    double I[4], h[6];
+    prism_field_hess<double>(lo, hi, p, I, h);
+    double *r = rec + kPrismRec * b;
+    r[0] = p[0];
+    r[1] = p[1];
+    r[2] = p[2];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) r[3 + q] = I[q];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) r[7 + q] = h[q];
 }
 
 // One output of one ray's split partials, as a double-float sum in FP32
@@ -176,7 +236,8 @@ __device__ __forceinline__ double reduce_partials_mixed(const float2 *__restrict
 // Reduce the pair-sum partials of one ray and add the mean subtraction:
 // F = (phi, dphi/dx1, dphi/dx2, dphi/dx3) at the ray's stage position.
 __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64, const void *partials, int64_t n,
-                                             int64_t i, int rep, const double p[3], double mfac, double F[4])
+                                             int64_t i, int rep, const double p[3], double mfac, double F[4],
+                                             const double *rec = nullptr)
 {
     double acc[4] = {0.0, 0.0, 0.0, 0.0};
     if (fp64) {
@@ -203,7 +264,7 @@ __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64
 #pragma unroll
         for (int o = 0; o < 4; ++o) acc[o] = (double)hi[o] + (double)lo[o];
     }
-    field_from_sums(f, acc, rep, p, mfac, F);
+    field_from_sums(f, acc, rep, p, mfac, F, rec);
 }
 
 // d y / d lambda for y = (t, x1, x2, x3, dt/dl, dx1/dl, dx2/dl, dx3/dl):
@@ -243,7 +304,8 @@ __device__ __forceinline__ void geodesic_rhs(const double y[8], const double F[4
 __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField &f, const RayState &rs, int S,
                                           bool fp64, double mfac, const void *__restrict__ partials,
                                           const double *__restrict__ dlam, double chi_s, int step, int stage,
-                                          unsigned long long *cnt, int64_t i, const double *pre = nullptr)
+                                          unsigned long long *cnt, int64_t i, const double *pre = nullptr,
+                                          const double *prism = nullptr)
 {
     const int64_t st = rs.stride;
     const int64_t b = i / rs.nr;
@@ -256,8 +318,9 @@ __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField 
         y[q] = rs.y[q * st + i];
     }
     double F[4];
-    if (pre) field_from_sums(f, pre, rep, ys + 1, mfac, F);
-    else gather_field(f, S, fp64, partials, rs.n_rays, i, rep, ys + 1, mfac, F);
+    const double *rec = prism ? prism + kPrismRec * b : nullptr;
+    if (pre) field_from_sums(f, pre, rep, ys + 1, mfac, F, rec);
+    else gather_field(f, S, fp64, partials, rs.n_rays, i, rep, ys + 1, mfac, F, rec);
     const double a = cosmo_a(tp.cosmo, ys[0]);
     const double ad = cosmo_adot(tp.cosmo, a);
     if (step == 0 && stage == 0) {
