@@ -106,6 +106,10 @@ def lib():
         L.orc_histogram.argtypes = [C.c_int64, _dp, C.POINTER(C.c_int32), C.POINTER(HistOpts),
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _dp]
         L.orc_histogram.restype = C.c_int
+        L.orc_prism_hessian.argtypes = [_dp, _dp, _dp, _dp]
+        L.orc_prism_hessian.restype = None
+        L.orc_born.argtypes = [pc, C.POINTER(Field), C.c_double, C.c_int64, _dp, C.POINTER(TraceOpts), _dp, C.c_int]
+        L.orc_born.restype = C.c_int
         L.orc_shear_histogram.argtypes = [C.c_int64, _dp, _dp, _dp, C.POINTER(C.c_int32), C.POINTER(HistOpts),
                                           C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _dp]
         L.orc_shear_histogram.restype = C.c_int
@@ -315,3 +319,22 @@ def shear_histogram(mu, gamma1, gamma2, flags=None, bins=200, g_min=1e-4, g_max=
         raise ValueError("orc_shear_histogram failed: %d" % rc)
     keys = ("n_used", "n_under", "n_over", "n_neg", "n_bad", "W_total", "mean_w", "sigma_w")
     return counts, wfix, dict(zip(keys, sc))
+
+
+def prism_hessian(lo, hi, r):
+    lo, hi, r = (np.ascontiguousarray(x, np.float64) for x in (lo, hi, r))
+    out = np.zeros(6)
+    lib().orc_prism_hessian(_p(lo), _p(hi), _p(r), _p(out))
+    return out
+
+
+def born(cosmo, field, z_s, theta, schedule=0, n_steps=1000, lens_chi=0.0, asinh_s=1.0, nthreads=None):
+    """Born-approximation (kappa, gamma1, gamma2) per line of sight, (n_b, 3)"""
+    theta = np.ascontiguousarray(theta, np.float64).reshape(-1, 2)
+    o = TraceOpts(4, 1e-6, 0.0, schedule, n_steps, lens_chi, asinh_s, 0, 0)
+    out = np.zeros((theta.shape[0], 3))
+    rc = lib().orc_born(C.byref(cosmo.c), C.byref(field.f), float(z_s), theta.shape[0], _p(theta), C.byref(o),
+                        _p(out), nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("orc_born failed: %d" % rc)
+    return out

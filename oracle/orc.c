@@ -219,6 +219,34 @@ void orc_prism(const double lo[3], const double hi[3], const double r[3], double
     out[3] = gz;
 }
 
+/* second derivatives of the prism integral: the corner function has
+ * d2F/dx2 = -atan(yz/(x r)) and d2F/dxdy = log(z + r) (cyclic); with X =
+ * corner - r the sign of d2/dr2 is that of d2/dX2.  out = (xx, xy, xz, yy,
+ * yz, zz). */
+void orc_prism_hessian(const double lo[3], const double hi[3], const double r[3], double out[6])
+{
+    double X[2] = {lo[0] - r[0], hi[0] - r[0]};
+    double Y[2] = {lo[1] - r[1], hi[1] - r[1]};
+    double Z[2] = {lo[2] - r[2], hi[2] - r[2]};
+    for (int q = 0; q < 6; ++q) out[q] = 0.0;
+    for (int a = 0; a < 2; ++a)
+        for (int b = 0; b < 2; ++b)
+            for (int d = 0; d < 2; ++d) {
+                double sgn = (a ? 1.0 : -1.0) * (b ? 1.0 : -1.0) * (d ? 1.0 : -1.0);
+                double x = X[a], y = Y[b], z = Z[d];
+                double x2 = x * x, y2 = y * y, z2 = z * z, rr = sqrt(x2 + y2 + z2);
+                double txx = x != 0.0 ? -atan(y * z / (x * rr)) : 0.0;
+                double tyy = y != 0.0 ? -atan(z * x / (y * rr)) : 0.0;
+                double tzz = z != 0.0 ? -atan(x * y / (z * rr)) : 0.0;
+                out[0] += sgn * txx;
+                out[1] += sgn * log_a_plus_r(z, rr, x2 + y2);
+                out[2] += sgn * log_a_plus_r(y, rr, x2 + z2);
+                out[3] += sgn * tyy;
+                out[4] += sgn * log_a_plus_r(x, rr, y2 + z2);
+                out[5] += sgn * tzz;
+            }
+}
+
 /* ------------------------------------------------------------------------ */
 /* mass distribution: world positions of a replica (Sec. 5.2)               */
 /* READING: replica j is the box rotated about its centre by a proper 90-   */
@@ -734,5 +762,95 @@ int orc_shear_histogram(int64_t n, const double *mu, const double *g1, const dou
     sc[5] = Wt;
     sc[6] = mean;
     sc[7] = used ? sqrt(nval(S2) / Wt) : 0.0;
+    return 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Born approximation (Sec. 6): convergence and shear along the unperturbed */
+/* line of sight x(chi) = (theta_x chi, theta_y chi, chi).  With A_ij =     */
+/* d_ij - 2 int W d_i d_j psi dchi, W = chi (chi_s - chi) / chi_s, psi =    */
+/* phi / a (Eq. phicotophys):                                               */
+/*   kappa = int W (d11 + d22) psi,  gamma1 = int W (d11 - d22) psi,        */
+/*   gamma2 = 2 int W d12 psi.                                              */
+/* READING: the integral runs over the trace's node table (Eq. RKstepsize   */
+/* reading) by the trapezoid rule in the node variable (uniform in chi, or  */
+/* in u for the asinh nodes chi = chi_l + s sinh u); a(chi) = 1/(1+z(chi)); */
+/* boxes use the replica holding the node, minus the mean-density prism.    */
+/* ------------------------------------------------------------------------ */
+static void hessian_eval(const orc_field *f, const prep_field *pf, int rep, const double *r, double h[6])
+{
+    const double *w = pf->w[f->replicated ? rep : 0];
+    nsum s[6];
+    for (int q = 0; q < 6; ++q) s[q].s = s[q].c = 0.0;
+    for (int64_t i = 0; i < pf->n; ++i) {
+        double d[3] = {r[0] - w[3 * i], r[1] - w[3 * i + 1], r[2] - w[3 * i + 2]};
+        double r2 = d[0] * d[0] + d[1] * d[1] + d[2] * d[2] + pf->eps2[i];
+        double inv = 1.0 / sqrt(r2);
+        double i3 = pf->m[i] * inv * inv * inv, i5 = i3 * inv * inv;
+        /* d_i d_j of -m / r: m (delta_ij / r^3 - 3 d_i d_j / r^5) */
+        nadd(&s[0], i3 - 3.0 * d[0] * d[0] * i5);
+        nadd(&s[1], -3.0 * d[0] * d[1] * i5);
+        nadd(&s[2], -3.0 * d[0] * d[2] * i5);
+        nadd(&s[3], i3 - 3.0 * d[1] * d[1] * i5);
+        nadd(&s[4], -3.0 * d[1] * d[2] * i5);
+        nadd(&s[5], i3 - 3.0 * d[2] * d[2] * i5);
+    }
+    double mu = orc_mu_G();
+    for (int q = 0; q < 6; ++q) h[q] = mu * nval(s[q]);
+    if (f->replicated && f->mean_subtract) {
+        double L = f->L;
+        double lo[3] = {-0.5 * L, -0.5 * L, (double)rep * L};
+        double hi[3] = {0.5 * L, 0.5 * L, (double)(rep + 1) * L};
+        double H[6];
+        orc_prism_hessian(lo, hi, r, H);
+        double k = mu * pf->rho_bar;  /* phi_bg = -mu_G rho I: its Hessian is removed */
+        for (int q = 0; q < 6; ++q) h[q] += k * H[q];
+    }
+}
+
+int orc_born(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b, const double *theta,
+             const orc_trace_opts *o, double *out, int nthreads)
+{
+    if (o->n_steps < 1 || !(z_s > 0.0) || f->grid) return -1;
+    const int n = o->n_steps;
+    const double chi_s = orc_chi(c, z_s);
+    double *x = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    double *dl = (double *)malloc(sizeof(double) * (size_t)n);
+    double *wt = (double *)malloc(sizeof(double) * (size_t)(n + 1));
+    if (!x || !dl || !wt) { free(x); free(dl); free(wt); return -2; }
+    if (orc_schedule(c, chi_s, o->schedule, n, o->lens_chi, o->asinh_s, dl, x) != 0) {
+        free(x); free(dl); free(wt);
+        return -1;
+    }
+    /* trapezoid weights in the node variable times W / a */
+    double du = o->schedule == 1 ? (asinh((chi_s - o->lens_chi) / o->asinh_s) - asinh(-o->lens_chi / o->asinh_s)) / n
+                                 : chi_s / n;
+    for (int k = 0; k <= n; ++k) {
+        double jac = o->schedule == 1 ? sqrt(o->asinh_s * o->asinh_s + (x[k] - o->lens_chi) * (x[k] - o->lens_chi))
+                                      : 1.0;
+        double W = x[k] * (chi_s - x[k]) / chi_s;
+        double inv_a = 1.0 + orc_z_of_chi(c, x[k]);
+        wt[k] = (k == 0 || k == n ? 0.5 : 1.0) * du * jac * W * inv_a;
+    }
+    prep_field pf;
+    if (prep_make(f, &pf) != 0) { prep_free(&pf); free(x); free(dl); free(wt); return -2; }
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
+    for (int64_t b = 0; b < n_b; ++b) {
+        nsum kap = {0, 0}, g1 = {0, 0}, g2 = {0, 0};
+        for (int k = 0; k <= n; ++k) {
+            if (wt[k] == 0.0) continue;
+            double r[3] = {theta[2 * b] * x[k], theta[2 * b + 1] * x[k], x[k]};
+            double h[6];
+            hessian_eval(f, &pf, rep_of(f, x[k]), r, h);
+            nadd(&kap, wt[k] * (h[0] + h[3]));
+            nadd(&g1, wt[k] * (h[0] - h[3]));
+            nadd(&g2, wt[k] * 2.0 * h[1]);
+        }
+        out[3 * b] = nval(kap);
+        out[3 * b + 1] = nval(g1);
+        out[3 * b + 2] = nval(g2);
+    }
+    prep_free(&pf);
+    free(x); free(dl); free(wt);
     return 0;
 }

@@ -101,6 +101,9 @@ int orc_potential(const orc_field *f, int64_t n, const double *pts,
  * out = (I, dI/dx1, dI/dx2, dI/dx3). */
 void orc_prism(const double lo[3], const double hi[3], const double r[3], double out[4]);
 
+/* second derivatives of the same integral: out = (xx, xy, xz, yy, yz, zz) */
+void orc_prism_hessian(const double lo[3], const double hi[3], const double r[3], double out[6]);
+
 /* ---- geodesic right-hand side (Eq. geodesiceqn, App. A) ---------------- */
 /* y = (t, x1, x2, x3, dt/dl, dx1/dl, dx2/dl, dx3/dl); F = (phi, grad phi).
  * christoffel 0: App. A as printed; 1: Gamma^t_ij derived from the metric. */
@@ -145,6 +148,12 @@ typedef struct {
 int orc_histogram(int64_t n, const double *mu, const int32_t *flags,
                   const orc_hist_opts *o, uint64_t *counts, uint64_t *wfix,
                   double *scalars);
+
+/* Born approximation (Sec. 6): kappa, gamma1, gamma2 of n_b lines of sight
+ * theta (n_b*2) from the Hessian of psi along the unperturbed rays, over the
+ * node table of o (schedule, n_steps, lens_chi, asinh_s); out = n_b*3. */
+int orc_born(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b, const double *theta,
+             const orc_trace_opts *o, double *out, int nthreads);
 
 /* shear PDF (Sec. 5.4, Fig. RBMvsMudShear): as orc_histogram, but bins are
  * uniform in log10|gamma|, |gamma| = sqrt(gamma1^2 + gamma2^2), over
