@@ -41,7 +41,7 @@ KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "
 # summarised under profiles/
 PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31): 2130432,
                        ("k_force_bundle2", 128, 196): 2169600 + 68610304,
-                       ("k_force_bundle2x", 64, 131): 2154752 + 34375680}
+                       ("k_force_bundle2x", 64, 131): 2146560 + 24772352}
 
 
 def workload(full=True):
@@ -214,6 +214,42 @@ def run_grid(args):
            "grid_vs_direct_sum": {"median_abs_dmu_over_mu": float(np.median(dmu)),
                                   "max_abs_dmu_over_mu": float(np.max(dmu))},
            "clocks": clocks, "gpu_launches": int(launches)}
+    print(json.dumps(out))
+    return 0
+
+
+def run_born(args):
+    """The Born approximation (Sec. 6) on the NFW workload: kappa and gamma of
+    every bundle centre from the Hessian pair sum at every node of the 2000-
+    step table.  One step = one rt3d_born call (host arrays in and out)."""
+    import torch
+
+    import paper_1110_4894_gb300 as P
+    cfg, name = workload(full=not args.small)
+    kw = dict(schedule=cfg["schedule"], n_steps=cfg["n_steps"], lens_chi=cfg["lens_chi"], asinh_s=cfg["asinh_s"])
+    ctx = P.Context(0, precision=P.MIXED)
+    ctx.set_cosmology(*cfg["cosmo"])
+    ctx.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"])
+    nb = cfg["theta"].shape[0]
+    for _ in range(args.warmup):
+        ctx.born(0, cfg["z_s"], cfg["theta"], **kw)
+    torch.cuda.synchronize()
+    times = []
+    with ClockSampler(0) as clk:
+        for _ in range(args.steps):
+            t0 = time.perf_counter()
+            ctx.born(0, cfg["z_s"], cfg["theta"], **kw)
+            times.append(time.perf_counter() - t0)
+    clocks = clk.summary()
+    pairs = nb * (cfg["n_steps"] + 1) * len(cfg["mass"])
+    t = statistics.mean(times)
+    out = {"metric": "Hessian pair interactions/s (Born approximation)", "value": pairs / t,
+           "unit": "interactions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * t,
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "bundles_per_s": nb / t,
+           "config": {"workload": name + "_born", "bundles": nb, "nodes": cfg["n_steps"] + 1,
+                      "particles": len(cfg["mass"]), "timing": "host wall time of the whole call"},
+           "clocks": clocks}
     print(json.dumps(out))
     return 0
 
@@ -462,7 +498,7 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
-    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid"])
+    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid", "born"])
     ap.add_argument("--grid-n", type=int, default=256, help="nodes per side of the grid workload")
     ap.add_argument("--cones", type=int, default=512)
     ap.add_argument("--cone-steps", type=int, default=16)
@@ -477,6 +513,8 @@ def main():
         return run_cones(args)
     if args.workload == "grid":
         return run_grid(args)
+    if args.workload == "born":
+        return run_born(args)
     return run_ours(args)
 
 

@@ -242,6 +242,20 @@ int rt3d_shear_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const doubl
                          const double *gamma2, const int32_t *flags, const rt3d_hist_opts *o,
                          rt3d_hist *out);
 
+/* Born approximation (Sec. 6): convergence and shear of each line of sight
+ * theta (n_bundles*2) from the Hessian of psi = phi / a along the unperturbed
+ * ray x(chi) = (theta_x chi, theta_y chi, chi):
+ *   kappa = int W (d11 + d22) psi,  gamma1 = int W (d11 - d22) psi,
+ *   gamma2 = 2 int W d12 psi,  W = chi (chi_s - chi) / chi_s,
+ * by the trapezoid rule over the node table of b (schedule, n_steps,
+ * lens_chi, asinh_s; the other fields are not used) in its node variable;
+ * a(chi) = 1 / (1 + z(chi)); boxes use the replica holding each node, minus
+ * the mean-density prism.  out: n_bundles*3 (kappa, gamma1, gamma2), host.
+ * The Hessian sums are FP32 with compensated accumulation, the rest FP64.
+ * Particle fields only (grid fields: RT3D_ENOTIMPL). */
+int rt3d_born(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_bundles, const double *theta,
+              const rt3d_bundle_opts *b, double *out);
+
 /* phi and grad phi (comoving, with mean subtraction when enabled) at n
  * points: out = n*4 (phi, dphi/dx1, dphi/dx2, dphi/dx3).  rep: replica per
  * point (replicated fields; NULL = 0).  Uses the context's precision. */

@@ -107,6 +107,7 @@ def lib(build=True):
                                  C.c_int),
         "rt3d_histogram_device": ([vp, vp, C.c_int64, vp, C.POINTER(HistOpts), vp, vp, vp], C.c_int),
         "rt3d_potential": ([vp, C.c_int, C.c_int64, _dp, _ip, _dp], C.c_int),
+        "rt3d_born": ([vp, C.c_int, C.c_double, C.c_int64, _dp, C.POINTER(BundleOpts), _dp], C.c_int),
         "rt3d_load_grid": ([vp, C.c_int, C.c_int64, _dp, _dp, C.c_double, C.POINTER(GridOpts)], C.c_int),
         "rt3d_grid_nodes": ([vp, C.c_int, _dp], C.c_int),
         "rt3d_schedule": ([vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp], C.c_int),
@@ -211,6 +212,15 @@ class Context:
         if want_rays:
             out["rays"] = rays
             out["steps"] = steps
+        return out
+
+    def born(self, field_id, z_s, theta, **kw):
+        """rt3d_born: Born-approximation (kappa, gamma1, gamma2) per line of sight, (n, 3)."""
+        theta = np.ascontiguousarray(theta, np.float64).reshape(-1, 2)
+        o = self.bundle_opts(**kw)
+        out = np.zeros((theta.shape[0], 3))
+        self._check(self.L.rt3d_born(self.h, int(field_id), float(z_s), theta.shape[0], _p(theta), C.byref(o),
+                                     _p(out)))
         return out
 
     def trace_device(self, stream, field_id, z_s, n_bundles, d_theta, d_bundle_out, d_ray_out=None, **kw):

@@ -1450,6 +1450,38 @@ extern "C" int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out)
     return RT3D_OK;
 }
 
+extern "C" int rt3d_born(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, const double *theta,
+                         const rt3d_bundle_opts *b, double *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
+    if (rc) return rc;
+    if (!theta || !out) return fail(ctx, RT3D_EINVAL, "null theta or output");
+    for (int64_t i = 0; i < 2 * n_b; ++i)
+        if (!isfinite(theta[i])) return fail(ctx, RT3D_EINVAL, "non-finite theta");
+    const FieldSlot &fs = ctx->fields[field_id];
+    if (fs.is_grid) return fail(ctx, RT3D_ENOTIMPL, "the Born approximation takes particle fields");
+    CK(cudaSetDevice(ctx->device));
+    cudaStream_t st = ctx->stream;
+    const int n = b->n_steps;
+    // node chunks of about 2^18 points; particle splits for about five waves
+    const int K = (int)std::max<int64_t>(1, std::min<int64_t>(n + 1, ((int64_t)1 << 18) / n_b));
+    const int64_t blocks = ((int64_t)K * n_b + 511) / 512;
+    const int64_t tiles = std::max<int64_t>(1, (fs.n + kTile - 1) / kTile);
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * 4 * 5 + blocks - 1) / blocks));
+    Scratch &sc = ctx->scr;
+    CK(grow(sc.theta, sc.theta_n, (size_t)(2 * n_b)));
+    CK(grow(sc.bout, sc.bout_n, (size_t)(6 * n_b)));
+    const size_t need = born_scratch_bytes(n_b, n, K, splits);
+    CK(grow(*(char **)&sc.partials, sc.partials_bytes, need));
+    CK(cudaMemcpyAsync(sc.theta, theta, 2 * n_b * sizeof(double), cudaMemcpyHostToDevice, st));
+    CK(born_run(ctx->cosmo, fs.df, fs.n, z_s, n_b, sc.theta, b->schedule, n, b->lens_chi, b->asinh_s, K, splits,
+                sc.partials, sc.bout, st));
+    CK(cudaMemcpyAsync(out, sc.bout, 3 * n_b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    return RT3D_OK;
+}
+
 extern "C" int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const double *pts, const int32_t *rep,
                               double *out)
 {

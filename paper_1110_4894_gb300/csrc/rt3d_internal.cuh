@@ -311,6 +311,13 @@ void grid_free(GridDev &g);
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
                              int mode, void *out, const unsigned long long *gate, cudaStream_t st);
 
+// Born approximation (born.cu): scratch size and the run over node chunks of
+// K nodes with the Hessian pair sum split `splits` ways; d_out = n_b x 3
+size_t born_scratch_bytes(int64_t n_b, int n_steps, int K, int splits);
+cudaError_t born_run(const Cosmo &c, const DevField &f, int64_t n_particles, double z_s, int64_t n_b,
+                     const double *d_theta, int kind, int n_steps, double chi_l, double s, int K, int splits,
+                     void *scratch, double *d_out, cudaStream_t st);
+
 int force_max_splits(const ForceShape &sh, int64_t n_particles);
 size_t partials_bytes(const ForceShape &sh, int64_t n_rays, bool fp64);
 

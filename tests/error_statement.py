@@ -243,7 +243,10 @@ def phase_compare(args):
         row["steps_equal"] = bool(np.array_equal(d[f"{name}/steps"][idx], o.steps))
         pts = d[f"{name}/pts"]
         rep = np.floor(pts[:, 2] / cfg["L"]).astype(np.int32) if cfg.get("replicated") else None
-        row["grad_phi"] = _stat(_grad_rel(d[f"{name}/pot"], oracle.potential(field, pts, rep)))
+        ref_pot = oracle.potential(field, pts, rep)
+        row["grad_phi"] = _stat(_grad_rel(d[f"{name}/pot"], ref_pot))
+        row["grad_phi_rms"] = _stat(np.linalg.norm(d[f"{name}/pot"][:, 1:4] - ref_pot[:, 1:4], axis=1)
+                                    / np.sqrt(np.mean(np.sum(ref_pot[:, 1:4] ** 2, axis=1))))
         if f"{name}/fp64_mu" in d:
             fi = d[f"{name}/fp64_idx"]
             row["mu_vs_gpu_fp64"] = _stat(np.abs(mu_g[fi] / d[f"{name}/fp64_mu"] - 1))
@@ -270,14 +273,15 @@ def _fmt(s, key="max"):
 def _print_table(rows):
     print("| workload | RK4 steps | bundles GPU / oracle | max / p99.9 \\|Δα/α\\| | max \\|Δα\\|/rms α "
           "| max / p99.9 \\|Δμ/μ\\| | \\|Δμ/μ\\| vs GPU FP64 (max) | \\|Δ∇φ\\|/\\|∇φ\\| max / p99.9 "
-          "| control \\|Δμ/μ\\| / \\|Δα/α\\| (max) |")
-    print("|---|---|---|---|---|---|---|---|---|")
+          "| max \\|Δ∇φ\\|/rms ∇φ | control \\|Δμ/μ\\| / \\|Δα/α\\| (max) |")
+    print("|---|---|---|---|---|---|---|---|---|---|")
     for name, r in rows.items():
         nb = "%s / %s" % (r.get("bundles_gpu"), r.get("bundles_oracle", r.get("mu", {}).get("n") if r.get("mu") else "—"))
-        print("| %s | %s | %s | %s / %s | %s | %s / %s | %s | %s / %s | %s / %s |" % (
+        print("| %s | %s | %s | %s / %s | %s | %s / %s | %s | %s / %s | %s | %s / %s |" % (
             name, r["steps"], nb, _fmt(r["alpha"]), _fmt(r["alpha"], "p999"), _fmt(r.get("alpha_rms")),
             _fmt(r["mu"]), _fmt(r["mu"], "p999"), _fmt(r.get("mu_vs_gpu_fp64")), _fmt(r.get("grad_phi")),
-            _fmt(r.get("grad_phi"), "p999"), _fmt(r.get("control_mu")), _fmt(r.get("control_alpha"))))
+            _fmt(r.get("grad_phi"), "p999"), _fmt(r.get("grad_phi_rms")), _fmt(r.get("control_mu")),
+            _fmt(r.get("control_alpha"))))
 
 
 def main():

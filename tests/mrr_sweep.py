@@ -60,7 +60,7 @@ def main():
     import oracle
     import oracle.analytic as A
     import paper_1110_4894_gb300 as P
-    om, ol, h = inputs.COSMO
+    om, ol, h = (0.3, 0.7, 0.7)  # the cosmology of every workload
     cosmo = oracle.Cosmology(om, ol, h)
     g = np.random.default_rng(2024)
     edges = np.logspace(math.log10(0.05), math.log10(2.0), args.bins + 1)
