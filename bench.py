@@ -37,11 +37,11 @@ HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
 KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2",
                 5: "k_force_bundle2x"}
 # dram__bytes_read.sum + dram__bytes_write.sum of one pair-sum launch on this
-# workload, per (kernel, threads per block, splits), from the ncu captures
-# summarised under profiles/
-PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31): 2130432,
-                       ("k_force_bundle2", 128, 196): 2169600 + 68610304,
-                       ("k_force_bundle2x", 64, 131): 2146560 + 24772352}
+# workload, per (kernel, threads per block, splits, cluster size), from the ncu
+# captures summarised under profiles/
+PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31, 1): 2130432,
+                       ("k_force_bundle2", 128, 196, 1): 2169600 + 68610304,
+                       ("k_force_bundle2x", 64, 131, 1): 2146560 + 24772352}
 
 
 def workload(full=True):
@@ -458,7 +458,7 @@ def run_ours(args):
         # DRAM bytes per pair-sum launch from the ncu capture of this kernel
         # (profiles/); null when the launched kernel was not captured
         traffic = None if args.small else PROFILED_DRAM_BYTES.get(
-            (kname, shape["threads_per_block"], shape["splits"]))
+            (kname, shape["threads_per_block"], shape["splits"], shape.get("cluster", 1)))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -469,7 +469,8 @@ def run_ours(args):
                           "l2": "256 MB buffer written between timed steps",
                           "launch_shape": {"rays_per_thread": shape["rays_per_thread"],
                                            "threads_per_block": shape["threads_per_block"],
-                                           "splits": shape["splits"], "kernel": kname}},
+                                           "splits": shape["splits"], "cluster": shape.get("cluster", 1),
+                                           "kernel": kname}},
                "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK / 1e12,
                             "unit": "TFLOP/s", "frac": achieved / FP32_PEAK, "traffic": traffic,
                             "kernel": kname, "flops_per_interaction": FLOPS_PER_INTERACTION,

@@ -138,7 +138,9 @@ typedef struct {
     int steps;            /* RK4 steps issued */
     int rays_per_thread, threads_per_block, splits; /* force launch shape used */
     int variant;          /* pair-sum kernel used: 0 packed, 1 scalar, 2 FP64, 3 bundle, 4 two bundles
-                             per thread, 5 two bundles per thread, expanded separations */
+                             per thread, 5 two bundles per thread, expanded separations, 6 grid path */
+    int cluster;          /* thread-block cluster size along the splits (1: none); the
+                             cluster's splits are added in distributed shared memory */
 } rt3d_stats;
 
 /* One light cone of a batch (Sec. 5): its field, source redshift, bundles and steps. */
@@ -273,6 +275,14 @@ int rt3d_schedule(rt3d_ctx *ctx, double z_s, int kind, int n_steps, double chi_l
  * (n_used, n_under, n_over, n_neg, n_bad, W_total, mean_w, sigma_w). */
 int rt3d_histogram_device(rt3d_ctx *ctx, void *stream, int64_t n, const double *d_bundle_out,
                           const rt3d_hist_opts *o, uint64_t *d_counts, uint64_t *d_wfix, double *d_scalars);
+
+/* Watchdog self-test (the paper has no counterpart): one GPU thread runs the
+ * bounded wait of the persistent kernel's grid barrier on a device word that
+ * nothing changes.  The wait must give up after limit_s (0 < limit_s <= 10)
+ * and report it, leaving the context usable: the call then returns
+ * RT3D_ETIMEOUT, which is the passing outcome; RT3D_ECUDA if the wait ended
+ * any other way. */
+int rt3d_watchdog_selftest(rt3d_ctx *ctx, double limit_s);
 
 /* ---- no-allocation variant ------------------------------------------------
  * rt3d_potential_device_noalloc: phi and grad phi of a loaded field at n

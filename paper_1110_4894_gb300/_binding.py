@@ -59,7 +59,7 @@ class Stats(C.Structure):
     _fields_ = [("interactions", C.c_double), ("device_ms", C.c_double), ("force_ms", C.c_double),
                 ("launches", C.c_int64), ("force_launches", C.c_int64), ("steps", C.c_int),
                 ("rays_per_thread", C.c_int), ("threads_per_block", C.c_int), ("splits", C.c_int),
-                ("variant", C.c_int)]
+                ("variant", C.c_int), ("cluster", C.c_int)]
 
 
 class GridOpts(C.Structure):
@@ -108,6 +108,7 @@ def lib(build=True):
         "rt3d_histogram_device": ([vp, vp, C.c_int64, vp, C.POINTER(HistOpts), vp, vp, vp], C.c_int),
         "rt3d_potential": ([vp, C.c_int, C.c_int64, _dp, _ip, _dp], C.c_int),
         "rt3d_born": ([vp, C.c_int, C.c_double, C.c_int64, _dp, C.POINTER(BundleOpts), _dp], C.c_int),
+        "rt3d_watchdog_selftest": ([vp, C.c_double], C.c_int),
         "rt3d_load_grid": ([vp, C.c_int, C.c_int64, _dp, _dp, C.c_double, C.POINTER(GridOpts)], C.c_int),
         "rt3d_grid_nodes": ([vp, C.c_int, _dp], C.c_int),
         "rt3d_schedule": ([vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp], C.c_int),
@@ -222,6 +223,10 @@ class Context:
         self._check(self.L.rt3d_born(self.h, int(field_id), float(z_s), theta.shape[0], _p(theta), C.byref(o),
                                      _p(out)))
         return out
+
+    def watchdog_selftest(self, limit_s=0.2):
+        """rt3d_watchdog_selftest: returns the status code (ETIMEOUT is the pass)."""
+        return self.L.rt3d_watchdog_selftest(self.h, float(limit_s))
 
     def trace_device(self, stream, field_id, z_s, n_bundles, d_theta, d_bundle_out, d_ray_out=None, **kw):
         """Enqueue a trace on a CUDA stream with device pointers (integers)."""

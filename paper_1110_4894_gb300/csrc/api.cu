@@ -492,6 +492,14 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
     return RT3D_OK;
 }
 
+// a clustered shape needs whole clusters along the splits; splits past the
+// particles are empty and add zeros
+static void round_to_clusters(ForceShape &sh)
+{
+    if (sh.cl > 1 && sh.splits < 2 * sh.cl) sh.cl = 1;  // too few splits to pair up
+    if (sh.cl > 1) sh.splits = (sh.splits + sh.cl - 1) / sh.cl * sh.cl;
+}
+
 // ---------------------------------------------------------------------------
 // launch shape
 // ---------------------------------------------------------------------------
@@ -539,6 +547,9 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
     const int64_t tps = (tiles + S - 1) / S;
     S = (int)((tiles + tps - 1) / tps);
     sh.splits = std::max(1, S);
+    // the expanded two-bundle kernel adds groups of 4 splits in a cluster
+    sh.cl = sh.variant == 5 ? 4 : 1;
+    round_to_clusters(sh);
     return sh;
 }
 
@@ -599,6 +610,7 @@ static ForceShape with_splits(ForceShape sh, int64_t n_points, int64_t n_particl
     S = std::min(S, tiles);
     const int64_t tps = (tiles + S - 1) / S;
     sh.splits = (int)std::max<int64_t>(1, (tiles + tps - 1) / tps);
+    round_to_clusters(sh);
     return sh;
 }
 
@@ -621,11 +633,12 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     std::vector<int> waves;
     const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
     const int rn64[][2] = {{2, 128}, {1, 128}};
-    // bundle shapes: {variant, bundles per block}
-    const int rnb[][3] = {{3, group, 128}, {3, group, 64}, {3, group, 256}, {4, group, 64},
-                          {4, group, 128}, {5, group, 64}, {5, group, 128}};
+    // bundle shapes: {variant, rays per bundle, threads per block, cluster size}
+    const int rnb[][4] = {{3, group, 128, 1}, {3, group, 64, 1}, {3, group, 256, 1}, {4, group, 64, 1},
+                          {4, group, 128, 1}, {5, group, 64, 1}, {5, group, 128, 1}, {5, group, 64, 4},
+                          {5, group, 128, 4}};
     const bool bundles = base.variant >= 3;
-    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 7 : 3) : 4);
+    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 9 : 3) : 4);
     for (int c = 0; c < nrn; ++c)
         for (int w : {2, 3, 5, 8}) {
             ForceShape s = base;
@@ -635,6 +648,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
                 s.variant = rnb[c][0];
                 s.R = rnb[c][1];
                 s.NT = rnb[c][2];
+                s.cl = rnb[c][3];
             } else {
                 const int *p = base.variant == 2 ? rn64[c] : rn[c];
                 s.R = p[0];
@@ -657,15 +671,17 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     size_t bi = 0;
     for (size_t c = 0; c < cand.size(); ++c) {
         CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
-        CK(cudaEventRecord(e0, st));
-        CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
-        CK(cudaEventRecord(e1, st));
-        CK(cudaEventSynchronize(e1));
-        float ms = 0.0f;
-        CK(cudaEventElapsedTime(&ms, e0, e1));
-        if (ms < best) {
-            best = ms;
-            bi = c;
+        for (int rep_t = 0; rep_t < 3; ++rep_t) {  // best of three: candidates are often within 1-2 %
+            CK(cudaEventRecord(e0, st));
+            CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
+            CK(cudaEventRecord(e1, st));
+            CK(cudaEventSynchronize(e1));
+            float ms = 0.0f;
+            CK(cudaEventElapsedTime(&ms, e0, e1));
+            if (ms < best) {
+                best = ms;
+                bi = c;
+            }
         }
     }
     cudaEventDestroy(e0);
@@ -822,6 +838,7 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     ctx->stats.rays_per_thread = sh.R;
     ctx->stats.threads_per_block = sh.NT;
     ctx->stats.splits = sh.splits;
+    ctx->stats.cluster = sh.cl;
     ctx->stats.variant = sh.variant;
     // grid path: one field evaluation per ray and stage counts as one
     ctx->last_npart = fs.is_grid ? 1.0 : (double)fs.n;
@@ -1150,6 +1167,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     ctx->stats.rays_per_thread = (nr == 5 || nr == 9) ? nr : 2 * P;
     ctx->stats.threads_per_block = NT;
     ctx->stats.variant = (nr == 5 || nr == 9) ? 3 : 0;
+    ctx->stats.cluster = 1;
     ctx->stats.splits = (int)per_item;
     ctx->stats.force_ms = ms;
     ctx->stats_pending = false;
@@ -1480,6 +1498,25 @@ extern "C" int rt3d_born(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, c
     CK(cudaMemcpyAsync(out, sc.bout, 3 * n_b * sizeof(double), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     return RT3D_OK;
+}
+
+extern "C" int rt3d_watchdog_selftest(rt3d_ctx *ctx, double limit_s)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (!(limit_s > 0.0) || limit_s > 10.0) return fail(ctx, RT3D_EINVAL, "limit must be in (0, 10] s");
+    CK(cudaSetDevice(ctx->device));
+    unsigned *d = nullptr;
+    CK(cudaMalloc(&d, 2 * sizeof(unsigned)));
+    cudaStream_t st = ctx->stream;
+    cudaError_t e = cudaMemsetAsync(d, 0, 2 * sizeof(unsigned), st);
+    if (e == cudaSuccess) e = launch_watchdog_probe(d, (int *)(d + 1), limit_s, st);
+    int err = 0;
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&err, d + 1, sizeof err, cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    cudaFree(d);
+    CK(e);
+    if (err) return fail(ctx, RT3D_ETIMEOUT, "watchdog self-test: the bounded wait expired as intended");
+    return fail(ctx, RT3D_ECUDA, "watchdog self-test: the wait ended without the watchdog");
 }
 
 extern "C" int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const double *pts, const int32_t *rep,

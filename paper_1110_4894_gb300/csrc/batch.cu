@@ -24,6 +24,24 @@ __device__ __forceinline__ unsigned long long global_ns()
     return t;
 }
 
+// Wait until *word differs from old; give up when *err is set or limit_ns
+// has elapsed (then set *err, so every other waiter stops too).  True if
+// the word changed.
+__device__ __forceinline__ bool bounded_wait(const volatile unsigned *word, unsigned old, int *err,
+                                             unsigned long long limit_ns)
+{
+    const unsigned long long t0 = global_ns();
+    while (*word == old) {
+        if (*(volatile int *)err) return false;
+        if (global_ns() - t0 > limit_ns) {
+            atomicExch(err, 1);
+            return false;
+        }
+        __nanosleep(128);
+    }
+    return true;
+}
+
 // Grid-wide barrier of a cooperative launch; every wait is bounded.
 __device__ __forceinline__ bool grid_sync(const BatchArgs &B)
 {
@@ -37,20 +55,25 @@ __device__ __forceinline__ bool grid_sync(const BatchArgs &B)
             __threadfence();
             atomicAdd(B.bar + 1, 1u);
         } else {
-            const unsigned long long t0 = global_ns();
-            while (*gen == g0) {
-                if (*(volatile int *)B.err) break;
-                if (global_ns() - t0 > B.limit_ns) {
-                    atomicExch(B.err, 1);
-                    break;
-                }
-                __nanosleep(128);
-            }
+            bounded_wait(gen, g0, B.err, B.limit_ns);
         }
         __threadfence();
     }
     __syncthreads();
     return *(volatile int *)B.err == 0;
+}
+
+// Watchdog check: one thread waits, with the barrier's bounded wait, on a
+// word that nothing changes; the wait must end after limit_ns with *err set.
+__global__ void k_watchdog_probe(unsigned *word, int *err, unsigned long long limit_ns)
+{
+    bounded_wait(word, *(volatile unsigned *)word, err, limit_ns);
+}
+
+cudaError_t launch_watchdog_probe(unsigned *d_word, int *d_err, double limit_s, cudaStream_t st)
+{
+    k_watchdog_probe<<<1, 1, 0, st>>>(d_word, d_err, (unsigned long long)(limit_s * 1e9));
+    return cudaGetLastError();
 }
 
 __device__ __forceinline__ bool cone_active(const BatchCone &C, int step)

@@ -59,6 +59,8 @@ inline BatchArgs make_batch_args(void *cones, int n_cones, const int4 *items, in
 
 // MODE: 4 or 8 = bundle-centric pair sum for rings of that size, 0 = packed
 cudaError_t batch_resident_blocks(int NT, int MODE, int *out);
+// one bounded wait on a word nothing changes (the watchdog self-test)
+cudaError_t launch_watchdog_probe(unsigned *d_word, int *d_err, double limit_s, cudaStream_t st);
 cudaError_t batch_launch(const BatchArgs &B, int NT, int MODE, int grid, int max_sched_steps, int64_t n_b_total,
                          cudaStream_t st);
 

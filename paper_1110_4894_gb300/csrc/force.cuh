@@ -18,11 +18,14 @@
 // * Block (x = ray block, y = particle split) writes (hi, lo) per output to
 //   partials[split][output][ray]; the integrator stage adds them in FP64.
 #pragma once
+#include <cooperative_groups.h>
 #include <limits.h>
 
 #include "rt3d_internal.cuh"
 
 namespace rt3d {
+
+namespace cg = cooperative_groups;
 
 constexpr int kTile = 256;
 constexpr int kTile64 = 128;
@@ -724,7 +727,7 @@ __global__ void __launch_bounds__(NT, 384 / NT) k_force_bundle2(ForceArgs A)
 // 56 f32x2 operations for 10 interactions (the unexpanded kernel: 60).
 // (Taking 1/r^2 from MUFU rcp instead of rsqrt^2 saves 5 more but was
 // measured 26 % slower: the MUFU pipe then limits.)
-template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int CL>
 __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const double *__restrict__ px,
                                                    const double *__restrict__ py, const double *__restrict__ pz,
                                                    const int *__restrict__ rep, int64_t n_b, int64_t n_rays,
@@ -890,16 +893,18 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
         }
     }
     // gradient of ring ray k: G_k + e_k S_k, as an FP32 (hi, lo) pair (the
-    // product's rounding error recovered by an FMA, the sum by TwoSum)
-    const int64_t sn = (int64_t)split * 4;
+    // product's rounding error recovered by an FMA, the sum by TwoSum).
+    // Outputs per thread: slot g (< NR) holds (phi_A, phi_B) of ray g, slot
+    // NR + (h NR + g) 3 + o - 1 the (hi, lo) of gradient component o of ray g
+    // of bundle h.
+    constexpr int NSLOT = NR + 2 * NR * 3;
+    float2 res[NSLOT];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        if (!valid[h]) continue;
-        const int64_t ic = bb[h] * NR;
+    for (int g = 0; g < NR; ++g) res[g] = phi[g];
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
 #pragma unroll
         for (int g = 0; g < NR; ++g) {
-            const int64_t i = ic + g;
-            out[(sn + 0) * n_rays + i] = make_float2(h ? phi[g].y : phi[g].x, 0.f);
             float shi = 0.f, slo = 0.f;
             if (g > 0) {
                 const float2 a = s_hi[(NR * 3 + g - 1) * NT + tid], c = s_lo[(NR * 3 + g - 1) * NT + tid];
@@ -916,21 +921,77 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
                     const float e = 0.5f * (h ? f2.y : f2.x);
                     const float p = e * shi;
                     const float pe = fmaf(e, shi, -p);
-                    const float s = hi + p;
-                    const float bv = s - hi;
-                    const float err = (hi - (s - bv)) + (p - bv);
+                    const float sm = hi + p;
+                    const float bv = sm - hi;
+                    const float err = (hi - (sm - bv)) + (p - bv);
                     lo = lo + (err + fmaf(e, slo, pe));
-                    hi = s;
+                    hi = sm;
                 }
-                out[(sn + 1 + oo) * n_rays + i] = make_float2(hi, lo);
+                res[NR + (h * NR + g) * 3 + oo] = make_float2(hi, lo);
             }
         }
+    if (CL == 1) {
+        const int64_t sn = (int64_t)split * 4;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!valid[h]) continue;
+            const int64_t ic = bb[h] * NR;
+#pragma unroll
+            for (int g = 0; g < NR; ++g) {
+                out[(sn + 0) * n_rays + ic + g] = make_float2(h ? res[g].y : res[g].x, 0.f);
+#pragma unroll
+                for (int oo = 0; oo < 3; ++oo) out[(sn + 1 + oo) * n_rays + ic + g] = res[NR + (h * NR + g) * 3 + oo];
+            }
+        }
+        return;
     }
+    // cluster of CL blocks (consecutive splits of the same bundle block): the
+    // partials are added in distributed shared memory, in rank order, and one
+    // partial per cluster is written (split / CL)
+    static_assert(NSLOT <= 2 * (NR * 3 + NRING), "outputs must fit the (hi, lo) buffer");
+    __syncthreads();  // every thread has read its (hi, lo) sums
+#pragma unroll
+    for (int q = 0; q < NSLOT; ++q) s_hl[q * NT + tid] = res[q];
+    cg::cluster_group cluster = cg::this_cluster();
+    cluster.sync();
+    const int rank = (int)cluster.block_rank();
+    constexpr int TPR = NT / CL;  // threads' outputs each rank reduces
+    const int64_t sn = (int64_t)(split / CL) * 4;
+    for (int it = tid; it < NSLOT * TPR; it += NT) {
+        const int q = it / TPR, t = rank * TPR + it % TPR;
+        float hx = 0.f, lx = 0.f, hy = 0.f, ly = 0.f;
+#pragma unroll
+        for (int r = 0; r < CL; ++r) {
+            const float2 v = cluster.map_shared_rank(s_hl, r)[q * NT + t];
+            if (q < NR) {  // potential of bundles A and B: plain sums
+                hx += v.x;
+                hy += v.y;
+            } else {  // (hi, lo) gradient: TwoSum on the high parts
+                const float sm = hx + v.x;
+                const float bv = sm - hx;
+                lx += ((hx - (sm - bv)) + (v.x - bv)) + v.y;
+                hx = sm;
+            }
+        }
+        if (q < NR) {
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+                const int64_t bh = b0 + h * NT + t;
+                if (bh < n_b) out[sn * n_rays + bh * NR + q] = make_float2(h ? hy : hx, 0.f);
+            }
+        } else {
+            const int k = q - NR, h = k / (NR * 3), g = (k / 3) % NR, oo = k % 3;
+            const int64_t bh = b0 + h * NT + t;
+            if (bh < n_b) out[(sn + 1 + oo) * n_rays + bh * NR + g] = make_float2(hx, lx);
+        }
+        (void)ly;
+    }
+    cluster.sync();  // no block leaves while the others read its shared memory
 }
 
 // TPSM: resident threads per SM the register allocation is bounded for (384:
 // 168 registers, with some spilling; 256: no spills)
-template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM>
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM, int CL>
 __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
 {
     if (A.gate && *A.gate == 0ull) return;
@@ -943,7 +1004,7 @@ __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
     const int split = blockIdx.y;
     const int64_t p0 = (int64_t)split * A.per_split;
     const int64_t p1 = min(A.f.n, p0 + A.per_split);
-    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
+    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS, CL>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
                                                      (float2 *)A.out, s_a, s_b, s_e, s_hl);
 }
 

@@ -4,31 +4,58 @@
 
 namespace rt3d {
 
+template <int NT, bool UMASS, bool REPL, bool PEPS, int T, int CL>
+static cudaError_t go_one(const ForceArgs &A, dim3 grid, cudaStream_t st)
+{
+    if (CL == 1) {
+        k_force_bundle2x<NT, 4, REPL, PEPS, UMASS, T, 1><<<grid, NT, 0, st>>>(A);
+        return cudaGetLastError();
+    }
+    // thread-block clusters of CL consecutive splits of one bundle block
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = dim3(NT);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 1;
+    attr[0].val.clusterDim.y = CL;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, k_force_bundle2x<NT, 4, REPL, PEPS, UMASS, T, CL>, A);
+}
+
 // 64-thread blocks are bounded for 6 blocks per SM (168 registers), 128-thread
 // blocks for 2 (no spills): the tuner times both register regimes
-template <int NT, bool UMASS>
+template <int NT, bool UMASS, int CL>
 static cudaError_t go_bundle2x(const ForceArgs &A, dim3 grid, cudaStream_t st)
 {
     constexpr int T = NT == 64 ? 384 : 256;
     const bool repl = A.f.replicated != 0, peps = A.f.eps2 != nullptr;
-    if (repl && peps) k_force_bundle2x<NT, 4, true, true, UMASS, T><<<grid, NT, 0, st>>>(A);
-    else if (repl) k_force_bundle2x<NT, 4, true, false, UMASS, T><<<grid, NT, 0, st>>>(A);
-    else if (peps) k_force_bundle2x<NT, 4, false, true, UMASS, T><<<grid, NT, 0, st>>>(A);
-    else k_force_bundle2x<NT, 4, false, false, UMASS, T><<<grid, NT, 0, st>>>(A);
-    return cudaGetLastError();
+    if (repl && peps) return go_one<NT, UMASS, true, true, T, CL>(A, grid, st);
+    if (repl) return go_one<NT, UMASS, true, false, T, CL>(A, grid, st);
+    if (peps) return go_one<NT, UMASS, false, true, T, CL>(A, grid, st);
+    return go_one<NT, UMASS, false, false, T, CL>(A, grid, st);
 }
 
-// rings of 4: grid.x counts blocks of 2 NT bundles
+// rings of 4: grid.x counts blocks of 2 NT bundles, grid.y the splits (a
+// multiple of sh.cl)
 cudaError_t dispatch_bundle2x(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st)
 {
     const int64_t n_b = A.n / 5;
     const dim3 grid((unsigned)((n_b + 2 * sh.NT - 1) / (2 * sh.NT)), (unsigned)sh.splits);
-    if (sh.R != 5) return cudaErrorInvalidConfiguration;
-    switch (sh.NT * 2 + (umass ? 1 : 0)) {
-    case 128: return go_bundle2x<64, false>(A, grid, st);
-    case 129: return go_bundle2x<64, true>(A, grid, st);
-    case 256: return go_bundle2x<128, false>(A, grid, st);
-    case 257: return go_bundle2x<128, true>(A, grid, st);
+    if (sh.R != 5 || sh.splits % sh.cl != 0) return cudaErrorInvalidConfiguration;
+    switch ((sh.NT * 2 + (umass ? 1 : 0)) * 8 + sh.cl) {
+    case 128 * 8 + 1: return go_bundle2x<64, false, 1>(A, grid, st);
+    case 129 * 8 + 1: return go_bundle2x<64, true, 1>(A, grid, st);
+    case 256 * 8 + 1: return go_bundle2x<128, false, 1>(A, grid, st);
+    case 257 * 8 + 1: return go_bundle2x<128, true, 1>(A, grid, st);
+    case 128 * 8 + 4: return go_bundle2x<64, false, 4>(A, grid, st);
+    case 129 * 8 + 4: return go_bundle2x<64, true, 4>(A, grid, st);
+    case 256 * 8 + 4: return go_bundle2x<128, false, 4>(A, grid, st);
+    case 257 * 8 + 4: return go_bundle2x<128, true, 4>(A, grid, st);
     default: return cudaErrorInvalidConfiguration;
     }
 }

@@ -118,7 +118,7 @@ cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, 
                          unsigned long long *d_counters, cudaStream_t st, const double *d_prism)
 {
     const int64_t blocks = (rs.n_rays + kStageRays - 1) / kStageRays;
-    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh),
+    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, partial_splits(sh), fp64 ? 1 : 0, partial_mass_factor(f, sh),
                                              d_partials, d_dlam, d_misc, step, stage, d_counters, d_prism);
     return cudaGetLastError();
 }
@@ -142,7 +142,7 @@ cudaError_t launch_stage_field(const DevField &f, const ForceShape &sh, bool fp6
 {
     const int64_t blocks = (n + 255) / 256;
     k_field_points<<<(unsigned)(blocks > 0 ? blocks : 1), 256, 0, st>>>(
-        f, sh.splits, fp64 ? 1 : 0, partial_mass_factor(f, sh), d_partials, d_pts, d_rep, n, d_out);
+        f, partial_splits(sh), fp64 ? 1 : 0, partial_mass_factor(f, sh), d_partials, d_pts, d_rep, n, d_out);
     return cudaGetLastError();
 }
 

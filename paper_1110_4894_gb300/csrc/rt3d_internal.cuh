@@ -230,10 +230,14 @@ struct TraceParams {
 struct ForceShape {
     int R;        // rays per thread
     int NT;       // threads per block
-    int splits;   // particle splits
-    int variant;  // 0 packed FP32x2, 1 scalar FP32, 2 FP64
+    int splits;   // particle splits (blocks along y)
+    int variant;  // 0 packed FP32x2, 1 scalar FP32, 2 FP64, 3-5 bundle-centric, 6 grid path
     int umass;    // packed kernel without per-particle masses (uniform-mass field)
+    int cl = 1;   // thread-block cluster size along the splits: the cluster adds its
+                  // CTAs' partials in distributed shared memory, one partial per cluster
 };
+// split partials a shape leaves for the integrator stage
+inline int partial_splits(const ForceShape &sh) { return sh.splits / sh.cl; }
 
 // device scratch of a trace (grow-only, owned by the context)
 struct Scratch {

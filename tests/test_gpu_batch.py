@@ -111,3 +111,23 @@ def test_batch_isolated_and_mixed_fields(cosmo):
     o1 = oracle.trace(cosmo, fb, b["z_s"], b["theta"], n_steps=60, **kw)
     assert rel_mu(res[0]["mu"], o0.mu).max() < 1e-4
     assert rel_mu(res[1]["mu"], o1.mu).max() < 1e-4
+
+
+def test_watchdog_expires_and_context_survives(batch_case):
+    # failure detection without a GPU fault: the persistent kernel's bounded
+    # barrier wait, run on a word nothing sets, gives up after its limit and
+    # reports ETIMEOUT; the context then still traces
+    import time
+
+    import paper_1110_4894_gb300 as P
+    cfg, orc = batch_case
+    ctx = P.Context(0, precision=P.MIXED)
+    ctx.set_cosmology(*cfg["cosmo"])
+    t0 = time.perf_counter()
+    rc = ctx.watchdog_selftest(0.2)
+    dt = time.perf_counter() - t0
+    assert rc == P._binding.ETIMEOUT
+    assert 0.19 < dt < 5.0
+    cones = _load(ctx, cfg)
+    res = ctx.trace_batch(cones, n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0)
+    assert rel_mu(res[0]["mu"], orc[0].mu).max() < 1e-4

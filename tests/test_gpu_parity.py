@@ -270,6 +270,28 @@ def test_errors_are_reported(P):
         ctx.trace(0, 0.5, np.full((1, 2), np.nan))
 
 
+@pytest.mark.parametrize("splits", [12, 16])
+def test_clustered_split_reduction(P, cosmo, splits):
+    # the expanded two-bundle kernel adds groups of 4 splits in a thread-block
+    # cluster (distributed shared memory); 20 tiles in 12 requested splits
+    # leave two empty splits in the last cluster
+    cfg = _c2_small(n_particles=5000, n_side=4, n_steps=120)
+    ctx = ctx_for(P, P.MIXED, variant=5, splits=splits)
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    st = ctx.stats()
+    assert st["cluster"] == 4 and st["splits"] % 4 == 0 and st["variant"] == 5
+    o = run_oracle(cfg, cfg["theta"], cosmo)
+    assert np.array_equal(g["flags"], o.flags)
+    assert rel_mu(g["mu"], o.mu).max() < 1e-4
+    assert rel_alpha(g["rays"], o).max() < 1e-5
+    c1 = ctx_for(P, P.MIXED, variant=4, splits=splits)  # no cluster: same sums in another order
+    gpu_load(c1, 0, cfg)
+    g1 = c1.trace(0, cfg["z_s"], cfg["theta"], **trace_kw(cfg))
+    assert c1.stats()["cluster"] == 1
+    assert np.max(np.abs(g["mu"] / g1["mu"] - 1)) < 1e-5
+
+
 def test_autotuned_shape_keeps_parity(P, cosmo):
     cfg = _c2_small(n_particles=8000, n_side=4, n_steps=120)
     ctx = ctx_for(P, P.MIXED, autotune=1)
