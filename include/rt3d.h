@@ -79,6 +79,9 @@ typedef struct {
                               1 = scalar FP32, 2 = packed FP32x2 per ray, 3 = one bundle per thread,
                               4 = two bundles per thread (rings of 4), 5 = as 4 with the ring
                               separations expanded about the central ray */
+    int cluster;           /* variant 5: 4 = thread-block clusters of 4 splits add their partials in
+                              distributed shared memory, 1 = no clusters, 0 = automatic (none unless
+                              the autotuner finds clusters faster) */
 } rt3d_options;
 
 /* Mass distribution layout.

@@ -22,7 +22,8 @@ class Rt3dError(RuntimeError):
 class Options(C.Structure):
     _fields_ = [("precision", C.c_int), ("christoffel", C.c_int), ("rays_per_thread", C.c_int),
                 ("threads_per_block", C.c_int), ("splits", C.c_int), ("autotune", C.c_int),
-                ("watchdog_s", C.c_double), ("time_kernels", C.c_int), ("variant", C.c_int)]
+                ("watchdog_s", C.c_double), ("time_kernels", C.c_int), ("variant", C.c_int),
+                ("cluster", C.c_int)]
 
 
 class Volume(C.Structure):
@@ -132,11 +133,11 @@ class Context:
     """One library context on one CUDA device (rt3d_create ... rt3d_destroy)."""
 
     def __init__(self, device=0, precision=MIXED, christoffel=CHRISTOFFEL_PAPER, rays_per_thread=0,
-                 threads_per_block=0, splits=0, autotune=0, watchdog_s=0.0, time_kernels=0, variant=0):
+                 threads_per_block=0, splits=0, autotune=0, watchdog_s=0.0, time_kernels=0, variant=0, cluster=0):
         self.L = lib()
         self.h = C.c_void_p()
         self.opt = Options(precision, christoffel, rays_per_thread, threads_per_block, splits, autotune,
-                           watchdog_s, time_kernels, variant)
+                           watchdog_s, time_kernels, variant, cluster)
         rc = self.L.rt3d_create(C.byref(self.h), int(device), C.byref(self.opt))
         if rc != OK:
             raise Rt3dError(rc, self.L.rt3d_status_string(rc).decode())

@@ -259,6 +259,10 @@ extern "C" int rt3d_create(rt3d_ctx **out, int dev, const rt3d_options *opt)
         delete ctx;
         return RT3D_EINVAL;
     }
+    if (ctx->opt.cluster != 0 && ctx->opt.cluster != 1 && ctx->opt.cluster != 4) {
+        delete ctx;
+        return RT3D_EINVAL;
+    }
     ctx->fields.resize(RT3D_MAX_FIELDS);
     int rc = RT3D_OK;
     do {
@@ -547,8 +551,9 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
     const int64_t tps = (tiles + S - 1) / S;
     S = (int)((tiles + tps - 1) / tps);
     sh.splits = std::max(1, S);
-    // the expanded two-bundle kernel adds groups of 4 splits in a cluster
-    sh.cl = sh.variant == 5 ? 4 : 1;
+    // the expanded two-bundle kernel can add groups of 4 splits in a cluster
+    // (off unless asked for: measured slower on the NFW workload, see the tuner)
+    sh.cl = (sh.variant == 5 && ctx->opt.cluster == 4) ? 4 : 1;
     round_to_clusters(sh);
     return sh;
 }
@@ -642,8 +647,9 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     for (int c = 0; c < nrn; ++c)
         for (int w : {2, 3, 5, 8}) {
             ForceShape s = base;
-            // a requested bundle kernel is tuned over its own shapes only
+            // a requested bundle kernel (or cluster size) is tuned over its own shapes only
             if (bundles && ctx->opt.variant >= 3 && rnb[c][0] != base.variant) continue;
+            if (bundles && ctx->opt.cluster > 0 && rnb[c][3] != ctx->opt.cluster) continue;
             if (bundles) {
                 s.variant = rnb[c][0];
                 s.R = rnb[c][1];

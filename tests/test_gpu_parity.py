@@ -276,7 +276,7 @@ def test_clustered_split_reduction(P, cosmo, splits):
     # cluster (distributed shared memory); 20 tiles in 12 requested splits
     # leave two empty splits in the last cluster
     cfg = _c2_small(n_particles=5000, n_side=4, n_steps=120)
-    ctx = ctx_for(P, P.MIXED, variant=5, splits=splits)
+    ctx = ctx_for(P, P.MIXED, variant=5, splits=splits, cluster=4)
     gpu_load(ctx, 0, cfg)
     g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
     st = ctx.stats()
