@@ -378,6 +378,9 @@ def run_ours(args):
     nb = cfg["theta"].shape[0]
     nr = 1 + cfg["n_ring"]
     npart = len(cfg["mass"])
+    if ws > 1:  # weak scaling: every rank traces its own lines of sight of the same halo
+        from paper_1110_4894_gb300.shard import rank_lines_of_sight
+        cfg["theta"] = rank_lines_of_sight(cfg["theta"], rank)
 
     ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=1, variant=args.variant)
     ctx.set_cosmology(*cfg["cosmo"])
@@ -428,6 +431,16 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.all_reduce(t_rank, op=torch.distributed.ReduceOp.MAX)
     t_max = float(t_rank.item())
+    # the muPDF of all ranks' bundles (outside the timed region): one exchange
+    # of two integer vectors and seven sums
+    from paper_1110_4894_gb300.shard import allreduce_histogram
+    keys = ("n_used", "n_under", "n_over", "n_neg", "n_bad", "W_total", "mean_w", "sigma_w")
+    sc = dict(zip(keys, d_scal.cpu().numpy().tolist()))
+    hc, hw = d_counts.cpu().numpy().astype(np.uint64), d_wfix.cpu().numpy().view(np.uint64)
+    if ws > 1:
+        hc, hw, sc = allreduce_histogram(hc, hw, sc, device=dev)
+    mupdf = {"bundles_binned": int(sc["n_used"]), "mean_w": sc["mean_w"], "sigma_w": sc["sigma_w"],
+             "bins": HIST["bins"], "mu_range": [HIST["mu_min"], HIST["mu_max"]], "ranks": ws}
     total_inter = inter * ws
     value = total_inter / t_max
     bundles_s = nb * args.steps * ws / t_max
@@ -479,6 +492,7 @@ def run_ours(args):
                "clocks": clocks,
                "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
                "gpu_launches": int(launches),
+               "mupdf": mupdf,
                "wall_s": wall}
         if not args.no_cpu:
             out["cpu_baseline"] = cpu_baseline(cfg, n_steps=args.cpu_steps)
