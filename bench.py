@@ -41,7 +41,8 @@ KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "
 # captures summarised under profiles/
 PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31, 1): 2130432,
                        ("k_force_bundle2", 128, 196, 1): 2169600 + 68610304,
-                       ("k_force_bundle2x", 64, 131, 1): 2146560 + 24772352}
+                       ("k_force_bundle2", 64, 131, 1): 2131456 + 24840704,
+                       ("k_force_bundle2x", 64, 131, 1): 2139136 + 25478144}
 
 
 def workload(full=True):
@@ -249,6 +250,72 @@ def run_born(args):
            "bundles_per_s": nb / t,
            "config": {"workload": name + "_born", "bundles": nb, "nodes": cfg["n_steps"] + 1,
                       "particles": len(cfg["mass"]), "timing": "host wall time of the whole call"},
+           "clocks": clocks}
+    print(json.dumps(out))
+    return 0
+
+
+def run_box(args):
+    """A cosmological box over a fixed window of RK4 steps: the 2^21-particle
+    100/h Mpc box (z_s = 0.5, all 256^2 bundles) or the 2^24-particle 200/h
+    Mpc box (z_s = 1, a patch of --box-bundles of its 1024^2 bundles),
+    replicated with random rotations and shifts and mean subtraction.  A
+    converged trace to z_s takes thousands of steps (hours for the larger
+    box); every RK4 step costs the same pair-sum work whatever its length, so
+    the rate is measured on a trace with a short uniform table of
+    --rk4-steps steps (default 4)."""
+    import torch
+
+    import inputs
+    import paper_1110_4894_gb300 as P
+    big = args.workload == "box5"
+    steps = args.rk4_steps or 4
+    cfg = inputs.config_c5(n_steps=1000) if big else inputs.config_c3(n_steps=1000)
+    theta = cfg["theta"][:args.box_bundles] if big else cfg["theta"]
+    nb = theta.shape[0]
+    ctx = P.Context(0, precision=P.MIXED, time_kernels=1, autotune=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    ctx.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"], replicated=True, box_length=cfg["L"],
+                       rot=cfg["rot"], shift=cfg["shift"], mean_subtract=True)
+    # no extra steps: rays still short of the source plane after the window
+    # would cost whole pair-sum launches for the few of them that count
+    kw = dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0, n_steps=steps, max_extra=0)
+    dev = torch.device("cuda", 0)
+    d_theta = torch.from_numpy(np.ascontiguousarray(theta)).to(dev)
+    d_bout = torch.zeros(nb * 6, dtype=torch.float64, device=dev)
+    sp = torch.cuda.current_stream(dev).cuda_stream
+    kw_w = kw
+    for _ in range(args.warmup):
+        ctx.trace_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), d_bout.data_ptr(), **kw_w)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    inter, force_ms, force_launches = 0.0, 0.0, 0
+    stream = torch.cuda.current_stream(dev)
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            ctx.trace_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), d_bout.data_ptr(), **kw_w)
+            ev[k][1].record(stream)
+            st = ctx.stats()
+            inter += st["interactions"]
+            force_ms += st["force_ms"]
+            force_launches += st["force_launches"]
+    clocks = clk.summary()
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    per_launch = inter / max(1, force_launches)
+    avg = force_ms / 1e3 / max(1, force_launches)
+    out = {"metric": METRIC, "value": inter / dev_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "config": {"workload": ("box_2e24p_200mpch" if big else "box_2e21p_100mpch") +
+                      "_%db_%dsteps_window" % (nb, steps), "particles": len(cfg["mass"]), "bundles": nb,
+                      "replicas": int(cfg["n_rep"]), "rk4_steps_timed": steps,
+                      "step_mpc": float(ctx.schedule(cfg["z_s"], 0, steps)[1] / steps),
+                      "launch_shape": {k: st[k] for k in ("threads_per_block", "splits", "cluster", "variant")}},
+           "roofline": {"bound": "alu", "achieved": FLOPS_PER_INTERACTION * per_launch / avg / 1e12,
+                        "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
+                        "frac": FLOPS_PER_INTERACTION * per_launch / avg / FP32_PEAK, "traffic": None,
+                        "kernel": KERNEL_NAMES.get(st["variant"], "k_force"), "avg_launch_ms": avg * 1e3},
            "clocks": clocks}
     print(json.dumps(out))
     return 0
@@ -513,7 +580,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
-    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid", "born"])
+    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid", "born", "box3", "box5"])
+    ap.add_argument("--box-bundles", type=int, default=65536, help="bundles of the 2^24-particle box")
     ap.add_argument("--grid-n", type=int, default=256, help="nodes per side of the grid workload")
     ap.add_argument("--cones", type=int, default=512)
     ap.add_argument("--cone-steps", type=int, default=16)
@@ -530,6 +598,8 @@ def main():
         return run_grid(args)
     if args.workload == "born":
         return run_born(args)
+    if args.workload in ("box3", "box5"):
+        return run_box(args)
     return run_ours(args)
 
 

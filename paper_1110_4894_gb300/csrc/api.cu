@@ -144,6 +144,8 @@ struct rt3d_ctx {
     bool stats_pending = false;
     std::vector<cudaEvent_t> tev;  // per-launch timing events
     int tev_used = 0;
+    double *atab = nullptr;  // a(t) table of the cosmology (device)
+    size_t atab_n = 0;
     unsigned long long *d_hist_u64 = nullptr;  // bins*2 + 5
     double *d_hist_f64 = nullptr;              // 8
     int hist_cap = 0;
@@ -297,6 +299,7 @@ extern "C" int rt3d_destroy(rt3d_ctx *ctx)
     cudaFree(s.bout);
     cudaFree(s.rout);
     cudaFree(s.prism);
+    cudaFree(ctx->atab);
     cudaFree(ctx->d_hist_u64);
     cudaFree(ctx->d_hist_f64);
     cudaFree(ctx->d_io);
@@ -339,6 +342,18 @@ extern "C" int rt3d_set_cosmology(rt3d_ctx *ctx, double om, double ol, double h)
     c.t0 = 2.0 / (3.0 * c.H0 * sqrt(ol)) * asinh(sqrt(ol / om));
     c.k = 1.5 * sqrt(ol) * c.H0;
     c.r = om / ol;
+    // a(t) table up to the lookback time of z = 5 (a = 1/6):
+    // t(a) = t0 - asinh(sqrt(a^3 / r)) / k
+    CK(cudaSetDevice(ctx->device));
+    const int n = 4096;
+    const double t_max = c.t0 - asinh(sqrt(pow(1.0 / 6.0, 3.0) / c.r)) / c.k;
+    CK(grow(ctx->atab, ctx->atab_n, (size_t)(2 * n)));
+    c.atab = nullptr;  // the table is filled from the closed form
+    CK(launch_atab(c, n, t_max / (n - 1), ctx->atab, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    c.atab = ctx->atab;
+    c.atab_n = n;
+    c.atab_h = t_max / (n - 1);
     ctx->have_cosmo = true;
     return RT3D_OK;
 }

@@ -16,7 +16,8 @@
 // * Sums are accumulated in FP32 over chunks of CHUNK particles and merged
 //   into a (hi, lo) pair by an error-free TwoSum per chunk.
 // * Block (x = ray block, y = particle split) writes (hi, lo) per output to
-//   partials[split][output][ray]; the integrator stage adds them in FP64.
+//   partials[split][output][ray]; the integrator stage adds them as FP32
+//   double-float numbers and converts once to FP64.
 #pragma once
 #include <cooperative_groups.h>
 #include <limits.h>
