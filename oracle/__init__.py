@@ -49,6 +49,7 @@ class Field(C.Structure):
         ("shift", C.POINTER(C.c_double)),
         ("mean_subtract", C.c_int),
         ("grid", C.POINTER(Grid)),
+        ("grid_cubes", C.c_int),
     ]
 
 
@@ -106,6 +107,8 @@ def lib():
         L.orc_histogram.argtypes = [C.c_int64, _dp, C.POINTER(C.c_int32), C.POINTER(HistOpts),
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_uint64), _dp]
         L.orc_histogram.restype = C.c_int
+        L.orc_replica_world.argtypes = [C.POINTER(Field), C.c_int, _dp]
+        L.orc_replica_world.restype = None
         L.orc_prism_hessian.argtypes = [_dp, _dp, _dp, _dp]
         L.orc_prism_hessian.restype = None
         L.orc_born.argtypes = [pc, C.POINTER(Field), C.c_double, C.c_int64, _dp, C.POINTER(TraceOpts), _dp, C.c_int]
@@ -172,7 +175,7 @@ class MassField:
     """A particle mass distribution as the oracle sees it (Sec. 3.3, 5.2)."""
 
     def __init__(self, pos, mass, soft, replicated=False, L=0.0, rot=None, shift=None,
-                 mean_subtract=False, grid=None):
+                 mean_subtract=False, grid=None, grid_cubes=0):
         self.pos = np.ascontiguousarray(pos, dtype=np.float64).reshape(-1, 3)
         n = self.pos.shape[0]
         self.mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, np.float64), (n,)))
@@ -193,7 +196,7 @@ class MassField:
         self.f = Field(n, _p(self.pos), _p(self.mass),
                        _p(self.soft) if self.soft is not None else None, self.soft_scalar,
                        int(self.replicated), self.L, self.n_rep, _p(self.rot, C.c_int32), _p(self.shift),
-                       int(self.mean_subtract), C.pointer(grid.g) if grid is not None else None)
+                       int(self.mean_subtract), grid.pointer() if grid is not None else None, int(grid_cubes))
         self.grid = grid  # keeps the node arrays alive
 
 
@@ -337,4 +340,11 @@ def born(cosmo, field, z_s, theta, schedule=0, n_steps=1000, lens_chi=0.0, asinh
                         _p(out), nthreads or default_threads())
     if rc != 0:
         raise ValueError("orc_born failed: %d" % rc)
+    return out
+
+
+def replica_world(field, j):
+    """world positions (n, 3) of replica j of a replicated MassField"""
+    out = np.zeros((field.pos.shape[0], 3))
+    lib().orc_replica_world(C.byref(field.f), int(j), _p(out))
     return out

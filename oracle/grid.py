@@ -113,6 +113,7 @@ class GridField:
         self.eps = float(soft)
         if val is None:
             M = cic(pos, mass, self.lo, self.h, self.n)
+            self.M_raw = M
             if mean_subtract:
                 M = M - M.mean()
             self.M = M
@@ -129,7 +130,46 @@ class GridField:
             lib().orc_grid_eval(C.byref(self.g), _p(pts[i]), _p(out[i]))
         return out
 
+    def pointer(self):
+        return C.pointer(self.g)
+
     def field(self):
         """an oracle MassField whose phi and grad phi come from this grid"""
         from . import MassField
         return MassField(np.zeros((0, 3)), np.zeros(0), 0.0, grid=self)
+
+
+class BoxGridField:
+    """A replicated box on cube grids (Sec. 5.2): the prism of each replica
+    around the optical axis, |x1|, |x2| <= W/2 with W = L / cubes, is cut
+    along x3 into `cubes` cubes of side W; the particles of each cube (half-
+    open in every axis, the others dropped) go on that cube's own n^3 grid
+    with nodes on its faces (spacing W / (n - 1)), minus the cube's mean node
+    mass, and each cube's field is computed from its own mass only ("structure
+    within the box only").  A bundle uses the cube holding its central ray."""
+
+    def __init__(self, pos, mass, soft, L, rot, shift, cubes, n, n_int=2, mean_subtract=True):
+        from . import MassField, replica_world
+        self.L, self.cubes, self.n = float(L), int(cubes), int(n)
+        W = self.L / self.cubes
+        h = W / (self.n - 1)
+        box = MassField(pos, mass, soft, replicated=True, L=L, rot=rot, shift=shift)
+        mass = np.broadcast_to(np.asarray(mass, np.float64), (box.pos.shape[0],))
+        self.rot, self.shift, self.n_rep = box.rot, box.shift, box.n_rep
+        self.grids = []
+        for j in range(self.n_rep):
+            w = replica_world(box, j)
+            for c in range(self.cubes):
+                lo = np.array([-0.5 * W, -0.5 * W, j * self.L + c * W])
+                inside = np.all((w >= lo) & (w < lo + W), axis=1)
+                self.grids.append(GridField(w[inside], mass[inside], soft, lo, h, self.n, n_int=n_int,
+                                            mean_subtract=mean_subtract))
+        self.array = (Grid * len(self.grids))(*[gf.g for gf in self.grids])
+
+    def pointer(self):
+        return C.cast(self.array, C.POINTER(Grid))
+
+    def field(self):
+        from . import MassField
+        return MassField(np.zeros((0, 3)), np.zeros(0), 0.0, replicated=True, L=self.L,
+                         rot=self.rot, shift=self.shift, grid=self, grid_cubes=self.cubes)

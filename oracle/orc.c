@@ -329,7 +329,8 @@ static void field_eval(const orc_field *f, const prep_field *pf, int rep, const 
                        double out[4], double *npairs)
 {
     if (f->grid) {  /* grid path: the field interpolated from the nodes (App. B) */
-        orc_grid_eval(f->grid, r, out);
+        /* cube-tiled boxes: rep is the cell (replica, cube) the caller chose */
+        orc_grid_eval(f->grid + (f->replicated ? rep : 0), r, out);
         return;
     }
     const double *w = pf->w[f->replicated ? rep : 0];
@@ -441,8 +442,27 @@ void orc_grid_eval(const orc_grid *g, const double r[3], double out[4])
     }
 }
 
+/* READING (grid boxes): a bundle uses the cube holding its central ray's
+ * stage position, as for replicas; the cell index is replica * cubes + cube */
+static int cell_of(const orc_field *f, double x3)
+{
+    if (!f->replicated) return 0;
+    double q = floor(x3 / f->L);
+    int j = q < 0.0 ? 0 : (q > (double)(f->n_rep - 1) ? f->n_rep - 1 : (int)q);
+    double W = f->L / (double)f->grid_cubes;
+    double c = floor((x3 - (double)j * f->L) / W);
+    int cc = c < 0.0 ? 0 : (c > (double)(f->grid_cubes - 1) ? f->grid_cubes - 1 : (int)c);
+    return j * f->grid_cubes + cc;
+}
+
+void orc_replica_world(const orc_field *f, int j, double *out)
+{
+    replica_world(f, j, out);
+}
+
 static int rep_of(const orc_field *f, double x3)
 {
+    if (f->grid && f->replicated) return cell_of(f, x3);
     if (!f->replicated) return 0;
     double q = floor(x3 / f->L);
     if (q < 0.0) return 0;
@@ -453,14 +473,16 @@ static int rep_of(const orc_field *f, double x3)
 int orc_potential(const orc_field *f, int64_t n, const double *pts, const int32_t *rep,
                   double *out, int nthreads)
 {
-    if (f->grid && f->replicated) return -1;
+    if (f->grid && f->replicated && f->grid_cubes < 1) return -1;
     prep_field pf;
     if (prep_make(f, &pf) != 0) { prep_free(&pf); return -2; }
+    const int cubes = f->grid && f->replicated;  /* grid boxes: the point's own cell */
     for (int64_t i = 0; i < n; ++i)
-        if (f->replicated && (rep[i] < 0 || rep[i] >= f->n_rep)) { prep_free(&pf); return -1; }
+        if (f->replicated && !cubes && (rep[i] < 0 || rep[i] >= f->n_rep)) { prep_free(&pf); return -1; }
 #pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1)
     for (int64_t i = 0; i < n; ++i)
-        field_eval(f, &pf, f->replicated ? rep[i] : 0, pts + 3 * i, out + 4 * i, NULL);
+        field_eval(f, &pf, cubes ? cell_of(f, pts[3 * i + 2]) : (f->replicated ? rep[i] : 0), pts + 3 * i,
+                   out + 4 * i, NULL);
     prep_free(&pf);
     return 0;
 }
@@ -550,7 +572,7 @@ int orc_trace(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b,
               double *bundle_out, int32_t *steps_out, double *n_pairs, int nthreads)
 {
     if (o->n_ring < 2 || o->n_steps < 1 || !(z_s > 0.0)) return -1;
-    if (f->grid && f->replicated) return -1;
+    if (f->grid && f->replicated && f->grid_cubes < 1) return -1;
     const int nr = 1 + o->n_ring;
     const double chi_s = orc_chi(c, z_s);
     double *dlam = (double *)malloc(sizeof(double) * (size_t)o->n_steps);

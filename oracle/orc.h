@@ -63,7 +63,11 @@ typedef struct {
     const double *shift;  /* n_rep * 3 shifts in [0, L) */
     int mean_subtract;    /* subtract the field of the replica's uniform mean */
     const struct orc_grid *grid; /* non-NULL: phi and grad phi come from this
-                                    gridded field (isolated fields only) */
+                                    gridded field; for replicated fields an array
+                                    of n_rep * grid_cubes cube grids (below) */
+    int grid_cubes;      /* replicated grid fields: cubes of side L / grid_cubes
+                            along x3 per replica (Sec. 5.2: the prism of each box
+                            split into cubes, each on its own grid) */
 } orc_field;
 
 /* ---- gridded field (Sec. 3.3 grid path, App. B interpolation) ---------- */
@@ -89,6 +93,11 @@ void orc_grid_y2(int n, const double *val, double *y2);
 
 /* App. B evaluation at r: out = (phi, grad phi); zero outside the node range */
 void orc_grid_eval(const orc_grid *g, const double r[3], double out[4]);
+
+/* world positions (n*3) of replica j of a replicated field (the transform the
+ * direct sum uses): rotation about the box centre, periodic shift, the box
+ * centred on the optical axis at x3 in [jL, (j+1)L) */
+void orc_replica_world(const orc_field *f, int j, double *out);
 
 /* phi and grad phi (Eqs. psi, derivs, phicotophys, as a Plummer-softened
  * direct sum) at n points; rep[i] selects the replica for point i (ignored

@@ -152,3 +152,41 @@ def test_grid_trace_matches_direct_sum_for_a_smooth_lens(cosmo):
     # missing, so compare the magnification, which is set near the lens
     assert np.max(np.abs(got.mu / ref.mu - 1)) < 2e-2
     assert np.max(np.abs(got.mu - 1) / np.abs(ref.mu - 1)) > 0.5
+
+
+def _box_grid(cubes=4, n=12, n_rep=3):
+    import inputs as I
+    L = I.box_length(20.0 / 0.7)
+    pos, mass, _ = I.halo_box(3000, L, 8, I.BASE_SEED + 61)
+    rot, shift = I.replicas(n_rep, L, I.BASE_SEED + 61)
+    return G.BoxGridField(pos, mass, 0.02, L, rot, shift, cubes=cubes, n=n), pos, mass, rot, shift, L
+
+
+def test_replica_world_is_the_direct_sums_replica():
+    bg, pos, mass, rot, shift, L = _box_grid()
+    box = oracle.MassField(pos, mass, 0.02, replicated=True, L=L, rot=rot, shift=shift)
+    j = 2
+    w = oracle.replica_world(box, j)
+    pts = np.array([[0.3, -1.1, (j + 0.4) * L], [-2.0, 0.7, (j + 0.9) * L]])
+    a = oracle.potential(box, pts, np.array([j, j], np.int32))
+    b = oracle.potential(oracle.MassField(w, mass, 0.02), pts)
+    assert np.allclose(a, b, rtol=1e-12, atol=0)
+
+
+def test_box_grid_cubes_hold_the_prism_mass_and_select_by_x3():
+    bg, pos, mass, rot, shift, L = _box_grid()
+    W = L / bg.cubes
+    box = oracle.MassField(pos, mass, 0.02, replicated=True, L=L, rot=rot, shift=shift)
+    for j in range(bg.n_rep):
+        w = oracle.replica_world(box, j)
+        inside = (w[:, 0] >= -0.5 * W) & (w[:, 0] < 0.5 * W) & (w[:, 1] >= -0.5 * W) & (w[:, 1] < 0.5 * W)
+        # every particle of the prism lands in exactly one cube, with all its mass (nodes on the faces)
+        held = sum(bg.grids[j * bg.cubes + c].M_raw.sum() for c in range(bg.cubes))
+        assert held == pytest.approx(mass[inside].sum(), rel=1e-12)
+    g = np.random.default_rng(4)
+    pts = np.stack([g.uniform(-0.4, 0.4, 30) * W, g.uniform(-0.4, 0.4, 30) * W, g.uniform(0, bg.n_rep * L, 30)], 1)
+    got = oracle.potential(bg.field(), pts)
+    for p, v in zip(pts, got):
+        j = min(int(p[2] // L), bg.n_rep - 1)
+        c = min(int((p[2] - j * L) // W), bg.cubes - 1)
+        assert np.array_equal(v, bg.grids[j * bg.cubes + c].eval(p[None, :])[0])
