@@ -219,6 +219,92 @@ def run_grid(args):
     return 0
 
 
+def run_prism(args):
+    """The grid path on the sampling region of Sec. 5.2: 256^3 particles in a
+    50/h Mpc box replicated 28 times to z_s = 0.5, each replica's 6.25/h Mpc
+    prism cut into 8 cubes on 128^3-node grids (App. B interpolation,
+    n_int = 2), 176^2 bundles inside the prism, 1000 uniform RK4 steps.  One
+    step = one full trace of every bundle (rt3d_trace_device + histogram).
+    Reported beside it: the build time of the 224 cube grids and the muPDF's
+    weighted mean and width."""
+    import torch
+
+    import inputs
+    import paper_1110_4894_gb300 as P
+    dev = torch.device("cuda", 0)
+    cfg = inputs.config_prism(n_steps=args.rk4_steps or 1000)
+    n, cubes = cfg["grid_n"], cfg["cubes"]
+    nb = cfg["theta"].shape[0]
+    ctx = P.Context(0, precision=P.MIXED, time_kernels=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    t0 = time.perf_counter()
+    ctx.load_grid_box(0, cfg["pos"], cfg["mass"], cfg["soft"], cfg["L"], cfg["rot"], cfg["shift"], cubes, n,
+                      n_int=2, mean_subtract=True)
+    build_s = time.perf_counter() - t0
+    kw = dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0, n_steps=cfg["n_steps"])
+    d_theta = torch.from_numpy(np.ascontiguousarray(cfg["theta"])).to(dev)
+    d_bout = torch.zeros(nb * 6, dtype=torch.float64, device=dev)
+    d_counts = torch.zeros(HIST["bins"], dtype=torch.int64, device=dev)
+    d_wfix = torch.zeros(HIST["bins"], dtype=torch.int64, device=dev)
+    d_scal = torch.zeros(8, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+
+    def step():
+        ctx.trace_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), d_bout.data_ptr(), **kw)
+        ctx.histogram_device(sp, nb, d_bout.data_ptr(), d_counts.data_ptr(), d_wfix.data_ptr(), d_scal.data_ptr(),
+                             **HIST)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize(dev)
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    eval_ms, eval_launches, evals, launches = 0.0, 0, 0.0, 0
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            step()
+            ev[k][1].record(stream)
+            st = ctx.stats()
+            eval_ms += st["force_ms"]
+            eval_launches += st["force_launches"]
+            evals += st["interactions"]
+            launches += st["launches"] + 2
+    clocks = clk.summary()
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    scal = d_scal.cpu().numpy()
+    res = d_bout.view(nb, 6).cpu().numpy()
+    per_launch_s = eval_ms / 1e3 / max(1, eval_launches)
+    w = 4
+    bytes_per_launch = nb * (1 + cfg["n_ring"]) * 4 * w * w * 4 * 8
+    peaks = {}
+    try:
+        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
+    except Exception:
+        pass
+    hbm = peaks.get("hbm_gbs") or 6800.0
+    out = {"metric": "ray bundles/s (grid path, replicated box)", "value": nb * args.steps / dev_s,
+           "unit": "bundles/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": "prism_box_2e24p_%dcubes_grid%d" % (cubes, n), "particles": int(cfg["pos"].shape[0]),
+                      "replicas": int(cfg["n_rep"]), "cubes_per_replica": cubes, "grid_n": n,
+                      "node_spacing_mpc": cfg["L"] / cubes / (n - 1), "n_int": 2, "bundles": nb,
+                      "rk4_steps": cfg["n_steps"], "z_s": cfg["z_s"],
+                      "l2": "30 GB of cube grids, larger than L2"},
+           "grid_build_s": build_s,
+           "field_evals_per_s": evals / dev_s,
+           "roofline": {"bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9, "peak": hbm,
+                        "unit": "GB/s", "frac": bytes_per_launch / per_launch_s / 1e9 / hbm, "traffic": None,
+                        "kernel": "k_grid_eval", "avg_launch_ms": per_launch_s * 1e3,
+                        "note": "algorithmic bytes = spline reads along x3 per ray and field; most hit L1/L2"},
+           "mupdf": {"bundles_binned": int(scal[0]), "mean_w": float(scal[6]), "sigma_w": float(scal[7]),
+                     "flagged_bundles": int(np.count_nonzero(res[:, 5]))},
+           "clocks": clocks, "gpu_launches": int(launches)}
+    print(json.dumps(out))
+    return 0
+
+
 def run_born(args):
     """The Born approximation (Sec. 6) on the NFW workload: kappa and gamma of
     every bundle centre from the Hessian pair sum at every node of the 2000-
@@ -304,6 +390,20 @@ def run_box(args):
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     per_launch = inter / max(1, force_launches)
     avg = force_ms / 1e3 / max(1, force_launches)
+    # the all-FP64 path on the first bundles of the same window: rate, and
+    # the magnification difference to the mixed path on those bundles
+    k = min(nb, args.fp64_bundles)
+    mu_mixed = d_bout.view(nb, 6)[:k, 0].cpu().numpy()
+    c64 = P.Context(0, precision=P.FP64)
+    c64.set_cosmology(*cfg["cosmo"])
+    c64.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"], replicated=True, box_length=cfg["L"],
+                       rot=cfg["rot"], shift=cfg["shift"], mean_subtract=True)
+    t0 = time.perf_counter()
+    r64 = c64.trace(0, cfg["z_s"], theta[:k], **kw)
+    t64 = time.perf_counter() - t0
+    fp64_rate = c64.stats()["interactions"] / t64
+    fp64 = {"bundles": k, "interactions_per_s": fp64_rate, "speedup_of_mixed": (inter / dev_s) / fp64_rate,
+            "max_rel_dmu_vs_mixed": float(np.max(np.abs(mu_mixed / r64["mu"] - 1)))}
     out = {"metric": METRIC, "value": inter / dev_s, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
            "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True,
            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -316,6 +416,7 @@ def run_box(args):
                         "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
                         "frac": FLOPS_PER_INTERACTION * per_launch / avg / FP32_PEAK, "traffic": None,
                         "kernel": KERNEL_NAMES.get(st["variant"], "k_force"), "avg_launch_ms": avg * 1e3},
+           "fp64_same_window": fp64,
            "clocks": clocks}
     print(json.dumps(out))
     return 0
@@ -580,8 +681,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=1)
     ap.add_argument("--cpu-steps", type=int, default=250)
     ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
-    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid", "born", "box3", "box5"])
+    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid", "born", "box3", "box5", "prism"])
     ap.add_argument("--box-bundles", type=int, default=65536, help="bundles of the 2^24-particle box")
+    ap.add_argument("--fp64-bundles", type=int, default=256, help="bundles of the box run on the FP64 path")
     ap.add_argument("--grid-n", type=int, default=256, help="nodes per side of the grid workload")
     ap.add_argument("--cones", type=int, default=512)
     ap.add_argument("--cone-steps", type=int, default=16)
@@ -598,6 +700,8 @@ def main():
         return run_grid(args)
     if args.workload == "born":
         return run_born(args)
+    if args.workload == "prism":
+        return run_prism(args)
     if args.workload in ("box3", "box5"):
         return run_box(args)
     return run_ours(args)

@@ -204,8 +204,27 @@ typedef struct {
 int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                    double soft, const rt3d_grid_opts *g);
 
+/* Grid path for a replicated box (Sec. 5.2): each replica of the box (as in
+ * rt3d_load_particles: rot[j] about the box centre, shift[j] with periodic
+ * wrap, centred on the optical axis at x3 in [jL, (j+1)L)) is cut to the
+ * prism |x1|, |x2| < W/2 around the optical axis, W = L / cubes, and the prism
+ * into `cubes` cubes of side W along x3.  The particles of each cube (half-
+ * open intervals; particles outside the prism are dropped) go on that cube's
+ * own n^3 grid with nodes on its faces (spacing W / (n - 1)); with
+ * g->mean_subtract the cube's mean node mass is removed; the cube's field
+ * comes from its own mass only (zero-padded FFT).  A bundle reads the cube
+ * holding its central ray's stage position (rt3d_potential: each point its
+ * own cube); up to one node spacing beyond that cube's faces the end splines
+ * are extrapolated (the other rays of a bundle that straddles a face),
+ * further out the field is zero.  g->lo and g->h are not
+ * used.  Positions must lie in [0, L).  Memory: 8 n^3 doubles per cube stay
+ * on the device.  Errors as rt3d_load_grid. */
+int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
+                       double soft, const rt3d_volume *vol, int cubes, const rt3d_grid_opts *g);
+
 /* Copy a grid slot's node values to out (host, 4 n^3 doubles, [f][i1][i2][i3]
- * with i3 fastest, f = phi, dphi/dx1, dphi/dx2, dphi/dx3). */
+ * with i3 fastest, f = phi, dphi/dx1, dphi/dx2, dphi/dx3; for a box grid,
+ * n_replicas * cubes such blocks, replica-major). */
 int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out);
 
 /* Trace n_bundles bundles with centres theta (n_bundles*2, tangent-plane

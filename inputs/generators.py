@@ -33,7 +33,7 @@ __all__ = [
     "QUANTUM", "BASE_SEED", "rng", "quantize", "chi_placement", "hubble_placement",
     "r200_physical", "point_lens", "nfw_halo", "plummer_particle", "halo_box", "proper_rotations",
     "replicas", "bundle_line", "bundle_grid", "config_c1", "config_c2", "config_c3",
-    "config_c4", "config_c5", "box_length", "theta_einstein_placement",
+    "config_c4", "config_c5", "config_prism", "box_length", "theta_einstein_placement",
 ]
 
 
@@ -281,6 +281,26 @@ def config_c3(N=2097152, n_side=256, n_steps=1000, n_halos=3000, seed=BASE_SEED 
 def config_c5(N=16777216, n_side=1024, n_steps=1000, n_halos=24000, seed=BASE_SEED + 5):
     """2^24 particles in a 200/h Mpc box, z_s = 1.0, n_side^2 bundles, +-2.3 deg."""
     return _box_config("c5_box", N, 200.0, n_halos, 1.0, n_side, 2.3, n_steps, seed)
+
+
+def config_prism(N=16777216, n_side=176, n_steps=1000, n_halos=24000, cubes=8, grid_n=128, seed=BASE_SEED + 6):
+    """The sampling region of Sec. 5.2: 256^3 particles in a periodic 50/h Mpc
+    box, replicated to z_s = 0.5 (28 replicas), each replica's prism 6.25/h
+    Mpc across cut into 8 cubes with 128^3-node grids; n_side^2 bundles on a
+    grid inside 0.9 of the prism's half-width at the source plane."""
+    om, ol, h = COSMO
+    zs = 0.5
+    L = box_length(50.0 / h)
+    pos, mass, info = halo_box(N, L, n_halos, seed, om, ol, h)
+    chi_s = chi_placement(zs, om, ol, h)
+    n_rep = int(math.ceil(chi_s / L)) + 1
+    rot, shift = replicas(n_rep, L, seed)
+    half = 0.9 * 0.5 * (L / cubes) / chi_s
+    theta = bundle_grid(-half, half, n_side)
+    return dict(name="prism_box", cosmo=COSMO, z_s=zs, pos=pos, mass=mass, soft=0.016 / h, theta=theta,
+                n_ring=4, theta_r=math.radians(1.0 / 3600.0), schedule=0, n_steps=n_steps,
+                lens_chi=0.0, asinh_s=1.0, L=L, rot=rot, shift=shift, n_rep=n_rep, info=info, cubes=cubes,
+                grid_n=grid_n, precision="mixed", replicated=True, mean_subtract=True)
 
 
 def config_c4(n_cones=512, n_steps=1000, seed=BASE_SEED + 4, n_min=1000, n_max=1000000,

@@ -32,6 +32,7 @@ class Grid(C.Structure):
         ("n_int", C.c_int),
         ("val", C.POINTER(C.c_double)),
         ("y2", C.POINTER(C.c_double)),
+        ("margin", C.c_double),
     ]
 
 

@@ -107,7 +107,7 @@ class GridField:
     """A particle set on the App. B node grid, ready for the oracle's field
     evaluation and trace (pass ``grid=`` to ``MassField``)."""
 
-    def __init__(self, pos, mass, soft, lo, h, n, n_int=2, mean_subtract=False, val=None):
+    def __init__(self, pos, mass, soft, lo, h, n, n_int=2, mean_subtract=False, val=None, margin=0.0):
         self.n, self.h, self.n_int = int(n), float(h), int(n_int)
         self.lo = np.asarray(lo, np.float64).reshape(3)
         self.eps = float(soft)
@@ -121,7 +121,8 @@ class GridField:
         self.val = np.ascontiguousarray(val, np.float64)
         self.y2 = np.zeros_like(self.val)
         lib().orc_grid_y2(self.n, _p(self.val), _p(self.y2))
-        self.g = Grid(self.n, (C.c_double * 3)(*self.lo), self.h, self.n_int, _p(self.val), _p(self.y2))
+        self.g = Grid(self.n, (C.c_double * 3)(*self.lo), self.h, self.n_int, _p(self.val), _p(self.y2),
+                      float(margin))
 
     def eval(self, pts):
         pts = np.ascontiguousarray(pts, np.float64).reshape(-1, 3)
@@ -146,7 +147,9 @@ class BoxGridField:
     open in every axis, the others dropped) go on that cube's own n^3 grid
     with nodes on its faces (spacing W / (n - 1)), minus the cube's mean node
     mass, and each cube's field is computed from its own mass only ("structure
-    within the box only").  A bundle uses the cube holding its central ray."""
+    within the box only").  A bundle uses the cube holding its central ray;
+    points up to one node spacing outside the cube's nodes (the bundle's other
+    rays near a face) take the end intervals' cubics."""
 
     def __init__(self, pos, mass, soft, L, rot, shift, cubes, n, n_int=2, mean_subtract=True):
         from . import MassField, replica_world
@@ -163,7 +166,7 @@ class BoxGridField:
                 lo = np.array([-0.5 * W, -0.5 * W, j * self.L + c * W])
                 inside = np.all((w >= lo) & (w < lo + W), axis=1)
                 self.grids.append(GridField(w[inside], mass[inside], soft, lo, h, self.n, n_int=n_int,
-                                            mean_subtract=mean_subtract))
+                                            mean_subtract=mean_subtract, margin=1.0))
         self.array = (Grid * len(self.grids))(*[gf.g for gf in self.grids])
 
     def pointer(self):

@@ -415,7 +415,7 @@ void orc_grid_eval(const orc_grid *g, const double r[3], double out[4])
     if (w < 2 || w > 16 || n < w) return;
     for (int d = 0; d < 3; ++d) {
         u[d] = (r[d] - g->lo[d]) / g->h;
-        if (!(u[d] >= 0.0 && u[d] <= (double)(n - 1))) return;  /* outside the nodes: no field */
+        if (!(u[d] >= -g->margin && u[d] <= (double)(n - 1) + g->margin)) return;  /* outside: no field */
         s[d] = (int)floor(u[d]) - g->n_int + 1;
         if (s[d] > n - w) s[d] = n - w;
         if (s[d] < 0) s[d] = 0;

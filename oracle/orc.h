@@ -82,6 +82,10 @@ typedef struct orc_grid {
     int n_int;          /* App. B: n_int nodes on either side per dimension */
     const double *val;  /* 4 n^3 */
     const double *y2;   /* 4 n^3 */
+    double margin;      /* points up to margin node spacings outside the node
+                           range take the end intervals' cubics (box cubes: 1,
+                           so the rays of a bundle near a cube face keep their
+                           field); farther out the field is zero */
 } orc_grid;
 
 /* second derivatives of the natural cubic spline through y[0..n-1] (unit

@@ -112,6 +112,8 @@ def lib(build=True):
         "rt3d_watchdog_selftest": ([vp, C.c_double], C.c_int),
         "rt3d_load_grid": ([vp, C.c_int, C.c_int64, _dp, _dp, C.c_double, C.POINTER(GridOpts)], C.c_int),
         "rt3d_grid_nodes": ([vp, C.c_int, _dp], C.c_int),
+        "rt3d_load_grid_box": ([vp, C.c_int, C.c_int64, _dp, _dp, C.c_double, C.POINTER(Volume), C.c_int,
+                                C.POINTER(GridOpts)], C.c_int),
         "rt3d_schedule": ([vp, C.c_double, C.c_int, C.c_int, C.c_double, C.c_double, _dp, _dp], C.c_int),
         "rt3d_get_stats": ([vp, C.POINTER(Stats)], C.c_int),
         "rt3d_status_string": ([C.c_int], C.c_char_p),
@@ -187,9 +189,30 @@ class Context:
         self._grid_n[int(field_id)] = int(n)
         self._check(self.L.rt3d_load_grid(self.h, int(field_id), npart, _p(pos), _p(mass), float(soft), C.byref(g)))
 
+    def load_grid_box(self, field_id, pos, mass, soft, box_length, rot, shift, cubes, n, n_int=2,
+                      mean_subtract=True):
+        """rt3d_load_grid_box: a replicated box on cube grids (n^3 nodes per cube)."""
+        pos = np.ascontiguousarray(pos, np.float64).reshape(-1, 3)
+        npart = pos.shape[0]
+        mass = np.ascontiguousarray(np.broadcast_to(np.asarray(mass, np.float64), (npart,)))
+        rot = np.ascontiguousarray(np.asarray(rot, np.int32).reshape(-1, 9))
+        shift = np.ascontiguousarray(np.asarray(shift, np.float64).reshape(-1, 3))
+        vol = Volume(1, float(box_length), rot.shape[0], _p(rot, C.c_int32), _p(shift), 0)
+        g = GridOpts(int(n), (C.c_double * 3)(0.0, 0.0, 0.0), 0.0, int(n_int), int(bool(mean_subtract)))
+        self._grid_n = getattr(self, "_grid_n", {})
+        self._grid_n[int(field_id)] = (int(n), rot.shape[0] * int(cubes))
+        self._check(self.L.rt3d_load_grid_box(self.h, int(field_id), npart, _p(pos), _p(mass), float(soft),
+                                              C.byref(vol), int(cubes), C.byref(g)))
+
     def grid_nodes(self, field_id):
-        """rt3d_grid_nodes: phi and grad phi on the nodes, (4, n, n, n)."""
+        """rt3d_grid_nodes: phi and grad phi on the nodes, (4, n, n, n) (boxes:
+        (cells, 4, n, n, n))."""
         n = self._grid_n[int(field_id)]
+        if isinstance(n, tuple):
+            n, cells = n
+            out = np.zeros((cells, 4, n, n, n))
+            self._check(self.L.rt3d_grid_nodes(self.h, int(field_id), _p(out)))
+            return out
         out = np.zeros((4, n, n, n))
         self._check(self.L.rt3d_grid_nodes(self.h, int(field_id), _p(out)))
         return out

@@ -836,7 +836,7 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
             }
             if (fs.is_grid)
                 CK(launch_grid_eval(fs.gd, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, n_rays,
-                                    fp64 ? 1 : 0, s.partials, gate, st));
+                                    fp64 ? 1 : 0, s.partials, gate, st, nr));
             else
                 CK(run_force(ctx, fs.df, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays,
                              rs.rep + (g & 1) * n_b, nr, n_rays, sh, fp64, s.partials, gate, st));
@@ -1474,6 +1474,117 @@ extern "C" int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const doub
     return RT3D_OK;
 }
 
+extern "C" int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
+                                  double soft, const rt3d_volume *vol, int cubes, const rt3d_grid_opts *g)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (field_id < 0 || field_id >= RT3D_MAX_FIELDS) return fail(ctx, RT3D_EINVAL, "field id out of range");
+    if (!g || !vol || !vol->replicated) return fail(ctx, RT3D_EINVAL, "a replicated volume and grid options are needed");
+    if (g->n_int < 1 || g->n_int > 4) return fail(ctx, RT3D_EINVAL, "n_int must be 1..4");
+    if (g->n < 2 * g->n_int || g->n > 512) return fail(ctx, RT3D_EINVAL, "grid n must be in [2 n_int, 512]");
+    const double L = vol->box_length;
+    if (!(L > 0.0) || !isfinite(L) || vol->n_replicas < 1 || !vol->rot || !vol->shift)
+        return fail(ctx, RT3D_EINVAL, "replicated volume needs box_length > 0 and replica transforms");
+    if (cubes < 1 || cubes > 64) return fail(ctx, RT3D_EINVAL, "cubes per replica must be 1..64");
+    if (!(soft >= 0.0) || !isfinite(soft)) return fail(ctx, RT3D_EINVAL, "softening must be >= 0");
+    if (n < 0 || (n > 0 && (!pos || !mass))) return fail(ctx, RT3D_EINVAL, "null particle arrays");
+    for (int64_t i = 0; i < n; ++i) {
+        for (int d = 0; d < 3; ++d)
+            if (!(pos[3 * i + d] >= 0.0 && pos[3 * i + d] < L)) return fail(ctx, RT3D_EINVAL, "positions must be in [0, L)");
+        if (!(mass[i] > 0.0) || !isfinite(mass[i])) return fail(ctx, RT3D_EINVAL, "particle masses must be > 0");
+    }
+    const int R = vol->n_replicas;
+    CK(cudaSetDevice(ctx->device));
+    CK(cudaStreamSynchronize(ctx->stream));
+    FieldSlot &fs = ctx->fields[field_id];
+    free_field(fs);
+    GridDev &G = fs.gd;
+    G.n = g->n;
+    G.n_int = g->n_int;
+    G.cubes = cubes;
+    G.n_rep = R;
+    G.L = L;
+    G.W = L / cubes;
+    G.h = G.W / (g->n - 1);
+    G.margin = 1.0;
+    const size_t stride = 4 * (size_t)g->n * g->n * g->n;
+    CK(cudaMalloc(&G.val, sizeof(double) * stride * (size_t)R * cubes));
+    CK(cudaMalloc(&G.y2, sizeof(double) * stride * (size_t)R * cubes));
+    // replica j: the box rotated about its centre by rot[j], shifted by shift[j]
+    // with periodic wrap, centred on the optical axis at x3 in [jL, (j+1)L)
+    const double c = 0.5 * L;
+    std::vector<std::vector<double>> cp((size_t)cubes), cm((size_t)cubes);
+    for (int j = 0; j < R; ++j) {
+        const int32_t *Rm = vol->rot + 9 * j;
+        const double *sh = vol->shift + 3 * j;
+        for (int q = 0; q < cubes; ++q) {
+            cp[q].clear();
+            cm[q].clear();
+        }
+        for (int64_t i = 0; i < n; ++i) {
+            const double *p = pos + 3 * i;
+            double w[3];
+            for (int r = 0; r < 3; ++r) {
+                double v = 0.0;
+                for (int k = 0; k < 3; ++k) v += (double)Rm[3 * r + k] * (p[k] - c);
+                v = v + c + sh[r];
+                while (v >= L) v -= L;
+                while (v < 0.0) v += L;
+                w[r] = v;
+            }
+            w[0] -= c;
+            w[1] -= c;
+            w[2] += (double)j * L;
+            if (!(w[0] >= -0.5 * G.W && w[0] < 0.5 * G.W && w[1] >= -0.5 * G.W && w[1] < 0.5 * G.W)) continue;
+            for (int q = 0; q < cubes; ++q) {
+                const double z0 = (double)j * L + (double)q * G.W;
+                if (w[2] >= z0 && w[2] < z0 + G.W) {
+                    cp[q].insert(cp[q].end(), w, w + 3);
+                    cm[q].push_back(mass[i]);
+                    break;
+                }
+            }
+        }
+        for (int q = 0; q < cubes; ++q) {
+            GridDev one;
+            one.n = g->n;
+            one.n_int = g->n_int;
+            one.h = G.h;
+            one.lo[0] = -0.5 * G.W;
+            one.lo[1] = -0.5 * G.W;
+            one.lo[2] = (double)j * L + (double)q * G.W;
+            int rc = grid_build(one, (int64_t)cm[q].size(), cp[q].data(), cm[q].data(), soft,
+                                g->mean_subtract ? 1 : 0, ctx->stream, ctx->err);
+            if (rc == RT3D_OK) {
+                const size_t off = ((size_t)j * cubes + q) * stride;
+                cudaError_t e = cudaMemcpyAsync(G.val + off, one.val, sizeof(double) * stride, cudaMemcpyDeviceToDevice,
+                                                ctx->stream);
+                if (e == cudaSuccess)
+                    e = cudaMemcpyAsync(G.y2 + off, one.y2, sizeof(double) * stride, cudaMemcpyDeviceToDevice,
+                                        ctx->stream);
+                if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
+                if (e != cudaSuccess) rc = fail(ctx, RT3D_ECUDA, cudaGetErrorString(e));
+            }
+            grid_free(one);
+            if (rc != RT3D_OK) {
+                free_field(fs);
+                return rc;
+            }
+        }
+    }
+    DevField &df = fs.df;
+    df = DevField{};
+    df.n = n;
+    df.n_rep = 1;
+    df.mscale_inv = 1.0;
+    df.delta = 1.0;
+    df.inv_delta = 1.0;
+    fs.n = n;
+    fs.is_grid = true;
+    fs.loaded = true;
+    return RT3D_OK;
+}
+
 extern "C" int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out)
 {
     if (!ctx) return RT3D_EINVAL;
@@ -1483,7 +1594,7 @@ extern "C" int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out)
     if (!fs.is_grid) return fail(ctx, RT3D_EINVAL, "not a grid field");
     if (!out) return fail(ctx, RT3D_EINVAL, "null output");
     CK(cudaSetDevice(ctx->device));
-    const size_t m = 4 * (size_t)fs.gd.n * fs.gd.n * fs.gd.n;
+    const size_t m = 4 * (size_t)fs.gd.n * fs.gd.n * fs.gd.n * (fs.gd.cubes > 0 ? (size_t)fs.gd.cubes * fs.gd.n_rep : 1);
     CK(cudaMemcpyAsync(out, fs.gd.val, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
     CK(cudaStreamSynchronize(ctx->stream));
     return RT3D_OK;

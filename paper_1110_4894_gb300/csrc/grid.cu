@@ -203,10 +203,13 @@ __device__ __forceinline__ double local_spline(const double (&t)[W], double u)
     return A * yk + B * yk1 + ((A * A * A - A) * zk + (B * B * B - B) * zk1) / 6.0;
 }
 
+// group: points per bundle; a cube-tiled box takes the cube holding the x3
+// of the group's first point (the bundle's central ray), as the direct sum
+// takes its replica
 template <int NI>
 __global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const double *__restrict__ py,
                             const double *__restrict__ pz, int64_t n_pts, int mode, void *__restrict__ out,
-                            const unsigned long long *__restrict__ gate)
+                            const unsigned long long *__restrict__ gate, int group)
 {
     constexpr int W = 2 * NI;
     if (gate && *gate == 0ull) return;
@@ -215,13 +218,28 @@ __global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const doub
     if (i >= n_pts) return;
     const int n = g.n;
     const double r[3] = {px[i], py[i], pz[i]};
+    double lo[3] = {g.lo[0], g.lo[1], g.lo[2]};
+    const double *val = g.val, *y2t = g.y2;
+    if (g.cubes > 0) {
+        const double x3 = pz[(i / group) * group];
+        double q = floor(x3 / g.L);
+        const int j = q < 0.0 ? 0 : (q > (double)(g.n_rep - 1) ? g.n_rep - 1 : (int)q);
+        double cq = floor((x3 - (double)j * g.L) / g.W);
+        const int c = cq < 0.0 ? 0 : (cq > (double)(g.cubes - 1) ? g.cubes - 1 : (int)cq);
+        lo[0] = -0.5 * g.W;
+        lo[1] = -0.5 * g.W;
+        lo[2] = (double)j * g.L + (double)c * g.W;
+        const int64_t cell = (int64_t)j * g.cubes + c, stride = 4 * (int64_t)n * n * n;
+        val += cell * stride;
+        y2t += cell * stride;
+    }
     double u[3];
     int s[3];
     bool inside = true;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-        u[d] = (r[d] - g.lo[d]) / g.h;
-        inside = inside && (u[d] >= 0.0 && u[d] <= (double)(n - 1));
+        u[d] = (r[d] - lo[d]) / g.h;
+        inside = inside && (u[d] >= -g.margin && u[d] <= (double)(n - 1) + g.margin);
         int sd = inside ? (int)floor(u[d]) - NI + 1 : 0;
         sd = sd > n - W ? n - W : sd;
         s[d] = sd < 0 ? 0 : sd;
@@ -229,7 +247,7 @@ __global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const doub
     double F = 0.0;
     if (inside) {
         const int64_t n3 = (int64_t)n * n * n;
-        const double *v = g.val + f * n3, *y2 = g.y2 + f * n3;
+        const double *v = val + f * n3, *y2 = y2t + f * n3;
         int k3 = (int)floor(u[2]);
         k3 = k3 > n - 2 ? n - 2 : k3;
         k3 = k3 < 0 ? 0 : k3;
@@ -263,15 +281,15 @@ __global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const doub
 }
 
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
-                             int mode, void *out, const unsigned long long *gate, cudaStream_t st)
+                             int mode, void *out, const unsigned long long *gate, cudaStream_t st, int group)
 {
     if (n <= 0) return cudaSuccess;
     const dim3 grid((unsigned)((n + 127) / 128), 4);
     switch (g.n_int) {
-    case 1: k_grid_eval<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate); break;
-    case 2: k_grid_eval<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate); break;
-    case 3: k_grid_eval<3><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate); break;
-    case 4: k_grid_eval<4><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate); break;
+    case 1: k_grid_eval<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
+    case 2: k_grid_eval<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
+    case 3: k_grid_eval<3><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
+    case 4: k_grid_eval<4><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

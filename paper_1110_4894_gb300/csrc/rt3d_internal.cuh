@@ -331,6 +331,15 @@ struct GridDev {
     double lo[3] = {0.0, 0.0, 0.0};
     double h = 0.0;
     double *val = nullptr, *y2 = nullptr;
+    // cube-tiled replicated box (cubes > 0): n_rep * cubes cube grids stored
+    // one after the other (stride 4 n^3) in val and y2; cube c of replica j
+    // has lo = (-W/2, -W/2, j L + c W) and spacing W / (n - 1)
+    int cubes = 0, n_rep = 1;
+    double L = 0.0, W = 0.0;
+    // points up to margin node spacings outside the node range take the end
+    // intervals' cubics (box cubes: 1, for the rays of a bundle near a cube
+    // face); farther out the field is zero
+    double margin = 0.0;
 };
 // build g.val and g.y2 (allocated here) from host particles; returns an
 // rt3d status and sets err on failure
@@ -341,7 +350,8 @@ void grid_free(GridDev &g);
 // FP32 pairs in the pair-sum partial layout (one split); 1: -F as FP64
 // partials; 2: F at out[4 i + f]
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
-                             int mode, void *out, const unsigned long long *gate, cudaStream_t st);
+                             int mode, void *out, const unsigned long long *gate, cudaStream_t st,
+                             int group = 1);
 
 // Born approximation (born.cu): scratch size and the run over node chunks of
 // K nodes with the Hessian pair sum split `splits` ways; d_out = n_b x 3

@@ -120,3 +120,53 @@ def test_grid_errors(P):
     buf = np.zeros(4)
     rc = ctx.L.rt3d_grid_nodes(ctx.h, 1, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
     assert rc == P._binding.EINVAL  # not a grid field
+
+
+def _box(n_rep=3):
+    L = inputs.box_length(20.0 / 0.7)
+    pos, mass, _ = inputs.halo_box(3000, L, 8, inputs.BASE_SEED + 61)
+    rot, shift = inputs.replicas(n_rep, L, inputs.BASE_SEED + 61)
+    return pos, mass, rot, shift, L
+
+
+def test_box_grid_matches_oracle(P, cosmo):
+    pos, mass, rot, shift, L = _box()
+    cubes, n, soft = 4, 16, 0.02
+    bg = G.BoxGridField(pos, mass, soft, L, rot, shift, cubes=cubes, n=n)
+    ctx = P.Context(0, precision=P.FP64)
+    ctx.set_cosmology(0.3, 0.7, 0.7)
+    ctx.load_grid_box(0, pos, mass, soft, L, rot, shift, cubes, n)
+    nodes = ctx.grid_nodes(0)
+    for c, gf in enumerate(bg.grids):
+        for f in range(4):
+            assert np.max(np.abs(nodes[c, f] - gf.val[f])) <= 1e-11 * max(np.max(np.abs(gf.val[f])), 1e-300), (c, f)
+    W = L / cubes
+    g = inputs.rng(8)
+    pts = np.stack([g.uniform(-0.6, 0.6, 400) * W, g.uniform(-0.6, 0.6, 400) * W, g.uniform(0, 3 * L, 400)], 1)
+    want = oracle.potential(bg.field(), pts)
+    got = ctx.potential(0, pts)
+    assert np.all(np.abs(got - want) <= 1e-11 * np.max(np.abs(want), axis=0))
+    # traces: bundles within the prism, crossing several cubes and replicas
+    chi_s = 2.6 * L
+    z_s = cosmo.z_of_chi(chi_s)
+    th = g.uniform(-0.3, 0.3, (12, 2)) * W / chi_s
+    kw = dict(n_ring=4, theta_r=4.8e-6, schedule=0, n_steps=150)
+    o = oracle.trace(cosmo, bg.field(), z_s, th, **kw)
+    for prec, tol_mu, tol_a in ((P.FP64, 1e-9, 1e-8), (P.MIXED, 1e-7, 1e-5)):
+        c2 = P.Context(0, precision=prec)
+        c2.set_cosmology(0.3, 0.7, 0.7)
+        c2.load_grid_box(1, pos, mass, soft, L, rot, shift, cubes, n)
+        r = c2.trace(1, z_s, th, want_rays=True, **kw)
+        assert np.array_equal(r["flags"], o.flags) and np.array_equal(r["steps"], o.steps)
+        assert rel_mu(r["mu"], o.mu).max() < tol_mu
+        assert rel_alpha(r["rays"], o).max() < tol_a
+
+
+def test_box_grid_errors(P):
+    pos, mass, rot, shift, L = _box()
+    ctx = P.Context(0, precision=P.MIXED)
+    ctx.set_cosmology(0.3, 0.7, 0.7)
+    with pytest.raises(P.Rt3dError):
+        ctx.load_grid_box(0, pos, mass, 0.02, L, rot, shift, 0, 16)
+    with pytest.raises(P.Rt3dError):
+        ctx.load_grid_box(0, pos + L, mass, 0.02, L, rot, shift, 4, 16)  # outside [0, L)
