@@ -141,6 +141,9 @@ def run_grid(args):
     import paper_1110_4894_gb300 as P
     dev = torch.device("cuda", 0)
     cfg, name = workload(full=not args.small)
+    if args.rk4_steps:
+        cfg["n_steps"] = args.rk4_steps
+        name = name.rsplit("_", 1)[0] + "_%ds" % args.rk4_steps
     n = args.grid_n
     r200c = cfg["info"]["r200_phys"] * (1 + cfg["z_l"])
     half = 2.2 * r200c

@@ -1507,70 +1507,11 @@ extern "C" int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const 
     G.W = L / cubes;
     G.h = G.W / (g->n - 1);
     G.margin = 1.0;
-    const size_t stride = 4 * (size_t)g->n * g->n * g->n;
-    CK(cudaMalloc(&G.val, sizeof(double) * stride * (size_t)R * cubes));
-    CK(cudaMalloc(&G.y2, sizeof(double) * stride * (size_t)R * cubes));
-    // replica j: the box rotated about its centre by rot[j], shifted by shift[j]
-    // with periodic wrap, centred on the optical axis at x3 in [jL, (j+1)L)
-    const double c = 0.5 * L;
-    std::vector<std::vector<double>> cp((size_t)cubes), cm((size_t)cubes);
-    for (int j = 0; j < R; ++j) {
-        const int32_t *Rm = vol->rot + 9 * j;
-        const double *sh = vol->shift + 3 * j;
-        for (int q = 0; q < cubes; ++q) {
-            cp[q].clear();
-            cm[q].clear();
-        }
-        for (int64_t i = 0; i < n; ++i) {
-            const double *p = pos + 3 * i;
-            double w[3];
-            for (int r = 0; r < 3; ++r) {
-                double v = 0.0;
-                for (int k = 0; k < 3; ++k) v += (double)Rm[3 * r + k] * (p[k] - c);
-                v = v + c + sh[r];
-                while (v >= L) v -= L;
-                while (v < 0.0) v += L;
-                w[r] = v;
-            }
-            w[0] -= c;
-            w[1] -= c;
-            w[2] += (double)j * L;
-            if (!(w[0] >= -0.5 * G.W && w[0] < 0.5 * G.W && w[1] >= -0.5 * G.W && w[1] < 0.5 * G.W)) continue;
-            for (int q = 0; q < cubes; ++q) {
-                const double z0 = (double)j * L + (double)q * G.W;
-                if (w[2] >= z0 && w[2] < z0 + G.W) {
-                    cp[q].insert(cp[q].end(), w, w + 3);
-                    cm[q].push_back(mass[i]);
-                    break;
-                }
-            }
-        }
-        for (int q = 0; q < cubes; ++q) {
-            GridDev one;
-            one.n = g->n;
-            one.n_int = g->n_int;
-            one.h = G.h;
-            one.lo[0] = -0.5 * G.W;
-            one.lo[1] = -0.5 * G.W;
-            one.lo[2] = (double)j * L + (double)q * G.W;
-            int rc = grid_build(one, (int64_t)cm[q].size(), cp[q].data(), cm[q].data(), soft,
-                                g->mean_subtract ? 1 : 0, ctx->stream, ctx->err);
-            if (rc == RT3D_OK) {
-                const size_t off = ((size_t)j * cubes + q) * stride;
-                cudaError_t e = cudaMemcpyAsync(G.val + off, one.val, sizeof(double) * stride, cudaMemcpyDeviceToDevice,
-                                                ctx->stream);
-                if (e == cudaSuccess)
-                    e = cudaMemcpyAsync(G.y2 + off, one.y2, sizeof(double) * stride, cudaMemcpyDeviceToDevice,
-                                        ctx->stream);
-                if (e == cudaSuccess) e = cudaStreamSynchronize(ctx->stream);
-                if (e != cudaSuccess) rc = fail(ctx, RT3D_ECUDA, cudaGetErrorString(e));
-            }
-            grid_free(one);
-            if (rc != RT3D_OK) {
-                free_field(fs);
-                return rc;
-            }
-        }
+    int rc = grid_build_box(G, n, pos, mass, soft, vol->rot, vol->shift, g->mean_subtract ? 1 : 0, ctx->stream,
+                            ctx->err);
+    if (rc != RT3D_OK) {
+        free_field(fs);
+        return rc;
     }
     DevField &df = fs.df;
     df = DevField{};
@@ -1594,9 +1535,17 @@ extern "C" int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out)
     if (!fs.is_grid) return fail(ctx, RT3D_EINVAL, "not a grid field");
     if (!out) return fail(ctx, RT3D_EINVAL, "null output");
     CK(cudaSetDevice(ctx->device));
-    const size_t m = 4 * (size_t)fs.gd.n * fs.gd.n * fs.gd.n * (fs.gd.cubes > 0 ? (size_t)fs.gd.cubes * fs.gd.n_rep : 1);
-    CK(cudaMemcpyAsync(out, fs.gd.val, m * sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
-    CK(cudaStreamSynchronize(ctx->stream));
+    const size_t n3 = (size_t)fs.gd.n * fs.gd.n * fs.gd.n;
+    const size_t cells = fs.gd.cubes > 0 ? (size_t)fs.gd.cubes * fs.gd.n_rep : 1;
+    std::vector<double> tab(kGridRec * n3);
+    for (size_t c = 0; c < cells; ++c) {
+        CK(cudaMemcpyAsync(tab.data(), fs.gd.tab + c * kGridRec * n3, tab.size() * sizeof(double),
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        CK(cudaStreamSynchronize(ctx->stream));
+        double *o = out + c * 4 * n3;
+        for (size_t i = 0; i < n3; ++i)
+            for (int f = 0; f < 4; ++f) o[f * n3 + i] = tab[kGridRec * i + f];
+    }
     return RT3D_OK;
 }
 

@@ -13,9 +13,17 @@
 //      (App. B: computed once).
 // Per RK4 stage, App. B's interpolation at every ray: along x3 from the
 // global line splines, then natural splines through the 2 n_int nodes around
-// the ray along x1 and along x2.  One thread per (point, field); the four
-// fields of a point are blockIdx.y = 0..3.
+// the ray along x1 and along x2.  A natural spline through unit-spaced values
+// is linear in them, so the x1 and x2 splines are applied as weight vectors
+// (computed once per point) to the four fields at once.  One thread per point;
+// the node table keeps, per node, the four field values and their x3-spline
+// second derivatives side by side (64 bytes), so the two nodes a point reads on
+// each x3 line are one contiguous 128-byte span.
 #include <cufft.h>
+
+#include <algorithm>
+#include <thread>
+#include <vector>
 
 #include "rt3d_internal.cuh"
 
@@ -108,12 +116,13 @@ __global__ void k_fill_kernel(int n, int f, double h, double eps2, double *__res
     }
 }
 
-__global__ void k_cmul(int64_t m, const cufftDoubleComplex *__restrict__ a, cufftDoubleComplex *__restrict__ b,
-                       double scale)
+// out = a b scale (out may be b)
+__global__ void k_cmul(int64_t m, const cufftDoubleComplex *__restrict__ a, const cufftDoubleComplex *b,
+                       cufftDoubleComplex *out, double scale)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < m; i += (int64_t)gridDim.x * blockDim.x) {
         const cufftDoubleComplex x = a[i], y = b[i];
-        b[i] = make_cuDoubleComplex((x.x * y.x - x.y * y.y) * scale, (x.x * y.y + x.y * y.x) * scale);
+        out[i] = make_cuDoubleComplex((x.x * y.x - x.y * y.y) * scale, (x.x * y.y + x.y * y.x) * scale);
     }
 }
 
@@ -156,70 +165,82 @@ __global__ void k_spline_lines(int n, int64_t lines, const double *__restrict__ 
     for (int i = n - 3; i >= 1; --i) z[i] = z[i] - z[i + 1] / s_den[i];
 }
 
+// node table: per node the four values, then the four x3-spline second
+// derivatives (kGridRec doubles)
+__global__ void k_interleave(int64_t n3, const double *__restrict__ val, const double *__restrict__ y2,
+                             double *__restrict__ tab)
+{
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        double2 *t = reinterpret_cast<double2 *>(tab + kGridRec * i);
+        t[0] = make_double2(val[i], val[n3 + i]);
+        t[1] = make_double2(val[2 * n3 + i], val[3 * n3 + i]);
+        t[2] = make_double2(y2[i], y2[n3 + i]);
+        t[3] = make_double2(y2[2 * n3 + i], y2[3 * n3 + i]);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // App. B evaluation
 // ---------------------------------------------------------------------------
-__device__ __forceinline__ double splint_at(const double *y, const double *y2, int m, double u)
-{
-    int k = (int)floor(u);
-    k = k > m - 2 ? m - 2 : k;
-    k = k < 0 ? 0 : k;
-    const double A = (double)(k + 1) - u, B = u - (double)k;
-    return A * y[k] + B * y[k + 1] + ((A * A * A - A) * y2[k] + (B * B * B - B) * y2[k + 1]) / 6.0;
-}
-
-// natural spline through W unit-spaced values, evaluated at u in [0, W-1]
+// Weights c of the natural cubic spline through W unit-spaced values y,
+// evaluated at u in [0, W-1]: S(u) = sum_j c[j] y[j].  The second derivatives
+// z of the spline through the unit vector e_j solve the same tridiagonal
+// system as any data (z[i-1] + 4 z[i] + z[i+1] = 6 (e[i+1] - 2 e[i] + e[i-1]),
+// z = 0 at the ends); they are constants of W.
 template <int W>
-__device__ __forceinline__ double local_spline(const double (&t)[W], double u)
+__device__ __forceinline__ void spline_weights(double u, double (&c)[W])
 {
-    double z[W];
-    z[0] = 0.0;
-    z[W - 1] = 0.0;
-    if (W >= 3) {
-        double den[W], dp = 0.0, cp = 0.0;
-#pragma unroll
-        for (int i = 1; i <= W - 2; ++i) {
-            den[i] = 4.0 - cp;
-            cp = 1.0 / den[i];
-            dp = (6.0 * (t[i + 1] - 2.0 * t[i] + t[i - 1]) - dp) / den[i];
-            z[i] = dp;
-        }
-#pragma unroll
-        for (int i = W - 3; i >= 1; --i) z[i] = z[i] - z[i + 1] / den[i];
-    }
     int k = (int)floor(u);
     k = k > W - 2 ? W - 2 : k;
     k = k < 0 ? 0 : k;
     const double A = (double)(k + 1) - u, B = u - (double)k;
-    double yk = t[0], yk1 = t[1], zk = z[0], zk1 = z[1];
+    const double cA = (A * A * A - A) / 6.0, cB = (B * B * B - B) / 6.0;
 #pragma unroll
-    for (int i = 1; i < W - 1; ++i)
-        if (k == i) {
-            yk = t[i];
-            yk1 = t[i + 1];
-            zk = z[i];
-            zk1 = z[i + 1];
+    for (int j = 0; j < W; ++j) {
+        double z[W];
+        z[0] = 0.0;
+        z[W - 1] = 0.0;
+        if (W >= 3) {
+            double den[W], dp = 0.0, cp = 0.0;
+#pragma unroll
+            for (int i = 1; i <= W - 2; ++i) {
+                const double e = (i + 1 == j ? 1.0 : 0.0) - 2.0 * (i == j ? 1.0 : 0.0) + (i - 1 == j ? 1.0 : 0.0);
+                den[i] = 4.0 - cp;
+                cp = 1.0 / den[i];
+                dp = (6.0 * e - dp) / den[i];
+                z[i] = dp;
+            }
+#pragma unroll
+            for (int i = W - 3; i >= 1; --i) z[i] = z[i] - z[i + 1] / den[i];
         }
-    return A * yk + B * yk1 + ((A * A * A - A) * zk + (B * B * B - B) * zk1) / 6.0;
+        double zk = z[0], zk1 = z[1];
+#pragma unroll
+        for (int i = 1; i < W - 1; ++i)
+            if (k == i) {
+                zk = z[i];
+                zk1 = z[i + 1];
+            }
+        c[j] = (j == k ? A : 0.0) + (j == k + 1 ? B : 0.0) + (cA * zk + cB * zk1);
+    }
 }
 
 // group: points per bundle; a cube-tiled box takes the cube holding the x3
 // of the group's first point (the bundle's central ray), as the direct sum
 // takes its replica
 template <int NI>
-__global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const double *__restrict__ py,
-                            const double *__restrict__ pz, int64_t n_pts, int mode, void *__restrict__ out,
-                            const unsigned long long *__restrict__ gate, int group)
+__global__ void __launch_bounds__(128) k_grid_eval(GridDev g, const double *__restrict__ px,
+                                                   const double *__restrict__ py, const double *__restrict__ pz,
+                                                   int64_t n_pts, int mode, void *__restrict__ out,
+                                                   const unsigned long long *__restrict__ gate, int group)
 {
     constexpr int W = 2 * NI;
     if (gate && *gate == 0ull) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    const int f = blockIdx.y;
     if (i >= n_pts) return;
     const int n = g.n;
     const double r[3] = {px[i], py[i], pz[i]};
     double lo[3] = {g.lo[0], g.lo[1], g.lo[2]};
-    const double *val = g.val, *y2t = g.y2;
+    const double *tab = g.tab;
     if (g.cubes > 0) {
         const double x3 = pz[(i / group) * group];
         double q = floor(x3 / g.L);
@@ -229,9 +250,7 @@ __global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const doub
         lo[0] = -0.5 * g.W;
         lo[1] = -0.5 * g.W;
         lo[2] = (double)j * g.L + (double)c * g.W;
-        const int64_t cell = (int64_t)j * g.cubes + c, stride = 4 * (int64_t)n * n * n;
-        val += cell * stride;
-        y2t += cell * stride;
+        tab += ((int64_t)j * g.cubes + c) * kGridRec * (int64_t)n * n * n;
     }
     double u[3];
     int s[3];
@@ -244,39 +263,53 @@ __global__ void k_grid_eval(GridDev g, const double *__restrict__ px, const doub
         sd = sd > n - W ? n - W : sd;
         s[d] = sd < 0 ? 0 : sd;
     }
-    double F = 0.0;
+    double F[4] = {0.0, 0.0, 0.0, 0.0};
     if (inside) {
-        const int64_t n3 = (int64_t)n * n * n;
-        const double *v = val + f * n3, *y2 = y2t + f * n3;
         int k3 = (int)floor(u[2]);
         k3 = k3 > n - 2 ? n - 2 : k3;
         k3 = k3 < 0 ? 0 : k3;
         const double A = (double)(k3 + 1) - u[2], B = u[2] - (double)k3;
         const double cA = (A * A * A - A) / 6.0, cB = (B * B * B - B) / 6.0;
-        double w2[W];
+        double c1[W], c2[W];
+        spline_weights<W>(u[0] - (double)s[0], c1);
+        spline_weights<W>(u[1] - (double)s[1], c2);
 #pragma unroll
         for (int b = 0; b < W; ++b) {
-            double t[W];
+            double acc[4] = {0.0, 0.0, 0.0, 0.0};
 #pragma unroll
             for (int a = 0; a < W; ++a) {
-                // step 1: along x3 on node line (s1 + a, s2 + b), global spline
-                const int64_t line = ((int64_t)(s[0] + a) * n + (s[1] + b)) * n + k3;
-                t[a] = A * v[line] + B * v[line + 1] + (cA * y2[line] + cB * y2[line + 1]);
+                // along x3 on node line (s1 + a, s2 + b): the global spline
+                // from nodes k3 and k3 + 1 (values, then second derivatives)
+                const int64_t node = ((int64_t)(s[0] + a) * n + (s[1] + b)) * n + k3;
+                const double2 *p = reinterpret_cast<const double2 *>(tab + kGridRec * node);
+                const double2 v01 = __ldg(p), v23 = __ldg(p + 1), y01 = __ldg(p + 2), y23 = __ldg(p + 3);
+                const double2 w01 = __ldg(p + 4), w23 = __ldg(p + 5), z01 = __ldg(p + 6), z23 = __ldg(p + 7);
+                const double t0 = A * v01.x + B * w01.x + (cA * y01.x + cB * z01.x);
+                const double t1 = A * v01.y + B * w01.y + (cA * y01.y + cB * z01.y);
+                const double t2 = A * v23.x + B * w23.x + (cA * y23.x + cB * z23.x);
+                const double t3 = A * v23.y + B * w23.y + (cA * y23.y + cB * z23.y);
+                // along x1
+                acc[0] += c1[a] * t0;
+                acc[1] += c1[a] * t1;
+                acc[2] += c1[a] * t2;
+                acc[3] += c1[a] * t3;
             }
-            // steps 2-3: along x1
-            w2[b] = local_spline<W>(t, u[0] - (double)s[0]);
+            // along x2
+#pragma unroll
+            for (int f = 0; f < 4; ++f) F[f] += c2[b] * acc[f];
         }
-        // steps 4-5: along x2
-        F = local_spline<W>(w2, u[1] - (double)s[1]);
     }
-    if (mode == 2) {
-        ((double *)out)[4 * i + f] = F;
-    } else if (mode == 1) {
-        ((double *)out)[(int64_t)f * n_pts + i] = -F;
-    } else {
-        const float hi = (float)(-F);
-        const float lo = (float)(-F - (double)hi);
-        ((float2 *)out)[(int64_t)f * n_pts + i] = make_float2(hi, lo);
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+        if (mode == 2) {
+            ((double *)out)[4 * i + f] = F[f];
+        } else if (mode == 1) {
+            ((double *)out)[(int64_t)f * n_pts + i] = -F[f];
+        } else {
+            const float hi = (float)(-F[f]);
+            const float lo2 = (float)(-F[f] - (double)hi);
+            ((float2 *)out)[(int64_t)f * n_pts + i] = make_float2(hi, lo2);
+        }
     }
 }
 
@@ -284,7 +317,7 @@ cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *p
                              int mode, void *out, const unsigned long long *gate, cudaStream_t st, int group)
 {
     if (n <= 0) return cudaSuccess;
-    const dim3 grid((unsigned)((n + 127) / 128), 4);
+    const unsigned grid = (unsigned)((n + 127) / 128);
     switch (g.n_int) {
     case 1: k_grid_eval<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
     case 2: k_grid_eval<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
@@ -300,9 +333,8 @@ cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *p
 // ---------------------------------------------------------------------------
 void grid_free(GridDev &g)
 {
-    cudaFree(g.val);
-    cudaFree(g.y2);
-    g.val = g.y2 = nullptr;
+    cudaFree(g.tab);
+    g.tab = nullptr;
 }
 
 static unsigned blocks_for(int64_t m)
@@ -312,101 +344,225 @@ static unsigned blocks_for(int64_t m)
 }
 
 namespace {
-struct Tmp {  // temporary device buffers of a build, freed on every exit
-    double *pos = nullptr, *mass = nullptr, *buf = nullptr;
+// Device state for building grids of one shape (n nodes per side, spacing h,
+// softening eps): FFT buffers and plans, node-mass and value temporaries, and
+// (when cache_kernels) the four kernel spectra, which depend on the shape
+// only and so serve every cube of a replicated box.  Freed on every exit.
+struct Builder {
+    int n = 0;
+    double h = 0.0, eps2 = 0.0;
+    bool cache = false, have_k = false;
+    double *pos = nullptr, *mass = nullptr, *buf = nullptr, *val = nullptr, *y2 = nullptr;
+    int64_t cap = 0;
     unsigned long long *q = nullptr, *total = nullptr;
-    cufftDoubleComplex *fm = nullptr, *fk = nullptr;
+    cufftDoubleComplex *fm = nullptr, *fk = nullptr, *kspec = nullptr;
     cufftHandle r2c = 0, c2r = 0;
     bool have_r2c = false, have_c2r = false;
-    ~Tmp()
+    std::string *err = nullptr;
+    ~Builder()
     {
         cudaFree(pos);
         cudaFree(mass);
         cudaFree(buf);
+        cudaFree(val);
+        cudaFree(y2);
         cudaFree(q);
         cudaFree(total);
         cudaFree(fm);
         cudaFree(fk);
+        cudaFree(kspec);
         if (have_r2c) cufftDestroy(r2c);
         if (have_c2r) cufftDestroy(c2r);
     }
+    int cuda_fail(cudaError_t e, const char *what)
+    {
+        *err = std::string(what) + ": " + cudaGetErrorString(e);
+        return e == cudaErrorMemoryAllocation ? RT3D_ENOMEM : RT3D_ECUDA;
+    }
+    int fft_fail(cufftResult r, const char *what)
+    {
+        *err = std::string(what) + ": cuFFT error " + std::to_string((int)r);
+        return r == CUFFT_ALLOC_FAILED ? RT3D_ENOMEM : RT3D_ECUDA;
+    }
+    int64_t P3() const { return 8 * (int64_t)n * n * n; }
+    int64_t Pc() const { return 4 * (int64_t)n * n * (n + 1); }
+    int64_t n3() const { return (int64_t)n * n * n; }
 };
 }  // namespace
 
-int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, double soft, int mean_subtract,
-               cudaStream_t st, std::string &err)
+#define GCK(x, what)                                        \
+    do {                                                    \
+        cudaError_t e_ = (x);                               \
+        if (e_ != cudaSuccess) return B.cuda_fail(e_, what); \
+    } while (0)
+#define FCK(x, what)                                        \
+    do {                                                    \
+        cufftResult r_ = (x);                               \
+        if (r_ != CUFFT_SUCCESS) return B.fft_fail(r_, what); \
+    } while (0)
+
+static int builder_init(Builder &B, int n, double h, double soft, bool cache_kernels, cudaStream_t st,
+                        std::string &err)
 {
-    const int n = g.n, P = 2 * n;
-    const int64_t n3 = (int64_t)n * n * n, P3 = (int64_t)P * P * P, Pc = (int64_t)P * P * (P / 2 + 1);
-    Tmp t;
-    auto cuda_fail = [&](cudaError_t e, const char *what) {
-        err = std::string(what) + ": " + cudaGetErrorString(e);
-        return e == cudaErrorMemoryAllocation ? RT3D_ENOMEM : RT3D_ECUDA;
-    };
-#define GCK(x, what)                                       \
-    do {                                                   \
-        cudaError_t e_ = (x);                              \
-        if (e_ != cudaSuccess) return cuda_fail(e_, what); \
-    } while (0)
-#define FCK(x, what)                                                      \
-    do {                                                                  \
-        cufftResult r_ = (x);                                             \
-        if (r_ != CUFFT_SUCCESS) {                                        \
-            err = std::string(what) + ": cuFFT error " + std::to_string((int)r_); \
-            return r_ == CUFFT_ALLOC_FAILED ? RT3D_ENOMEM : RT3D_ECUDA;   \
-        }                                                                 \
-    } while (0)
+    B.n = n;
+    B.h = h;
+    B.eps2 = soft * soft;
+    B.err = &err;
+    const int P = 2 * n;
+    // the four kernel spectra stay resident only where they are small
+    B.cache = cache_kernels && 4 * B.Pc() * (int64_t)sizeof(cufftDoubleComplex) <= ((int64_t)2 << 30);
+    GCK(cudaMalloc(&B.q, sizeof(unsigned long long) * (size_t)B.n3()), "grid node buffer");
+    GCK(cudaMalloc(&B.total, sizeof(unsigned long long)), "grid total");
+    GCK(cudaMalloc(&B.buf, sizeof(double) * (size_t)B.P3()), "grid FFT buffer");
+    GCK(cudaMalloc(&B.fm, sizeof(cufftDoubleComplex) * (size_t)B.Pc()), "grid FFT buffer");
+    GCK(cudaMalloc(&B.fk, sizeof(cufftDoubleComplex) * (size_t)B.Pc()), "grid FFT buffer");
+    GCK(cudaMalloc(&B.val, sizeof(double) * 4 * (size_t)B.n3()), "grid values");
+    GCK(cudaMalloc(&B.y2, sizeof(double) * 4 * (size_t)B.n3()), "grid spline table");
+    if (B.cache) GCK(cudaMalloc(&B.kspec, sizeof(cufftDoubleComplex) * 4 * (size_t)B.Pc()), "grid kernel spectra");
+    FCK(cufftPlan3d(&B.r2c, P, P, P, CUFFT_D2Z), "cufftPlan3d D2Z");
+    B.have_r2c = true;
+    FCK(cufftPlan3d(&B.c2r, P, P, P, CUFFT_Z2D), "cufftPlan3d Z2D");
+    B.have_c2r = true;
+    FCK(cufftSetStream(B.r2c, st), "cufftSetStream");
+    FCK(cufftSetStream(B.c2r, st), "cufftSetStream");
+    return RT3D_OK;
+}
+
+// one grid: the particles' CIC node masses on the nodes lo + h i, optionally
+// minus their mean, convolved with the four Plummer kernels; the node table
+// (kGridRec n^3 doubles) goes to dest
+static int builder_run(Builder &B, int64_t np, const double *pos, const double *mass, const double lo[3],
+                       int mean_subtract, double *dest, cudaStream_t st)
+{
+    const int n = B.n;
+    const int64_t n3 = B.n3(), P3 = B.P3(), Pc = B.Pc();
     // fixed-point scale: the node sums stay below 2^62 for any assignment
     double msum = 0.0;
     for (int64_t i = 0; i < np; ++i) msum += mass[i];
     const int e = msum > 0.0 ? 61 - (int)ceil(log2(msum)) : 0;
     const double qscale = ldexp(1.0, e), qinv = ldexp(1.0, -e);
-    GCK(cudaMalloc(&t.q, sizeof(unsigned long long) * (size_t)n3), "grid node buffer");
-    GCK(cudaMalloc(&t.total, sizeof(unsigned long long)), "grid total");
-    GCK(cudaMemsetAsync(t.q, 0, sizeof(unsigned long long) * (size_t)n3, st), "memset");
-    GCK(cudaMemsetAsync(t.total, 0, sizeof(unsigned long long), st), "memset");
+    GCK(cudaMemsetAsync(B.q, 0, sizeof(unsigned long long) * (size_t)n3, st), "memset");
+    GCK(cudaMemsetAsync(B.total, 0, sizeof(unsigned long long), st), "memset");
     if (np > 0) {
-        GCK(cudaMalloc(&t.pos, sizeof(double) * 3 * (size_t)np), "particle upload");
-        GCK(cudaMalloc(&t.mass, sizeof(double) * (size_t)np), "particle upload");
-        GCK(cudaMemcpyAsync(t.pos, pos, sizeof(double) * 3 * (size_t)np, cudaMemcpyHostToDevice, st), "upload");
-        GCK(cudaMemcpyAsync(t.mass, mass, sizeof(double) * (size_t)np, cudaMemcpyHostToDevice, st), "upload");
-        k_cic<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(np, t.pos, t.mass, g.lo[0], g.lo[1], g.lo[2], 1.0 / g.h, n,
-                                                             qscale, t.q);
+        if (np > B.cap) {
+            GCK(cudaStreamSynchronize(st), "grid build");
+            cudaFree(B.pos);
+            cudaFree(B.mass);
+            B.pos = B.mass = nullptr;
+            B.cap = 0;
+            GCK(cudaMalloc(&B.pos, sizeof(double) * 3 * (size_t)np), "particle upload");
+            GCK(cudaMalloc(&B.mass, sizeof(double) * (size_t)np), "particle upload");
+            B.cap = np;
+        }
+        GCK(cudaMemcpyAsync(B.pos, pos, sizeof(double) * 3 * (size_t)np, cudaMemcpyHostToDevice, st), "upload");
+        GCK(cudaMemcpyAsync(B.mass, mass, sizeof(double) * (size_t)np, cudaMemcpyHostToDevice, st), "upload");
+        k_cic<<<(unsigned)((np + 255) / 256), 256, 0, st>>>(np, B.pos, B.mass, lo[0], lo[1], lo[2], 1.0 / B.h, n,
+                                                             qscale, B.q);
         GCK(cudaGetLastError(), "k_cic");
     }
-    k_sum_q<<<blocks_for(n3), 256, 0, st>>>(n3, t.q, t.total);
+    k_sum_q<<<blocks_for(n3), 256, 0, st>>>(n3, B.q, B.total);
     GCK(cudaGetLastError(), "k_sum_q");
-    GCK(cudaMalloc(&t.buf, sizeof(double) * (size_t)P3), "grid FFT buffer");
-    GCK(cudaMalloc(&t.fm, sizeof(cufftDoubleComplex) * (size_t)Pc), "grid FFT buffer");
-    GCK(cudaMalloc(&t.fk, sizeof(cufftDoubleComplex) * (size_t)Pc), "grid FFT buffer");
-    GCK(cudaMalloc(&g.val, sizeof(double) * 4 * (size_t)n3), "grid values");
-    GCK(cudaMalloc(&g.y2, sizeof(double) * 4 * (size_t)n3), "grid spline table");
-    FCK(cufftPlan3d(&t.r2c, P, P, P, CUFFT_D2Z), "cufftPlan3d D2Z");
-    t.have_r2c = true;
-    FCK(cufftPlan3d(&t.c2r, P, P, P, CUFFT_Z2D), "cufftPlan3d Z2D");
-    t.have_c2r = true;
-    FCK(cufftSetStream(t.r2c, st), "cufftSetStream");
-    FCK(cufftSetStream(t.c2r, st), "cufftSetStream");
-    k_fill_mass<<<blocks_for(P3), 256, 0, st>>>(n, t.q, t.total, qinv, mean_subtract, t.buf);
+    k_fill_mass<<<blocks_for(P3), 256, 0, st>>>(n, B.q, B.total, qinv, mean_subtract, B.buf);
     GCK(cudaGetLastError(), "k_fill_mass");
-    FCK(cufftExecD2Z(t.r2c, t.buf, t.fm), "cufftExecD2Z");
+    FCK(cufftExecD2Z(B.r2c, B.buf, B.fm), "cufftExecD2Z");
     for (int f = 0; f < 4; ++f) {
-        k_fill_kernel<<<blocks_for(P3), 256, 0, st>>>(n, f, g.h, soft * soft, t.buf);
-        GCK(cudaGetLastError(), "k_fill_kernel");
-        FCK(cufftExecD2Z(t.r2c, t.buf, t.fk), "cufftExecD2Z");
-        k_cmul<<<blocks_for(Pc), 256, 0, st>>>(Pc, t.fm, t.fk, 1.0 / (double)P3);
+        cufftDoubleComplex *ks = B.cache ? B.kspec + f * Pc : B.fk;
+        if (!B.cache || !B.have_k) {
+            k_fill_kernel<<<blocks_for(P3), 256, 0, st>>>(n, f, B.h, B.eps2, B.buf);
+            GCK(cudaGetLastError(), "k_fill_kernel");
+            FCK(cufftExecD2Z(B.r2c, B.buf, ks), "cufftExecD2Z");
+        }
+        k_cmul<<<blocks_for(Pc), 256, 0, st>>>(Pc, B.fm, ks, B.fk, 1.0 / (double)P3);
         GCK(cudaGetLastError(), "k_cmul");
-        FCK(cufftExecZ2D(t.c2r, t.fk, t.buf), "cufftExecZ2D");
-        k_extract<<<blocks_for(n3), 256, 0, st>>>(n, t.buf, g.val + f * n3);
+        FCK(cufftExecZ2D(B.c2r, B.fk, B.buf), "cufftExecZ2D");
+        k_extract<<<blocks_for(n3), 256, 0, st>>>(n, B.buf, B.val + f * n3);
         GCK(cudaGetLastError(), "k_extract");
     }
+    B.have_k = B.cache;
     const int64_t lines = 4 * (int64_t)n * n;
-    k_spline_lines<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(n, lines, g.val, g.y2);
+    k_spline_lines<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(n, lines, B.val, B.y2);
     GCK(cudaGetLastError(), "k_spline_lines");
-    GCK(cudaStreamSynchronize(st), "grid build");
-#undef GCK
-#undef FCK
+    k_interleave<<<blocks_for(n3), 256, 0, st>>>(n3, B.val, B.y2, dest);
+    GCK(cudaGetLastError(), "k_interleave");
     return RT3D_OK;
 }
+
+int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, double soft, int mean_subtract,
+               cudaStream_t st, std::string &err)
+{
+    Builder B;
+    int rc = builder_init(B, g.n, g.h, soft, false, st, err);
+    if (rc != RT3D_OK) return rc;
+    GCK(cudaMalloc(&g.tab, sizeof(double) * kGridRec * (size_t)B.n3()), "grid node table");
+    rc = builder_run(B, np, pos, mass, g.lo, mean_subtract, g.tab, st);
+    if (rc != RT3D_OK) return rc;
+    GCK(cudaStreamSynchronize(st), "grid build");
+    return RT3D_OK;
+}
+
+int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass, double soft,
+                   const int32_t *rot, const double *shift, int mean_subtract, cudaStream_t st, std::string &err)
+{
+    const int R = g.n_rep, C = g.cubes;
+    const double L = g.L, W = g.W, c = 0.5 * L;
+    // every replica's prism particles, cube by cube (host threads over replicas)
+    std::vector<std::vector<double>> cp((size_t)R * C), cm((size_t)R * C);
+    auto select = [&](int j) {
+        const int32_t *Rm = rot + 9 * j;
+        const double *sh = shift + 3 * j;
+        for (int64_t i = 0; i < np; ++i) {
+            const double *p = pos + 3 * i;
+            double w[3];
+            for (int r = 0; r < 3; ++r) {
+                double v = 0.0;
+                for (int k = 0; k < 3; ++k) v += (double)Rm[3 * r + k] * (p[k] - c);
+                v = v + c + sh[r];
+                while (v >= L) v -= L;
+                while (v < 0.0) v += L;
+                w[r] = v;
+            }
+            w[0] -= c;
+            w[1] -= c;
+            w[2] += (double)j * L;
+            if (!(w[0] >= -0.5 * W && w[0] < 0.5 * W && w[1] >= -0.5 * W && w[1] < 0.5 * W)) continue;
+            for (int q = 0; q < C; ++q) {
+                const double z0 = (double)j * L + (double)q * W;
+                if (w[2] >= z0 && w[2] < z0 + W) {
+                    std::vector<double> &P = cp[(size_t)j * C + q];
+                    P.insert(P.end(), w, w + 3);
+                    cm[(size_t)j * C + q].push_back(mass[i]);
+                    break;
+                }
+            }
+        }
+    };
+    {
+        const int nt = std::max(1, std::min(R, (int)std::thread::hardware_concurrency()));
+        std::vector<std::thread> th;
+        for (int t = 0; t < nt; ++t)
+            th.emplace_back([&, t] {
+                for (int j = t; j < R; j += nt) select(j);
+            });
+        for (auto &x : th) x.join();
+    }
+    Builder B;
+    int rc = builder_init(B, g.n, g.h, soft, true, st, err);
+    if (rc != RT3D_OK) return rc;
+    const size_t stride = kGridRec * (size_t)B.n3();
+    GCK(cudaMalloc(&g.tab, sizeof(double) * stride * (size_t)R * C), "grid node tables");
+    for (int j = 0; j < R; ++j)
+        for (int q = 0; q < C; ++q) {
+            const size_t cell = (size_t)j * C + q;
+            const double lo[3] = {-0.5 * W, -0.5 * W, (double)j * L + (double)q * W};
+            rc = builder_run(B, (int64_t)cm[cell].size(), cp[cell].data(), cm[cell].data(), lo, mean_subtract,
+                             g.tab + cell * stride, st);
+            if (rc != RT3D_OK) return rc;
+            // the host lists of this cube must outlive its asynchronous upload
+            GCK(cudaStreamSynchronize(st), "grid build");
+        }
+    return RT3D_OK;
+}
+#undef GCK
+#undef FCK
 
 }  // namespace rt3d

@@ -326,14 +326,17 @@ cudaError_t launch_stage_field(const DevField &f, const ForceShape &sh, bool fp6
 
 // gridded field (Sec. 3.3 grid path, App. B): node values and x3 spline
 // second derivatives, 4 n^3 doubles each, [f][i1][i2][i3] with i3 fastest
+// doubles per grid node in the node table: phi, dphi/dx1, dphi/dx2, dphi/dx3,
+// then their natural-spline second derivatives along x3 (App. B)
+constexpr int kGridRec = 8;
 struct GridDev {
     int n = 0, n_int = 0;
     double lo[3] = {0.0, 0.0, 0.0};
     double h = 0.0;
-    double *val = nullptr, *y2 = nullptr;
-    // cube-tiled replicated box (cubes > 0): n_rep * cubes cube grids stored
-    // one after the other (stride 4 n^3) in val and y2; cube c of replica j
-    // has lo = (-W/2, -W/2, j L + c W) and spacing W / (n - 1)
+    double *tab = nullptr;  // [i1][i2][i3][kGridRec], i3 fastest
+    // cube-tiled replicated box (cubes > 0): n_rep * cubes node tables stored
+    // one after the other (stride kGridRec n^3), replica-major; cube c of
+    // replica j has lo = (-W/2, -W/2, j L + c W) and spacing W / (n - 1)
     int cubes = 0, n_rep = 1;
     double L = 0.0, W = 0.0;
     // points up to margin node spacings outside the node range take the end
@@ -341,10 +344,15 @@ struct GridDev {
     // face); farther out the field is zero
     double margin = 0.0;
 };
-// build g.val and g.y2 (allocated here) from host particles; returns an
-// rt3d status and sets err on failure
+// build g.tab (allocated here) from host particles; returns an rt3d status
+// and sets err on failure
 int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, double soft, int mean_subtract,
                cudaStream_t st, std::string &err);
+// build the n_rep * cubes node tables of a cube-tiled replicated box (g.n,
+// n_rep, cubes, L, W, h set by the caller; g.tab allocated here) from the
+// box's host particles, each replica placed by rot[9 j] and shift[3 j]
+int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass, double soft,
+                   const int32_t *rot, const double *shift, int mean_subtract, cudaStream_t st, std::string &err);
 void grid_free(GridDev &g);
 // App. B evaluation at n points (SoA px, py, pz).  mode 0: -F as (hi, lo)
 // FP32 pairs in the pair-sum partial layout (one split); 1: -F as FP64
