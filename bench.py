@@ -129,6 +129,13 @@ def run_cones(args):
     return 0
 
 
+# App. B evaluation of one ray on the mixed path: 2 n_int = 4 node lines per
+# transverse axis, two nodes per x3 line, eight FP32 numbers per node
+GRID_BYTES_PER_RAY = 4 * 4 * 2 * 8 * 4
+GRID_ROOFLINE_NOTE = ("algorithmic bytes = the FP32 node records one ray's interpolation reads (1 KB); "
+                      "neighbouring rays share them, so most reads hit L1/L2")
+
+
 def run_grid(args):
     """The grid path (Sec. 3.3, App. B) on the NFW workload: the halo's
     particles on an n^3 node grid spanning +-2.2 r200 (comoving), App. B
@@ -195,9 +202,14 @@ def run_grid(args):
     cd.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"])
     mu_dir = cd.trace(0, cfg["z_s"], cfg["theta"], **kw)["mu"]
     dmu = np.abs(mu_grid / mu_dir - 1)
+    # the FP64 grid path on the same bundles: the mixed path's FP32 interpolation error
+    c64 = P.Context(0, precision=P.FP64)
+    c64.set_cosmology(*cfg["cosmo"])
+    c64.load_grid(0, cfg["pos"], cfg["mass"], cfg["soft"], lo, h, n, n_int=2)
+    mu64 = c64.trace(0, cfg["z_s"], cfg["theta"], **kw)["mu"]
+    dmu64 = float(np.max(np.abs(mu_grid / mu64 - 1)))
     per_launch_s = eval_ms / 1e3 / max(1, eval_launches)
-    w = 4  # 2 n_int nodes per axis
-    bytes_per_launch = nb * (1 + cfg["n_ring"]) * 4 * w * w * 4 * 8  # (val, y2) x (k, k+1) per x3 spline
+    bytes_per_launch = nb * (1 + cfg["n_ring"]) * GRID_BYTES_PER_RAY
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
@@ -213,10 +225,11 @@ def run_grid(args):
            "field_evals_per_s": evals / dev_s,
            "roofline": {"bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9, "peak": hbm,
                         "unit": "GB/s", "frac": bytes_per_launch / per_launch_s / 1e9 / hbm, "traffic": None,
-                        "kernel": "k_grid_eval", "avg_launch_ms": per_launch_s * 1e3,
-                        "note": "algorithmic bytes = spline reads along x3 per ray and field; most hit L1/L2"},
+                        "kernel": "k_grid_eval32", "avg_launch_ms": per_launch_s * 1e3,
+                        "note": GRID_ROOFLINE_NOTE},
            "grid_vs_direct_sum": {"median_abs_dmu_over_mu": float(np.median(dmu)),
                                   "max_abs_dmu_over_mu": float(np.max(dmu))},
+           "mixed_vs_fp64_grid": {"bundles": nb, "max_abs_dmu_over_mu": dmu64},
            "clocks": clocks, "gpu_launches": int(launches)}
     print(json.dumps(out))
     return 0
@@ -277,9 +290,16 @@ def run_prism(args):
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
     scal = d_scal.cpu().numpy()
     res = d_bout.view(nb, 6).cpu().numpy()
+    # the FP64 grid path on the first bundles: the mixed path's FP32 interpolation error
+    k = min(nb, args.fp64_bundles)
+    c64 = P.Context(0, precision=P.FP64)
+    c64.set_cosmology(*cfg["cosmo"])
+    c64.load_grid_box(0, cfg["pos"], cfg["mass"], cfg["soft"], cfg["L"], cfg["rot"], cfg["shift"], cubes, n,
+                      n_int=2, mean_subtract=True)
+    mu64 = c64.trace(0, cfg["z_s"], cfg["theta"][:k], **kw)["mu"]
+    dmu64 = float(np.max(np.abs(res[:k, 0] / mu64 - 1)))
     per_launch_s = eval_ms / 1e3 / max(1, eval_launches)
-    w = 4
-    bytes_per_launch = nb * (1 + cfg["n_ring"]) * 4 * w * w * 4 * 8
+    bytes_per_launch = nb * (1 + cfg["n_ring"]) * GRID_BYTES_PER_RAY
     peaks = {}
     try:
         peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
@@ -299,8 +319,9 @@ def run_prism(args):
            "field_evals_per_s": evals / dev_s,
            "roofline": {"bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9, "peak": hbm,
                         "unit": "GB/s", "frac": bytes_per_launch / per_launch_s / 1e9 / hbm, "traffic": None,
-                        "kernel": "k_grid_eval", "avg_launch_ms": per_launch_s * 1e3,
-                        "note": "algorithmic bytes = spline reads along x3 per ray and field; most hit L1/L2"},
+                        "kernel": "k_grid_eval32", "avg_launch_ms": per_launch_s * 1e3,
+                        "note": GRID_ROOFLINE_NOTE},
+           "mixed_vs_fp64_grid": {"bundles": k, "max_abs_dmu_over_mu": dmu64},
            "mupdf": {"bundles_binned": int(scal[0]), "mean_w": float(scal[6]), "sigma_w": float(scal[7]),
                      "flagged_bundles": int(np.count_nonzero(res[:, 5]))},
            "clocks": clocks, "gpu_launches": int(launches)}

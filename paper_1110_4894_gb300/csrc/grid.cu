@@ -166,16 +166,21 @@ __global__ void k_spline_lines(int n, int64_t lines, const double *__restrict__ 
 }
 
 // node table: per node the four values, then the four x3-spline second
-// derivatives (kGridRec doubles)
+// derivatives (kGridRec doubles); tab32 holds the same numbers rounded to FP32
 __global__ void k_interleave(int64_t n3, const double *__restrict__ val, const double *__restrict__ y2,
-                             double *__restrict__ tab)
+                             double *__restrict__ tab, float *__restrict__ tab32)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
+        const double r[kGridRec] = {val[i], val[n3 + i], val[2 * n3 + i], val[3 * n3 + i],
+                                    y2[i],  y2[n3 + i],  y2[2 * n3 + i],  y2[3 * n3 + i]};
         double2 *t = reinterpret_cast<double2 *>(tab + kGridRec * i);
-        t[0] = make_double2(val[i], val[n3 + i]);
-        t[1] = make_double2(val[2 * n3 + i], val[3 * n3 + i]);
-        t[2] = make_double2(y2[i], y2[n3 + i]);
-        t[3] = make_double2(y2[2 * n3 + i], y2[3 * n3 + i]);
+        t[0] = make_double2(r[0], r[1]);
+        t[1] = make_double2(r[2], r[3]);
+        t[2] = make_double2(r[4], r[5]);
+        t[3] = make_double2(r[6], r[7]);
+        float4 *t32 = reinterpret_cast<float4 *>(tab32 + kGridRec * i);
+        t32[0] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+        t32[1] = make_float4((float)r[4], (float)r[5], (float)r[6], (float)r[7]);
     }
 }
 
@@ -313,11 +318,130 @@ __global__ void __launch_bounds__(128) k_grid_eval(GridDev g, const double *__re
     }
 }
 
+// The mixed path's evaluation: the same interpolation from the FP32 node
+// table with FP32 weights and sums; the point's cube, node window and
+// fractional offsets come from FP64 coordinates.  Output as mode 0 (hi = F,
+// lo = 0).
+template <int W>
+__device__ __forceinline__ void spline_weights_f(float u, float (&c)[W])
+{
+    int k = (int)floorf(u);
+    k = k > W - 2 ? W - 2 : k;
+    k = k < 0 ? 0 : k;
+    const float A = (float)(k + 1) - u, B = u - (float)k;
+    const float cA = (A * A * A - A) * (1.0f / 6.0f), cB = (B * B * B - B) * (1.0f / 6.0f);
+#pragma unroll
+    for (int j = 0; j < W; ++j) {
+        float z[W];
+        z[0] = 0.0f;
+        z[W - 1] = 0.0f;
+        if (W >= 3) {
+            float den[W], dp = 0.0f, cp = 0.0f;
+#pragma unroll
+            for (int i = 1; i <= W - 2; ++i) {
+                const float e = (i + 1 == j ? 1.0f : 0.0f) - 2.0f * (i == j ? 1.0f : 0.0f) + (i - 1 == j ? 1.0f : 0.0f);
+                den[i] = 4.0f - cp;
+                cp = 1.0f / den[i];
+                dp = (6.0f * e - dp) / den[i];
+                z[i] = dp;
+            }
+#pragma unroll
+            for (int i = W - 3; i >= 1; --i) z[i] = z[i] - z[i + 1] / den[i];
+        }
+        float zk = z[0], zk1 = z[1];
+#pragma unroll
+        for (int i = 1; i < W - 1; ++i)
+            if (k == i) {
+                zk = z[i];
+                zk1 = z[i + 1];
+            }
+        c[j] = (j == k ? A : 0.0f) + (j == k + 1 ? B : 0.0f) + (cA * zk + cB * zk1);
+    }
+}
+
+template <int NI>
+__global__ void __launch_bounds__(128) k_grid_eval32(GridDev g, const double *__restrict__ px,
+                                                     const double *__restrict__ py, const double *__restrict__ pz,
+                                                     int64_t n_pts, float2 *__restrict__ out,
+                                                     const unsigned long long *__restrict__ gate, int group)
+{
+    constexpr int W = 2 * NI;
+    if (gate && *gate == 0ull) return;
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n_pts) return;
+    const int n = g.n;
+    const double r[3] = {px[i], py[i], pz[i]};
+    double lo[3] = {g.lo[0], g.lo[1], g.lo[2]};
+    const float *tab = g.tab32;
+    if (g.cubes > 0) {
+        const double x3 = pz[(i / group) * group];
+        double q = floor(x3 / g.L);
+        const int j = q < 0.0 ? 0 : (q > (double)(g.n_rep - 1) ? g.n_rep - 1 : (int)q);
+        double cq = floor((x3 - (double)j * g.L) / g.W);
+        const int c = cq < 0.0 ? 0 : (cq > (double)(g.cubes - 1) ? g.cubes - 1 : (int)cq);
+        lo[0] = -0.5 * g.W;
+        lo[1] = -0.5 * g.W;
+        lo[2] = (double)j * g.L + (double)c * g.W;
+        tab += ((int64_t)j * g.cubes + c) * kGridRec * (int64_t)n * n * n;
+    }
+    double u[3];
+    int s[3];
+    bool inside = true;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+        u[d] = (r[d] - lo[d]) / g.h;
+        inside = inside && (u[d] >= -g.margin && u[d] <= (double)(n - 1) + g.margin);
+        int sd = inside ? (int)floor(u[d]) - NI + 1 : 0;
+        sd = sd > n - W ? n - W : sd;
+        s[d] = sd < 0 ? 0 : sd;
+    }
+    float F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+    if (inside) {
+        int k3 = (int)floor(u[2]);
+        k3 = k3 > n - 2 ? n - 2 : k3;
+        k3 = k3 < 0 ? 0 : k3;
+        const float B = (float)(u[2] - (double)k3), A = 1.0f - B;
+        const float cA = (A * A * A - A) * (1.0f / 6.0f), cB = (B * B * B - B) * (1.0f / 6.0f);
+        float c1[W], c2[W];
+        spline_weights_f<W>((float)(u[0] - (double)s[0]), c1);
+        spline_weights_f<W>((float)(u[1] - (double)s[1]), c2);
+#pragma unroll
+        for (int b = 0; b < W; ++b) {
+            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+            for (int a = 0; a < W; ++a) {
+                const int64_t node = ((int64_t)(s[0] + a) * n + (s[1] + b)) * n + k3;
+                const float4 *p = reinterpret_cast<const float4 *>(tab + kGridRec * node);
+                const float4 v = __ldg(p), y = __ldg(p + 1), w = __ldg(p + 2), z = __ldg(p + 3);
+                acc[0] += c1[a] * (A * v.x + B * w.x + (cA * y.x + cB * z.x));
+                acc[1] += c1[a] * (A * v.y + B * w.y + (cA * y.y + cB * z.y));
+                acc[2] += c1[a] * (A * v.z + B * w.z + (cA * y.z + cB * z.z));
+                acc[3] += c1[a] * (A * v.w + B * w.w + (cA * y.w + cB * z.w));
+            }
+#pragma unroll
+            for (int f = 0; f < 4; ++f) F[f] += c2[b] * acc[f];
+        }
+    }
+#pragma unroll
+    for (int f = 0; f < 4; ++f) out[(int64_t)f * n_pts + i] = make_float2(-F[f], 0.0f);
+}
+
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
                              int mode, void *out, const unsigned long long *gate, cudaStream_t st, int group)
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((n + 127) / 128);
+    if (mode == 0 && g.tab32) {
+        float2 *o = static_cast<float2 *>(out);
+        switch (g.n_int) {
+        case 1: k_grid_eval32<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
+        case 2: k_grid_eval32<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
+        case 3: k_grid_eval32<3><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
+        case 4: k_grid_eval32<4><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
+        default: return cudaErrorInvalidValue;
+        }
+        return cudaGetLastError();
+    }
     switch (g.n_int) {
     case 1: k_grid_eval<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
     case 2: k_grid_eval<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
@@ -334,7 +458,9 @@ cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *p
 void grid_free(GridDev &g)
 {
     cudaFree(g.tab);
+    cudaFree(g.tab32);
     g.tab = nullptr;
+    g.tab32 = nullptr;
 }
 
 static unsigned blocks_for(int64_t m)
@@ -430,9 +556,9 @@ static int builder_init(Builder &B, int n, double h, double soft, bool cache_ker
 
 // one grid: the particles' CIC node masses on the nodes lo + h i, optionally
 // minus their mean, convolved with the four Plummer kernels; the node table
-// (kGridRec n^3 doubles) goes to dest
+// (kGridRec n^3 doubles) goes to dest, its FP32 copy to dest32
 static int builder_run(Builder &B, int64_t np, const double *pos, const double *mass, const double lo[3],
-                       int mean_subtract, double *dest, cudaStream_t st)
+                       int mean_subtract, double *dest, float *dest32, cudaStream_t st)
 {
     const int n = B.n;
     const int64_t n3 = B.n3(), P3 = B.P3(), Pc = B.Pc();
@@ -482,7 +608,7 @@ static int builder_run(Builder &B, int64_t np, const double *pos, const double *
     const int64_t lines = 4 * (int64_t)n * n;
     k_spline_lines<<<(unsigned)((lines + 127) / 128), 128, 0, st>>>(n, lines, B.val, B.y2);
     GCK(cudaGetLastError(), "k_spline_lines");
-    k_interleave<<<blocks_for(n3), 256, 0, st>>>(n3, B.val, B.y2, dest);
+    k_interleave<<<blocks_for(n3), 256, 0, st>>>(n3, B.val, B.y2, dest, dest32);
     GCK(cudaGetLastError(), "k_interleave");
     return RT3D_OK;
 }
@@ -494,7 +620,8 @@ int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, do
     int rc = builder_init(B, g.n, g.h, soft, false, st, err);
     if (rc != RT3D_OK) return rc;
     GCK(cudaMalloc(&g.tab, sizeof(double) * kGridRec * (size_t)B.n3()), "grid node table");
-    rc = builder_run(B, np, pos, mass, g.lo, mean_subtract, g.tab, st);
+    GCK(cudaMalloc(&g.tab32, sizeof(float) * kGridRec * (size_t)B.n3()), "grid node table");
+    rc = builder_run(B, np, pos, mass, g.lo, mean_subtract, g.tab, g.tab32, st);
     if (rc != RT3D_OK) return rc;
     GCK(cudaStreamSynchronize(st), "grid build");
     return RT3D_OK;
@@ -550,12 +677,13 @@ int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass
     if (rc != RT3D_OK) return rc;
     const size_t stride = kGridRec * (size_t)B.n3();
     GCK(cudaMalloc(&g.tab, sizeof(double) * stride * (size_t)R * C), "grid node tables");
+    GCK(cudaMalloc(&g.tab32, sizeof(float) * stride * (size_t)R * C), "grid node tables");
     for (int j = 0; j < R; ++j)
         for (int q = 0; q < C; ++q) {
             const size_t cell = (size_t)j * C + q;
             const double lo[3] = {-0.5 * W, -0.5 * W, (double)j * L + (double)q * W};
             rc = builder_run(B, (int64_t)cm[cell].size(), cp[cell].data(), cm[cell].data(), lo, mean_subtract,
-                             g.tab + cell * stride, st);
+                             g.tab + cell * stride, g.tab32 + cell * stride, st);
             if (rc != RT3D_OK) return rc;
             // the host lists of this cube must outlive its asynchronous upload
             GCK(cudaStreamSynchronize(st), "grid build");

@@ -334,6 +334,7 @@ struct GridDev {
     double lo[3] = {0.0, 0.0, 0.0};
     double h = 0.0;
     double *tab = nullptr;  // [i1][i2][i3][kGridRec], i3 fastest
+    float *tab32 = nullptr; // the same rounded to FP32 (the mixed path's evaluation)
     // cube-tiled replicated box (cubes > 0): n_rep * cubes node tables stored
     // one after the other (stride kGridRec n^3), replica-major; cube c of
     // replica j has lo = (-W/2, -W/2, j L + c W) and spacing W / (n - 1)
@@ -354,9 +355,9 @@ int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, do
 int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass, double soft,
                    const int32_t *rot, const double *shift, int mean_subtract, cudaStream_t st, std::string &err);
 void grid_free(GridDev &g);
-// App. B evaluation at n points (SoA px, py, pz).  mode 0: -F as (hi, lo)
-// FP32 pairs in the pair-sum partial layout (one split); 1: -F as FP64
-// partials; 2: F at out[4 i + f]
+// App. B evaluation at n points (SoA px, py, pz).  mode 0 (mixed path): -F
+// from the FP32 node table, as (hi, 0) pairs in the pair-sum partial layout
+// (one split); 1: -F as FP64 partials; 2: F at out[4 i + f] (FP64)
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
                              int mode, void *out, const unsigned long long *gate, cudaStream_t st,
                              int group = 1);

@@ -80,7 +80,8 @@ def test_grid_trace_matches_oracle(P, cosmo):
               lens_chi=cfg["lens_chi"], asinh_s=cfg["asinh_s"])
     o = oracle.trace(cosmo, gf.field(), cfg["z_s"], cfg["theta"], **kw)
     assert np.all(o.flags == 0)
-    for prec, tol_mu, tol_a in ((P.FP64, 1e-9, 1e-9), (P.MIXED, 1e-7, 1e-7)):
+    # the mixed path interpolates from the FP32 node table in FP32
+    for prec, tol_mu, tol_a in ((P.FP64, 1e-9, 1e-9), (P.MIXED, 1e-6, 1e-6)):
         ctx = P.Context(0, precision=prec)
         ctx.set_cosmology(*cfg["cosmo"])
         ctx.load_grid(1, cfg["pos"], cfg["mass"], cfg["soft"], lo, h, n, n_int=2)
@@ -152,7 +153,7 @@ def test_box_grid_matches_oracle(P, cosmo):
     th = g.uniform(-0.3, 0.3, (12, 2)) * W / chi_s
     kw = dict(n_ring=4, theta_r=4.8e-6, schedule=0, n_steps=150)
     o = oracle.trace(cosmo, bg.field(), z_s, th, **kw)
-    for prec, tol_mu, tol_a in ((P.FP64, 1e-9, 1e-8), (P.MIXED, 1e-7, 1e-5)):
+    for prec, tol_mu, tol_a in ((P.FP64, 1e-9, 1e-8), (P.MIXED, 1e-6, 1e-5)):
         c2 = P.Context(0, precision=prec)
         c2.set_cosmology(0.3, 0.7, 0.7)
         c2.load_grid_box(1, pos, mass, soft, L, rot, shift, cubes, n)
