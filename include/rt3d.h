@@ -194,11 +194,15 @@ typedef struct {
 
 /* Build a gridded field in slot field_id from n particles (pos n*3, mass n,
  * one softening length soft for the kernels).  The library copies the
- * inputs; the grid (8 n^3 doubles: node values and x3 spline second
- * derivatives) stays on the device until the slot is reloaded or the context
- * destroyed.  The build needs (2n)^3 doubles and two (2n)^2 (n+1) complex
- * FFT buffers of temporary device memory.  Traces, rt3d_potential and
- * rt3d_grid_nodes on the slot then use the grid; rt3d_trace_batch rejects
+ * inputs; the grid's node table (per node the four values and their x3
+ * spline second derivatives: 8 n^3 doubles in an RT3D_FP64 context, the same
+ * rounded to 8 n^3 floats in an RT3D_MIXED context, which also interpolates in
+ * FP32) stays on the device until the slot is reloaded or the context
+ * destroyed.  The build (always FP64) needs (2n)^3 doubles, 8 n^3 doubles and
+ * two (2n)^2 (n+1) complex FFT buffers of temporary device memory (a box
+ * keeps four more, the kernels' spectra, where they fit in 2 GiB).  Traces,
+ * rt3d_potential and rt3d_grid_nodes on the slot then use the grid
+ * (rt3d_grid_nodes of a mixed context returns the FP32 values); rt3d_trace_batch rejects
  * grid slots (RT3D_ENOTIMPL).  Errors: RT3D_EINVAL for a bad option or a
  * non-finite input, RT3D_ENOMEM, RT3D_ECUDA (including a cuFFT failure). */
 int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
@@ -217,8 +221,9 @@ int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, co
  * own cube); up to one node spacing beyond that cube's faces the end splines
  * are extrapolated (the other rays of a bundle that straddles a face),
  * further out the field is zero.  g->lo and g->h are not
- * used.  Positions must lie in [0, L).  Memory: 8 n^3 doubles per cube stay
- * on the device.  Errors as rt3d_load_grid. */
+ * used.  Positions must lie in [0, L).  Memory: one node table per cube (as
+ * rt3d_load_grid: 8 n^3 doubles, or floats in a mixed context) stays on the
+ * device.  Errors as rt3d_load_grid. */
 int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                        double soft, const rt3d_volume *vol, int cubes, const rt3d_grid_opts *g);
 

@@ -1456,7 +1456,8 @@ extern "C" int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const doub
     fs.gd.n_int = g->n_int;
     fs.gd.h = g->h;
     for (int d = 0; d < 3; ++d) fs.gd.lo[d] = g->lo[d];
-    int rc = grid_build(fs.gd, n, pos, mass, soft, g->mean_subtract ? 1 : 0, ctx->stream, ctx->err);
+    int rc = grid_build(fs.gd, n, pos, mass, soft, g->mean_subtract ? 1 : 0, ctx->opt.precision == RT3D_FP64,
+                        ctx->stream, ctx->err);
     if (rc != RT3D_OK) {
         free_field(fs);
         return rc;
@@ -1507,8 +1508,8 @@ extern "C" int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const 
     G.W = L / cubes;
     G.h = G.W / (g->n - 1);
     G.margin = 1.0;
-    int rc = grid_build_box(G, n, pos, mass, soft, vol->rot, vol->shift, g->mean_subtract ? 1 : 0, ctx->stream,
-                            ctx->err);
+    int rc = grid_build_box(G, n, pos, mass, soft, vol->rot, vol->shift, g->mean_subtract ? 1 : 0,
+                            ctx->opt.precision == RT3D_FP64, ctx->stream, ctx->err);
     if (rc != RT3D_OK) {
         free_field(fs);
         return rc;
@@ -1537,14 +1538,20 @@ extern "C" int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out)
     CK(cudaSetDevice(ctx->device));
     const size_t n3 = (size_t)fs.gd.n * fs.gd.n * fs.gd.n;
     const size_t cells = fs.gd.cubes > 0 ? (size_t)fs.gd.cubes * fs.gd.n_rep : 1;
-    std::vector<double> tab(kGridRec * n3);
+    std::vector<double> tab(fs.gd.tab ? kGridRec * n3 : 0);
+    std::vector<float> tab32(fs.gd.tab ? 0 : kGridRec * n3);
     for (size_t c = 0; c < cells; ++c) {
-        CK(cudaMemcpyAsync(tab.data(), fs.gd.tab + c * kGridRec * n3, tab.size() * sizeof(double),
-                           cudaMemcpyDeviceToHost, ctx->stream));
+        if (fs.gd.tab)
+            CK(cudaMemcpyAsync(tab.data(), fs.gd.tab + c * kGridRec * n3, tab.size() * sizeof(double),
+                               cudaMemcpyDeviceToHost, ctx->stream));
+        else
+            CK(cudaMemcpyAsync(tab32.data(), fs.gd.tab32 + c * kGridRec * n3, tab32.size() * sizeof(float),
+                               cudaMemcpyDeviceToHost, ctx->stream));
         CK(cudaStreamSynchronize(ctx->stream));
         double *o = out + c * 4 * n3;
         for (size_t i = 0; i < n3; ++i)
-            for (int f = 0; f < 4; ++f) o[f * n3 + i] = tab[kGridRec * i + f];
+            for (int f = 0; f < 4; ++f)
+                o[f * n3 + i] = fs.gd.tab ? tab[kGridRec * i + f] : (double)tab32[kGridRec * i + f];
     }
     return RT3D_OK;
 }

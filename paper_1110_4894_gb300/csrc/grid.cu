@@ -167,20 +167,25 @@ __global__ void k_spline_lines(int n, int64_t lines, const double *__restrict__ 
 
 // node table: per node the four values, then the four x3-spline second
 // derivatives (kGridRec doubles); tab32 holds the same numbers rounded to FP32
+// (either may be null)
 __global__ void k_interleave(int64_t n3, const double *__restrict__ val, const double *__restrict__ y2,
                              double *__restrict__ tab, float *__restrict__ tab32)
 {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n3; i += (int64_t)gridDim.x * blockDim.x) {
         const double r[kGridRec] = {val[i], val[n3 + i], val[2 * n3 + i], val[3 * n3 + i],
                                     y2[i],  y2[n3 + i],  y2[2 * n3 + i],  y2[3 * n3 + i]};
-        double2 *t = reinterpret_cast<double2 *>(tab + kGridRec * i);
-        t[0] = make_double2(r[0], r[1]);
-        t[1] = make_double2(r[2], r[3]);
-        t[2] = make_double2(r[4], r[5]);
-        t[3] = make_double2(r[6], r[7]);
-        float4 *t32 = reinterpret_cast<float4 *>(tab32 + kGridRec * i);
-        t32[0] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
-        t32[1] = make_float4((float)r[4], (float)r[5], (float)r[6], (float)r[7]);
+        if (tab) {
+            double2 *t = reinterpret_cast<double2 *>(tab + kGridRec * i);
+            t[0] = make_double2(r[0], r[1]);
+            t[1] = make_double2(r[2], r[3]);
+            t[2] = make_double2(r[4], r[5]);
+            t[3] = make_double2(r[6], r[7]);
+        }
+        if (tab32) {
+            float4 *t32 = reinterpret_cast<float4 *>(tab32 + kGridRec * i);
+            t32[0] = make_float4((float)r[0], (float)r[1], (float)r[2], (float)r[3]);
+            t32[1] = make_float4((float)r[4], (float)r[5], (float)r[6], (float)r[7]);
+        }
     }
 }
 
@@ -320,8 +325,8 @@ __global__ void __launch_bounds__(128) k_grid_eval(GridDev g, const double *__re
 
 // The mixed path's evaluation: the same interpolation from the FP32 node
 // table with FP32 weights and sums; the point's cube, node window and
-// fractional offsets come from FP64 coordinates.  Output as mode 0 (hi = F,
-// lo = 0).
+// fractional offsets come from FP64 coordinates.  Output modes 0 (hi = -F,
+// lo = 0) and 2.
 template <int W>
 __device__ __forceinline__ void spline_weights_f(float u, float (&c)[W])
 {
@@ -362,7 +367,7 @@ __device__ __forceinline__ void spline_weights_f(float u, float (&c)[W])
 template <int NI>
 __global__ void __launch_bounds__(128) k_grid_eval32(GridDev g, const double *__restrict__ px,
                                                      const double *__restrict__ py, const double *__restrict__ pz,
-                                                     int64_t n_pts, float2 *__restrict__ out,
+                                                     int64_t n_pts, int mode, void *__restrict__ out,
                                                      const unsigned long long *__restrict__ gate, int group)
 {
     constexpr int W = 2 * NI;
@@ -423,7 +428,12 @@ __global__ void __launch_bounds__(128) k_grid_eval32(GridDev g, const double *__
         }
     }
 #pragma unroll
-    for (int f = 0; f < 4; ++f) out[(int64_t)f * n_pts + i] = make_float2(-F[f], 0.0f);
+    for (int f = 0; f < 4; ++f) {
+        if (mode == 2)
+            ((double *)out)[4 * i + f] = (double)F[f];
+        else
+            ((float2 *)out)[(int64_t)f * n_pts + i] = make_float2(-F[f], 0.0f);
+    }
 }
 
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
@@ -431,17 +441,20 @@ cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *p
 {
     if (n <= 0) return cudaSuccess;
     const unsigned grid = (unsigned)((n + 127) / 128);
-    if (mode == 0 && g.tab32) {
-        float2 *o = static_cast<float2 *>(out);
+    // the FP32 table serves the mixed path (mode 0) and, where it is the only
+    // table, point evaluation (mode 2)
+    if (g.tab32 && (mode == 0 || !g.tab)) {
+        if (mode == 1) return cudaErrorInvalidValue;
         switch (g.n_int) {
-        case 1: k_grid_eval32<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
-        case 2: k_grid_eval32<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
-        case 3: k_grid_eval32<3><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
-        case 4: k_grid_eval32<4><<<grid, 128, 0, st>>>(g, px, py, pz, n, o, gate, group); break;
+        case 1: k_grid_eval32<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
+        case 2: k_grid_eval32<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
+        case 3: k_grid_eval32<3><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
+        case 4: k_grid_eval32<4><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
         default: return cudaErrorInvalidValue;
         }
         return cudaGetLastError();
     }
+    if (!g.tab) return cudaErrorInvalidValue;
     switch (g.n_int) {
     case 1: k_grid_eval<1><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
     case 2: k_grid_eval<2><<<grid, 128, 0, st>>>(g, px, py, pz, n, mode, out, gate, group); break;
@@ -614,13 +627,15 @@ static int builder_run(Builder &B, int64_t np, const double *pos, const double *
 }
 
 int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, double soft, int mean_subtract,
-               cudaStream_t st, std::string &err)
+               bool fp64, cudaStream_t st, std::string &err)
 {
     Builder B;
     int rc = builder_init(B, g.n, g.h, soft, false, st, err);
     if (rc != RT3D_OK) return rc;
-    GCK(cudaMalloc(&g.tab, sizeof(double) * kGridRec * (size_t)B.n3()), "grid node table");
-    GCK(cudaMalloc(&g.tab32, sizeof(float) * kGridRec * (size_t)B.n3()), "grid node table");
+    if (fp64)
+        GCK(cudaMalloc(&g.tab, sizeof(double) * kGridRec * (size_t)B.n3()), "grid node table");
+    else
+        GCK(cudaMalloc(&g.tab32, sizeof(float) * kGridRec * (size_t)B.n3()), "grid node table");
     rc = builder_run(B, np, pos, mass, g.lo, mean_subtract, g.tab, g.tab32, st);
     if (rc != RT3D_OK) return rc;
     GCK(cudaStreamSynchronize(st), "grid build");
@@ -628,7 +643,8 @@ int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, do
 }
 
 int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass, double soft,
-                   const int32_t *rot, const double *shift, int mean_subtract, cudaStream_t st, std::string &err)
+                   const int32_t *rot, const double *shift, int mean_subtract, bool fp64, cudaStream_t st,
+                   std::string &err)
 {
     const int R = g.n_rep, C = g.cubes;
     const double L = g.L, W = g.W, c = 0.5 * L;
@@ -676,14 +692,17 @@ int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass
     int rc = builder_init(B, g.n, g.h, soft, true, st, err);
     if (rc != RT3D_OK) return rc;
     const size_t stride = kGridRec * (size_t)B.n3();
-    GCK(cudaMalloc(&g.tab, sizeof(double) * stride * (size_t)R * C), "grid node tables");
-    GCK(cudaMalloc(&g.tab32, sizeof(float) * stride * (size_t)R * C), "grid node tables");
+    if (fp64)
+        GCK(cudaMalloc(&g.tab, sizeof(double) * stride * (size_t)R * C), "grid node tables");
+    else
+        GCK(cudaMalloc(&g.tab32, sizeof(float) * stride * (size_t)R * C), "grid node tables");
     for (int j = 0; j < R; ++j)
         for (int q = 0; q < C; ++q) {
             const size_t cell = (size_t)j * C + q;
             const double lo[3] = {-0.5 * W, -0.5 * W, (double)j * L + (double)q * W};
             rc = builder_run(B, (int64_t)cm[cell].size(), cp[cell].data(), cm[cell].data(), lo, mean_subtract,
-                             g.tab + cell * stride, g.tab32 + cell * stride, st);
+                             g.tab ? g.tab + cell * stride : nullptr, g.tab32 ? g.tab32 + cell * stride : nullptr,
+                             st);
             if (rc != RT3D_OK) return rc;
             // the host lists of this cube must outlive its asynchronous upload
             GCK(cudaStreamSynchronize(st), "grid build");

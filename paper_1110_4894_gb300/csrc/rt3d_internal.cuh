@@ -333,8 +333,10 @@ struct GridDev {
     int n = 0, n_int = 0;
     double lo[3] = {0.0, 0.0, 0.0};
     double h = 0.0;
-    double *tab = nullptr;  // [i1][i2][i3][kGridRec], i3 fastest
-    float *tab32 = nullptr; // the same rounded to FP32 (the mixed path's evaluation)
+    // one of the two: [i1][i2][i3][kGridRec], i3 fastest, in FP64 (FP64
+    // contexts) or rounded to FP32 (mixed contexts)
+    double *tab = nullptr;
+    float *tab32 = nullptr;
     // cube-tiled replicated box (cubes > 0): n_rep * cubes node tables stored
     // one after the other (stride kGridRec n^3), replica-major; cube c of
     // replica j has lo = (-W/2, -W/2, j L + c W) and spacing W / (n - 1)
@@ -345,19 +347,21 @@ struct GridDev {
     // face); farther out the field is zero
     double margin = 0.0;
 };
-// build g.tab (allocated here) from host particles; returns an rt3d status
-// and sets err on failure
+// build g.tab (fp64) or g.tab32 (allocated here) from host particles; returns
+// an rt3d status and sets err on failure
 int grid_build(GridDev &g, int64_t np, const double *pos, const double *mass, double soft, int mean_subtract,
-               cudaStream_t st, std::string &err);
+               bool fp64, cudaStream_t st, std::string &err);
 // build the n_rep * cubes node tables of a cube-tiled replicated box (g.n,
 // n_rep, cubes, L, W, h set by the caller; g.tab allocated here) from the
 // box's host particles, each replica placed by rot[9 j] and shift[3 j]
 int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass, double soft,
-                   const int32_t *rot, const double *shift, int mean_subtract, cudaStream_t st, std::string &err);
+                   const int32_t *rot, const double *shift, int mean_subtract, bool fp64, cudaStream_t st,
+                   std::string &err);
 void grid_free(GridDev &g);
-// App. B evaluation at n points (SoA px, py, pz).  mode 0 (mixed path): -F
-// from the FP32 node table, as (hi, 0) pairs in the pair-sum partial layout
-// (one split); 1: -F as FP64 partials; 2: F at out[4 i + f] (FP64)
+// App. B evaluation at n points (SoA px, py, pz) from the grid's table.  mode
+// 0 (mixed path, FP32 table): -F as (hi, 0) pairs in the pair-sum partial
+// layout (one split); 1 (FP64 table): -F as FP64 partials; 2: F at
+// out[4 i + f] as FP64 numbers
 cudaError_t launch_grid_eval(const GridDev &g, const double *px, const double *py, const double *pz, int64_t n,
                              int mode, void *out, const unsigned long long *gate, cudaStream_t st,
                              int group = 1);
