@@ -200,7 +200,7 @@ typedef struct {
  * FP32) stays on the device until the slot is reloaded or the context
  * destroyed.  The build (always FP64) needs (2n)^3 doubles, 8 n^3 doubles and
  * two (2n)^2 (n+1) complex FFT buffers of temporary device memory (a box
- * keeps four more, the kernels' spectra, where they fit in 2 GiB).  Traces,
+ * keeps four more, the kernels' spectra, where they fit in 8 GiB).  Traces,
  * rt3d_potential and rt3d_grid_nodes on the slot then use the grid
  * (rt3d_grid_nodes of a mixed context returns the FP32 values); rt3d_trace_batch rejects
  * grid slots (RT3D_ENOTIMPL).  Errors: RT3D_EINVAL for a bad option or a

@@ -354,6 +354,7 @@ extern "C" int rt3d_set_cosmology(rt3d_ctx *ctx, double om, double ol, double h)
     c.atab = ctx->atab;
     c.atab_n = n;
     c.atab_h = t_max / (n - 1);
+    c.atab_ih = 1.0 / c.atab_h;
     ctx->have_cosmo = true;
     return RT3D_OK;
 }

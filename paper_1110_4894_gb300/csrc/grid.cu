@@ -549,7 +549,7 @@ static int builder_init(Builder &B, int n, double h, double soft, bool cache_ker
     B.err = &err;
     const int P = 2 * n;
     // the four kernel spectra stay resident only where they are small
-    B.cache = cache_kernels && 4 * B.Pc() * (int64_t)sizeof(cufftDoubleComplex) <= ((int64_t)2 << 30);
+    B.cache = cache_kernels && 4 * B.Pc() * (int64_t)sizeof(cufftDoubleComplex) <= ((int64_t)8 << 30);
     GCK(cudaMalloc(&B.q, sizeof(unsigned long long) * (size_t)B.n3()), "grid node buffer");
     GCK(cudaMalloc(&B.total, sizeof(unsigned long long)), "grid total");
     GCK(cudaMalloc(&B.buf, sizeof(double) * (size_t)B.P3()), "grid FFT buffer");

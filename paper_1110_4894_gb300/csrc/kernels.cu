@@ -11,14 +11,14 @@ namespace rt3d {
 // One block computes chi_s; every thread then fills dlam[k] = int a^2 dchi over
 // [x_k, x_{k+1}] (the affine step of the unperturbed ray with dx3/dl = 1 at the
 // observer), by composite Boole's rule with 4 panels.
-// a(t) and da/dt at t = j h (the closed forms of Eq. scalefac2)
+// a(t) and h da/dt at t = j h (the closed forms of Eq. scalefac2)
 __global__ void k_atab(Cosmo c, int n, double h, double *__restrict__ tab)
 {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= n) return;
     const double a = cosmo_a_exact(c, (double)j * h);
     tab[2 * j] = a;
-    tab[2 * j + 1] = cosmo_adot(c, a);
+    tab[2 * j + 1] = h * cosmo_adot(c, a);
 }
 
 cudaError_t launch_atab(const Cosmo &c, int n, double h, double *d_tab, cudaStream_t st)

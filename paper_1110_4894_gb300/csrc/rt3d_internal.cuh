@@ -25,11 +25,11 @@ struct Cosmo {
     double t0;  // lookback time of the big bang (Mpc)
     double k;   // 1.5 sqrt(OL) H0
     double r;   // OM / OL
-    // a(t) and da/dt at t = j atab_h, j < atab_n (interleaved), or null: the
-    // closed form is then evaluated at every call
+    // a(t) and atab_h da/dt at t = j atab_h, j < atab_n (interleaved), or
+    // null: the closed form is then evaluated at every call
     const double *atab = nullptr;
     int atab_n = 0;
-    double atab_h = 0.0;
+    double atab_h = 0.0, atab_ih = 0.0;  // node spacing and its inverse
 };
 
 // Eq. scalefac2: a(t) for t the lookback time, closed form.
@@ -47,14 +47,16 @@ __device__ __forceinline__ double cosmo_a_exact(const Cosmo &c, double t)
 __device__ __forceinline__ double cosmo_a(const Cosmo &c, double t)
 {
     if (c.atab) {
-        const double u = t / c.atab_h;
+        const double u = t * c.atab_ih;
         if (u >= 0.0 && u < (double)(c.atab_n - 1)) {
             const int j = (int)u;
-            const double s = u - (double)j, s2 = s * s, s3 = s2 * s;
-            const double a0 = c.atab[2 * j], d0 = c.atab[2 * j + 1] * c.atab_h;
-            const double a1 = c.atab[2 * j + 2], d1 = c.atab[2 * j + 3] * c.atab_h;
-            return (2.0 * s3 - 3.0 * s2 + 1.0) * a0 + (s3 - 2.0 * s2 + s) * d0 + (3.0 * s2 - 2.0 * s3) * a1 +
-                   (s3 - s2) * d1;
+            const double s = u - (double)j;
+            const double a0 = c.atab[2 * j], d0 = c.atab[2 * j + 1];
+            const double a1 = c.atab[2 * j + 2], d1 = c.atab[2 * j + 3];
+            // the cubic through (a0, d0) at s = 0 and (a1, d1) at s = 1, in powers of s
+            const double D = a1 - a0;
+            const double c2 = 3.0 * D - 2.0 * d0 - d1, c3 = d0 + d1 - 2.0 * D;
+            return a0 + s * (d0 + s * (c2 + s * c3));
         }
     }
     return cosmo_a_exact(c, t);
@@ -64,6 +66,12 @@ __device__ __forceinline__ double cosmo_a(const Cosmo &c, double t)
 __device__ __forceinline__ double cosmo_adot(const Cosmo &c, double a)
 {
     return -a * c.H0 * sqrt(c.om / (a * a * a) + c.ol);
+}
+
+// the same with ia = 1 / a already at hand
+__device__ __forceinline__ double cosmo_adot_ia(const Cosmo &c, double a, double ia)
+{
+    return -a * c.H0 * sqrt(c.om * (ia * ia * ia) + c.ol);
 }
 
 // ---------------------------------------------------------------------------

@@ -273,12 +273,11 @@ __device__ __forceinline__ void gather_field(const DevField &f, int S, bool fp64
 //   Gamma^i_tt = phi_i / a^3,    Gamma^i_ti = a' (a + phi) / a^2,
 //   Gamma^i_jk = (-phi_k d_ij - phi_j d_ik + phi_i d_jk) / a
 // (christoffel = DERIVED replaces Gamma^t_ii by a' (a - 3 phi)).
-__device__ __forceinline__ void geodesic_rhs(const double y[8], const double F[4], double a, double ad,
+__device__ __forceinline__ void geodesic_rhs(const double y[8], const double F[4], double a, double ia, double ad,
                                              int christoffel, double k[8])
 {
     const double T = y[4], vx = y[5], vy = y[6], vz = y[7];
     const double phi = F[0], gx = F[1], gy = F[2], gz = F[3];
-    const double ia = 1.0 / a;
     const double gv = gx * vx + gy * vy + gz * vz;
     const double v2 = vx * vx + vy * vy + vz * vz;
     const double gtii = christoffel == RT3D_CHRISTOFFEL_DERIVED ? ad * (a - 3.0 * phi) : ad * (a + phi);
@@ -322,7 +321,8 @@ __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField 
     if (pre) field_from_sums(f, pre, rep, ys + 1, mfac, F, rec);
     else gather_field(f, S, fp64, partials, rs.n_rays, i, rep, ys + 1, mfac, F, rec);
     const double a = cosmo_a(tp.cosmo, ys[0]);
-    const double ad = cosmo_adot(tp.cosmo, a);
+    const double ia = 1.0 / a;
+    const double ad = cosmo_adot_ia(tp.cosmo, a, ia);
     if (step == 0 && stage == 0) {
         // null condition of Eq. expandingmetric with psi = phi / a
         const double vn = sqrt(ys[5] * ys[5] + ys[6] * ys[6] + ys[7] * ys[7]);
@@ -331,7 +331,7 @@ __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField 
         y[4] = T;
         rs.y[4 * st + i] = T;
     }
-    geodesic_rhs(ys, F, a, ad, tp.christoffel, k);
+    geodesic_rhs(ys, F, a, ia, ad, tp.christoffel, k);
     const double dl = dlam[step < tp.n_steps ? step : tp.n_steps - 1];
     const int done = rs.done[i];
     double nx[8];
@@ -346,7 +346,7 @@ __device__ __forceinline__ bool stage_ray(const TraceParams &tp, const DevField 
         }
     } else {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) nx[q] = y[q] + dl / 6.0 * (rs.ks[q * st + i] + k[q]);
+        for (int q = 0; q < 8; ++q) nx[q] = y[q] + dl * (1.0 / 6.0) * (rs.ks[q * st + i] + k[q]);
         if (!done && nx[3] >= chi_s) {
             const double s = (chi_s - y[3]) / (nx[3] - y[3]);
 #pragma unroll

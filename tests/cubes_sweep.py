@@ -4,7 +4,9 @@ to z_s = 0.5) with each replica's prism cut into 8 cubes of 256^3 nodes or
 16 cubes of 128^3 nodes, both about 24/h kpc node spacing.  16 cubes halve
 the prism's width, so their bundles cover a quarter of the sky patch; the
 paper traces 3e4 and 6e4 lines of sight.  Prints the muPDF moments of each
-setting and a two-sample comparison of the magnifications.
+setting, a two-sample comparison of the magnifications, and the 8-cube
+setting traced on the 16-cube setting's own bundles (same lines of sight,
+so the difference is the cut of the mass alone).
 
     python tests/cubes_sweep.py [--steps 2000]
 
@@ -24,7 +26,7 @@ sys.path.insert(0, os.path.dirname(HERE))
 import inputs  # noqa: E402
 
 
-def run(P, cubes, n, n_side, steps):
+def run(P, cubes, n, n_side, steps, extra_theta=None):
     cfg = inputs.config_prism(n_side=n_side, n_steps=steps, cubes=cubes, grid_n=n)
     ctx = P.Context(0, precision=P.MIXED)
     ctx.set_cosmology(*cfg["cosmo"])
@@ -38,9 +40,13 @@ def run(P, cubes, n, n_side, steps):
     trace = time.perf_counter() - t0
     counts, wfix, sc = ctx.histogram(r["mu"], r["flags"], bins=200, mu_min=0.5, mu_max=5.0)
     spacing = cfg["L"] / cubes / (n - 1) * cfg["cosmo"][2] * 1e3
+    extra = None
+    if extra_theta is not None:
+        extra = ctx.trace(0, cfg["z_s"], extra_theta, n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0,
+                          n_steps=steps)["mu"]
     ctx.close()
     return dict(cubes=cubes, n=n, bundles=len(r["mu"]), spacing_h_kpc=spacing, build_s=build, trace_s=trace,
-                mu=r["mu"], flags=r["flags"], counts=counts, sc=sc)
+                mu=r["mu"], flags=r["flags"], counts=counts, sc=sc, extra=extra, theta=cfg["theta"])
 
 
 def boot_moments(mu, reps=200, seed=7):
@@ -62,7 +68,8 @@ def main():
     ap.add_argument("--json", default="")
     args = ap.parse_args()
     import paper_1110_4894_gb300 as P
-    res = [run(P, 8, 256, 176, args.steps), run(P, 16, 128, 245, args.steps)]
+    r16 = run(P, 16, 128, 245, args.steps)
+    res = [run(P, 8, 256, 176, args.steps, extra_theta=r16["theta"]), r16]
     from scipy.stats import ks_2samp
     print("| cubes x nodes | node spacing (h^-1 kpc) | bundles | build (s) | trace (s) | <mu>_w | sigma_w | "
           "5% / 50% / 95% of mu | flagged |")
@@ -78,6 +85,17 @@ def main():
                         sigma_w_err=ds, quantiles=q.tolist(), build_s=r["build_s"], trace_s=r["trace_s"]))
     ks = ks_2samp(res[0]["mu"], res[1]["mu"])
     print("\ntwo-sample KS on mu: D = %.4f, p = %.3g" % (ks.statistic, ks.pvalue))
+    # the same lines of sight through both cuts of the mass
+    m8, m16 = res[0]["extra"], res[1]["mu"]
+    (a8, da8), (s8, ds8) = zip(*boot_moments(m8))
+    d = np.abs(m8 / m16 - 1)
+    ks2 = ks_2samp(m8, m16)
+    same = dict(bundles=len(m16), mean_w_8=a8, sigma_w_8=s8, abs_dmu_median=float(np.median(d)),
+                abs_dmu_p99=float(np.percentile(d, 99)), ks_D=float(ks2.statistic), ks_p=float(ks2.pvalue))
+    print("8 cubes on the 16-cube bundles: <mu>_w = %.4f +- %.4f, sigma_w = %.4f +- %.4f; "
+          "|mu8/mu16 - 1| median %.2e, 99%% %.2e; KS D = %.4f" % (a8, da8, s8, ds8, same["abs_dmu_median"],
+                                                                 same["abs_dmu_p99"], same["ks_D"]))
+    out.append(dict(same_bundles=same))
     if args.json:
         with open(args.json, "w") as f:
             json.dump(dict(settings=out, ks_D=float(ks.statistic), ks_p=float(ks.pvalue), steps=args.steps), f)
