@@ -22,6 +22,7 @@
 #include <cufft.h>
 
 #include <algorithm>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -682,11 +683,21 @@ int grid_build_box(GridDev &g, int64_t np, const double *pos, const double *mass
     {
         const int nt = std::max(1, std::min(R, (int)std::thread::hardware_concurrency()));
         std::vector<std::thread> th;
+        std::vector<char> oom((size_t)nt, 0);
         for (int t = 0; t < nt; ++t)
             th.emplace_back([&, t] {
-                for (int j = t; j < R; j += nt) select(j);
+                try {
+                    for (int j = t; j < R; j += nt) select(j);
+                } catch (const std::bad_alloc &) {
+                    oom[(size_t)t] = 1;
+                }
             });
         for (auto &x : th) x.join();
+        for (char o : oom)
+            if (o) {
+                err = "host memory for the prism particles";
+                return RT3D_ENOMEM;
+            }
     }
     Builder B;
     int rc = builder_init(B, g.n, g.h, soft, true, st, err);
