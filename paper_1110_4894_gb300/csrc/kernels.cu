@@ -81,6 +81,9 @@ cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *
 // which keeps four times more loads in flight), then one thread per ray runs
 // the FP64 stage update with whole warps active.
 constexpr int kStageRays = 64;
+// from this many rays on, one ray per thread still gives every SM several
+// blocks of 256
+constexpr int kStageWideRays = 152 * 4 * 256;
 
 // the bundles' prism records of this stage (mean-subtracted boxes), read by
 // every ray of the bundle in k_stage
@@ -129,13 +132,50 @@ __global__ void __launch_bounds__(256) k_stage(TraceParams tp, DevField f, RaySt
     if (threadIdx.x == 0 && s_active) atomicAdd(&cnt[2], (unsigned long long)s_active);
 }
 
+// One ray per thread, its four outputs reduced by the same thread: for few
+// splits (the grid path) or enough rays to fill the GPU, where the FP64
+// stage, not the reduction, needs the threads.
+__global__ void __launch_bounds__(256) k_stage_wide(TraceParams tp, DevField f, RayState rs, int S, int fp64,
+                                                   double mfac, const void *__restrict__ partials,
+                                                   const double *__restrict__ dlam,
+                                                   const double *__restrict__ misc, int step, int stage,
+                                                   unsigned long long *cnt, const double *__restrict__ prism)
+{
+    if (stage == 0 && blockIdx.x == 0 && threadIdx.x == 0) cnt[step & 1] = 0ull;
+    if (step >= tp.n_steps && cnt[(step - 1) & 1] == 0ull) return;  // every ray is across
+    __shared__ unsigned s_active;
+    if (threadIdx.x == 0) s_active = 0;
+    __syncthreads();
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < rs.n_rays) {
+        double acc[4];
+        if (!fp64) {
+#pragma unroll
+            for (int o = 0; o < 4; ++o) acc[o] = reduce_partials_mixed((const float2 *)partials, S, rs.n_rays, i, o);
+        }
+        if (stage_ray(tp, f, rs, S, fp64 != 0, mfac, partials, dlam, misc[0], step, stage, cnt, i,
+                      fp64 ? nullptr : acc, prism))
+            atomicAdd(&s_active, 1u);
+    }
+    __syncthreads();
+    if (threadIdx.x == 0 && s_active) atomicAdd(&cnt[2], (unsigned long long)s_active);
+}
+
 cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, const ForceShape &sh, bool fp64,
                          const void *d_partials, const double *d_dlam, const double *d_misc, int step, int stage,
                          unsigned long long *d_counters, cudaStream_t st, const double *d_prism)
 {
-    const int64_t blocks = (rs.n_rays + kStageRays - 1) / kStageRays;
-    k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, partial_splits(sh), fp64 ? 1 : 0, partial_mass_factor(f, sh),
-                                             d_partials, d_dlam, d_misc, step, stage, d_counters, d_prism);
+    const int S = partial_splits(sh);
+    const double mfac = partial_mass_factor(f, sh);
+    if (S <= 8 || rs.n_rays >= (int64_t)kStageWideRays) {
+        const int64_t blocks = (rs.n_rays + 255) / 256;
+        k_stage_wide<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, S, fp64 ? 1 : 0, mfac, d_partials, d_dlam, d_misc,
+                                                       step, stage, d_counters, d_prism);
+    } else {
+        const int64_t blocks = (rs.n_rays + kStageRays - 1) / kStageRays;
+        k_stage<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, S, fp64 ? 1 : 0, mfac, d_partials, d_dlam, d_misc, step,
+                                                 stage, d_counters, d_prism);
+    }
     return cudaGetLastError();
 }
 
