@@ -116,7 +116,7 @@ def run_cones(args):
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "bundles_per_s": nb * args.steps / sum(times),
            "config": {"workload": name, "cones": args.cones, "particles": npart, "bundles": nb,
                       "rk4_steps_per_cone": args.cone_steps, "launch_shape": {k: st[k] for k in ("threads_per_block",
-                                                                                                "splits")}},
+                                                                                                "splits", "variant")}},
            "roofline": {"bound": "alu", "achieved": FLOPS_PER_INTERACTION * st["interactions"] / dev_s / 1e12,
                         "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
                         "frac": FLOPS_PER_INTERACTION * st["interactions"] / dev_s / FP32_PEAK, "traffic": None,

@@ -182,7 +182,8 @@ struct rt3d_ctx {
         size_t prism_n = 0;
         cudaGraphExec_t exec = nullptr;
         std::vector<long long> key;
-        std::map<std::tuple<int, int, int>, std::pair<int, int>> tuned;  // (cones, log2 rays, log2 pairs) -> (NT, items)
+        // (cones, log2 rays, log2 pairs) -> (NT, particles per item, kernel mode)
+        std::map<std::tuple<int, int, int>, std::tuple<int, int, int>> tuned;
     } batch;
 };
 
@@ -1096,14 +1097,15 @@ static void unpack_bundles(const double *bo, int64_t nb, rt3d_bundle_result *out
 // upload it, and run (or replay) the graph.  g_limit > 0 runs only that many
 // global stages (autotuner timing); then nothing is read back.
 static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const rt3d_bundle_opts *b, int NT,
-                     int64_t per_item, int g_limit, bool want_rays, float *ms_out)
+                     int64_t per_item, int MODE, int g_limit, bool want_rays, float *ms_out)
 {
     auto &BS = ctx->batch;
     const int P = 2;
     const int nr = 1 + b->n_ring;
-    // rays per block: NT bundles (bundle-centric kernel, rings of 4 or 8) or
-    // 2P rays per thread (packed kernel); both are multiples of 32
-    const int RB = (nr == 5 || nr == 9) ? NT * nr : 2 * P * NT;
+    // rays per block: 2 NT bundles (expanded two-bundle kernel, rings of 4),
+    // NT bundles (bundle-centric kernel, rings of 4 or 8) or 2P rays per
+    // thread (packed kernel); all are multiples of 32
+    const int RB = MODE == 5 ? 2 * NT * nr : ((nr == 5 || nr == 9) ? NT * nr : 2 * P * NT);
     BatchPlan plan;
     int rc = plan_batch(ctx->fields.data(), n_cones, cones, nr, RB, NT, per_item, b->max_extra, plan);
     if (rc) return fail(ctx, rc, "invalid cone list");
@@ -1134,14 +1136,13 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     CK(cudaMemcpyAsync(BS.rb2cone, plan.rb2cone.data(), plan.rb2cone.size() * sizeof(int), cudaMemcpyHostToDevice, st));
     CK(cudaMemsetAsync(BS.bar, 0, 8 * sizeof(unsigned), st));
     int grid = 0;
-    const int MODE = nr == 5 ? 4 : (nr == 9 ? 8 : 0);
     CK(batch_resident_blocks(NT, MODE, &grid));
     if (grid < 1) return fail(ctx, RT3D_ECUDA, "persistent kernel cannot be resident");
     BatchArgs A = make_batch_args(BS.cones, n_cones, BS.items, (int64_t)plan.items.size(), BS.rb2cone, T, RB,
                                   g_limit > 0 ? g_limit : plan.g_end, BS.bar, (int *)(BS.bar + 2),
                                   ctx->opt.watchdog_s > 0 ? ctx->opt.watchdog_s : 120.0, BS.bout);
     // the graph is keyed by everything its launches capture
-    std::vector<long long> key = {n_cones, T, (long long)plan.items.size(), A.g_end, NT, per_item, grid,
+    std::vector<long long> key = {n_cones, T, (long long)plan.items.size(), A.g_end, NT, MODE, per_item, grid,
                                   plan.max_steps, plan.n_b_total, (long long)(intptr_t)BS.cones,
                                   (long long)(intptr_t)BS.items, (long long)(intptr_t)BS.bout,
                                   (long long)(intptr_t)BS.prism};
@@ -1188,7 +1189,7 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     ctx->stats.steps = plan.max_steps + b->max_extra;
     ctx->stats.rays_per_thread = (nr == 5 || nr == 9) ? nr : 2 * P;
     ctx->stats.threads_per_block = NT;
-    ctx->stats.variant = (nr == 5 || nr == 9) ? 3 : 0;
+    ctx->stats.variant = MODE == 5 ? 5 : ((nr == 5 || nr == 9) ? 3 : 0);
     ctx->stats.cluster = 1;
     ctx->stats.splits = (int)per_item;
     ctx->stats.force_ms = ms;
@@ -1240,9 +1241,20 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
     }
     bool want_rays = false;
     for (int c = 0; c < n_cones; ++c) want_rays |= outs[c].ray_state != nullptr || outs[c].ray_steps != nullptr;
-    // launch shape: block size and particles per work item (autotuned per size class)
+    // launch shape: kernel, block size and particles per work item (autotuned
+    // per size class).  Rings of 4 default to the expanded two-bundle kernel
+    // (64 threads: its compensated sums fill the static shared memory), other
+    // rings to the bundle-centric or packed kernel; variant 3 asks for the
+    // bundle-centric kernel, variant 5 for the two-bundle one.
+    const int nr = 1 + b->n_ring;
+    const int mode_plain = nr == 5 ? 4 : (nr == 9 ? 8 : 0);
     int NT = ctx->opt.threads_per_block == 64 || ctx->opt.threads_per_block == 256 ? ctx->opt.threads_per_block : 128;
     if (NT == 256 && b->n_ring == 8) NT = 128;
+    int MODE = mode_plain;
+    if (nr == 5 && ctx->opt.variant != 3 && (ctx->opt.threads_per_block <= 0 || ctx->opt.threads_per_block == 64)) {
+        MODE = 5;
+        NT = 64;
+    }
     int64_t per_item = ctx->opt.splits > 0 ? (int64_t)ctx->opt.splits * kTile : 16 * kTile;
     if (ctx->opt.autotune && ctx->opt.threads_per_block <= 0 && ctx->opt.splits <= 0) {
         int64_t rays = 0;
@@ -1254,30 +1266,34 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
         const auto key = std::make_tuple(n_cones, ilog2(rays), ilog2((int64_t)std::max(1.0, pairs)));
         auto it = ctx->batch.tuned.find(key);
         if (it != ctx->batch.tuned.end()) {
-            NT = it->second.first;
-            per_item = it->second.second;
+            std::tie(NT, per_item, MODE) = it->second;
         } else {
             float best = 1e30f;
-            for (int nt : {128, 256, 64})
+            // (threads, kernel mode) candidates
+            std::vector<std::pair<int, int>> shapes;
+            if (nr == 5 && ctx->opt.variant != 3) shapes.push_back({64, 5});
+            if (!(nr == 5 && ctx->opt.variant == 5))
+                for (int nt : {128, 256, 64})
+                    if (!(nt == 256 && b->n_ring == 8)) shapes.push_back({nt, mode_plain});
+            for (const auto &sh : shapes)
                 for (int tiles : {8, 16, 32}) {
-                    if (nt == 256 && b->n_ring == 8) continue;
                     float ms = 0.0f;
-                    rc = batch_run(ctx, n_cones, cones, b, nt, (int64_t)tiles * kTile, 8, false, &ms);
+                    rc = batch_run(ctx, n_cones, cones, b, sh.first, (int64_t)tiles * kTile, sh.second, 8, false, &ms);
                     if (rc) return rc;
                     if (ms < best) {
                         best = ms;
-                        NT = nt;
+                        NT = sh.first;
+                        MODE = sh.second;
                         per_item = (int64_t)tiles * kTile;
                     }
                 }
-            ctx->batch.tuned[key] = std::make_pair(NT, (int)per_item);
+            ctx->batch.tuned[key] = std::make_tuple(NT, (int)per_item, MODE);
         }
     }
-    rc = batch_run(ctx, n_cones, cones, b, NT, per_item, 0, want_rays, nullptr);
+    rc = batch_run(ctx, n_cones, cones, b, NT, per_item, MODE, 0, want_rays, nullptr);
     if (rc) return rc;
     // read back per cone
     auto &BS = ctx->batch;
-    const int nr = 1 + b->n_ring;
     int64_t nbt = 0;
     for (int c = 0; c < n_cones; ++c) nbt += cones[c].n_bundles;
     std::vector<double> bo((size_t)(6 * nbt));

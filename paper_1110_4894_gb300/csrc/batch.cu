@@ -108,16 +108,36 @@ __global__ void k_batch_init(BatchArgs B)
     init_ray(C.tp, C.f, C.theta, C.rs, local);
 }
 
-// MODE 4 / 8: bundle-centric kernel for rings of 4 / 8 rays; MODE 0: packed
+// MODE 4 / 8: bundle-centric kernel for rings of 4 / 8 rays; MODE 5: the
+// expanded two-bundle kernel for rings of 4 (block = 2 NT bundles); MODE 0:
+// packed
 template <int P, int NT, int MODE>
 __device__ __forceinline__ void batch_item(const BatchCone &C, int4 item, int g, float4 *s_a, float4 *s_b,
-                                           float2 *s_e)
+                                           float2 *s_e, float2 *s_hl)
 {
     const int64_t p0 = (int64_t)item.z * C.per_split;
     const int64_t p1 = min(C.f.n, p0 + C.per_split);
     const int64_t st = C.rs.stride;
     const double *px = C.rs.ys + st, *py = C.rs.ys + 2 * st, *pz = C.rs.ys + 3 * st;
     const int *rep = C.rs.rep + (g & 1) * C.rs.n_b;
+    if constexpr (MODE == 5) {
+        const int64_t b0 = (int64_t)item.y * 2 * NT;
+#define RT3D_XITEM(R_, E_, U_)                                                                                   \
+    bundle2x_block_sum<NT, 4, R_, E_, U_, 1>(C.f, px, py, pz, rep, C.rs.n_b, C.rs.n_rays, b0, p0, p1, item.z,      \
+                                             C.partials, s_a, s_b, (float *)s_e, s_hl)
+        switch (C.flags) {
+        case 0: RT3D_XITEM(false, false, false); break;
+        case 1: RT3D_XITEM(true, false, false); break;
+        case 2: RT3D_XITEM(false, true, false); break;
+        case 3: RT3D_XITEM(true, true, false); break;
+        case 4: RT3D_XITEM(false, false, true); break;
+        case 5: RT3D_XITEM(true, false, true); break;
+        case 6: RT3D_XITEM(false, true, true); break;
+        default: RT3D_XITEM(true, true, true); break;
+        }
+#undef RT3D_XITEM
+        return;
+    }
     if (MODE != 0) {  // bundle-centric: block = NT bundles
         const int64_t b0 = (int64_t)item.y * NT;
 #define RT3D_BITEM(NRING_, R_, E_, U_)                                                                          \
@@ -162,6 +182,7 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
     __shared__ float4 s_a[kTile];
     __shared__ float4 s_b[kTile];
     __shared__ float2 s_e[kTile];
+    __shared__ float2 s_hl[MODE == 5 ? 2 * (5 * 3 + 4) * NT : 1];
     __shared__ unsigned s_it;
     const int64_t nthreads = (int64_t)gridDim.x * NT;
     for (int g = 0; g < B.g_end; ++g) {
@@ -186,7 +207,7 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
                 if (b < C.rs.n_b) bundle_prism(C.f, C.rs, g, b, C.prism);
                 continue;
             }
-            batch_item<P, NT, MODE>(C, item, g, s_a, s_b, s_e);
+            batch_item<P, NT, MODE>(C, item, g, s_a, s_b, s_e, s_hl);
         }
         if (!grid_sync(B)) return;
         for (int64_t r = (int64_t)blockIdx.x * NT + threadIdx.x; r < B.T; r += nthreads) {
@@ -239,7 +260,8 @@ static cudaError_t batch_coop(const cudaLaunchConfig_t &cfg, const BatchArgs &B)
 }
 
 #define RT3D_BATCH_SHAPES(F, ...)                                              \
-    if (NT == 128 && MODE == 4) e = F<128, 4>(__VA_ARGS__);                    \
+    if (NT == 64 && MODE == 5) e = F<64, 5>(__VA_ARGS__);                      \
+    else if (NT == 128 && MODE == 4) e = F<128, 4>(__VA_ARGS__);               \
     else if (NT == 256 && MODE == 4) e = F<256, 4>(__VA_ARGS__);               \
     else if (NT == 64 && MODE == 4) e = F<64, 4>(__VA_ARGS__);                 \
     else if (NT == 128 && MODE == 8) e = F<128, 8>(__VA_ARGS__);               \

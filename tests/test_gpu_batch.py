@@ -77,13 +77,20 @@ def test_batch_fp64_one_cone_per_launch(batch_case):
 def test_batch_autotuned_and_shapes(batch_case):
     import paper_1110_4894_gb300 as P
     cfg, orc = batch_case
-    for kw in (dict(autotune=1), dict(threads_per_block=256, splits=4), dict(threads_per_block=64, splits=1)):
+    # default (expanded two-bundle kernel), tuned, the bundle-centric kernel, fixed shapes
+    for kw in (dict(), dict(autotune=1), dict(variant=3), dict(variant=5, splits=2),
+               dict(threads_per_block=256, splits=4), dict(threads_per_block=64, splits=1)):
         ctx = P.Context(0, precision=P.MIXED, **kw)
         ctx.set_cosmology(*cfg["cosmo"])
         cones = _load(ctx, cfg)
         res = ctx.trace_batch(cones, n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0)
         for r, o in zip(res, orc):
             assert rel_mu(r["mu"], o.mu).max() < 1e-4
+        st = ctx.stats()
+        if kw.get("variant") in (3, 5):
+            assert st["variant"] == kw["variant"]
+        elif not kw:
+            assert st["variant"] == 5 and st["threads_per_block"] == 64
         ctx.close()
 
 
