@@ -1093,6 +1093,15 @@ static void unpack_bundles(const double *bo, int64_t nb, rt3d_bundle_result *out
     }
 }
 
+// rays per ray block of the batched kernel: 2 NT bundles (expanded
+// two-bundle kernel, rings of 4), NT bundles (bundle-centric kernel, rings of
+// 4 or 8) or 2 kBatchP rays per thread (packed kernel); all multiples of 32
+constexpr int kBatchP = 2;
+static int batch_rays_per_block(int nr, int NT, int MODE)
+{
+    return MODE == 5 ? 2 * NT * nr : ((nr == 5 || nr == 9) ? NT * nr : 2 * kBatchP * NT);
+}
+
 // Build the batch layout for launch shape (NT, particles per work item),
 // upload it, and run (or replay) the graph.  g_limit > 0 runs only that many
 // global stages (autotuner timing); then nothing is read back.
@@ -1100,12 +1109,9 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
                      int64_t per_item, int MODE, int g_limit, bool want_rays, float *ms_out)
 {
     auto &BS = ctx->batch;
-    const int P = 2;
+    const int P = kBatchP;
     const int nr = 1 + b->n_ring;
-    // rays per block: 2 NT bundles (expanded two-bundle kernel, rings of 4),
-    // NT bundles (bundle-centric kernel, rings of 4 or 8) or 2P rays per
-    // thread (packed kernel); all are multiples of 32
-    const int RB = MODE == 5 ? 2 * NT * nr : ((nr == 5 || nr == 9) ? NT * nr : 2 * P * NT);
+    const int RB = batch_rays_per_block(nr, NT, MODE);
     BatchPlan plan;
     int rc = plan_batch(ctx->fields.data(), n_cones, cones, nr, RB, NT, per_item, b->max_extra, plan);
     if (rc) return fail(ctx, rc, "invalid cone list");
@@ -1315,7 +1321,7 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
         // crossing steps: read each cone's done/steps view
         std::vector<int> steps;
         int64_t T = 0;
-        const int RB = (nr == 5 || nr == 9) ? NT * nr : 4 * NT;
+        const int RB = batch_rays_per_block(nr, NT, MODE);
         for (int c = 0; c < n_cones; ++c) T += ((cones[c].n_bundles * nr + RB - 1) / RB) * RB;
         steps.resize((size_t)T);
         CK(cudaMemcpy(steps.data(), BS.ints + T, T * sizeof(int), cudaMemcpyDeviceToHost));
