@@ -201,9 +201,9 @@ typedef struct {
  * destroyed.  The build (always FP64) needs (2n)^3 doubles, 8 n^3 doubles and
  * two (2n)^2 (n+1) complex FFT buffers of temporary device memory (a box
  * keeps four more, the kernels' spectra, where they fit in 8 GiB).  Traces,
- * rt3d_potential and rt3d_grid_nodes on the slot then use the grid
- * (rt3d_grid_nodes of a mixed context returns the FP32 values); rt3d_trace_batch rejects
- * grid slots (RT3D_ENOTIMPL).  Errors: RT3D_EINVAL for a bad option or a
+ * rt3d_potential, rt3d_grid_nodes and rt3d_trace_batch cones on the slot then
+ * use the grid (rt3d_grid_nodes of a mixed context returns the FP32 values);
+ * rt3d_born rejects grid slots (RT3D_ENOTIMPL).  Errors: RT3D_EINVAL for a bad option or a
  * non-finite input, RT3D_ENOMEM, RT3D_ECUDA (including a cuFFT failure). */
 int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                    double soft, const rt3d_grid_opts *g);
@@ -248,7 +248,10 @@ int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int
                       double *d_ray_out);
 
 /* Trace many independent cones (each with its own field, z_s, bundles and
- * step count) in one persistent launch recorded in a CUDA graph.
+ * step count) in one persistent launch recorded in a CUDA graph.  A cone's
+ * field may be a particle field or a grid (isolated or cube-tiled box); all
+ * cones share the bundle options b, each with its own n_steps.  An RT3D_FP64
+ * context traces the cones one after another through rt3d_trace.
  * outs[i] receives cone i's results. */
 int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones,
                      const rt3d_bundle_opts *b, rt3d_bundle_result *outs);

@@ -979,6 +979,28 @@ static int plan_batch(const FieldSlot *fields, int n_cones, const rt3d_cone *con
     for (int c = 0; c < n_cones; ++c) {
         const int64_t nb = cones[c].n_bundles, n_rays = nb * nr, N = fields[cones[c].field_id].n;
         const int64_t nrb = (n_rays + RB - 1) / RB;
+        if (fields[cones[c].field_id].is_grid) {
+            // a grid cone: one evaluation item per ray block, one split
+            p.ray_base.push_back(p.T);
+            p.b_base.push_back(p.n_b_total);
+            p.dlam_off.push_back(p.dlam_total);
+            p.part_off.push_back(p.partials_total);
+            p.per_split.push_back(0);
+            p.S.push_back(1);
+            for (int64_t rb = 0; rb < nrb; ++rb) {
+                p.items.push_back(make_int4(c, (int)rb, 0, 1));
+                // about 500 FP32 operations and 1 KB of node reads per ray
+                p.cost.push_back(25 * std::min<int64_t>(RB, n_rays - rb * RB));
+                p.rb2cone.push_back(c);
+            }
+            p.T += nrb * RB;
+            p.n_b_total += nb;
+            p.dlam_total += cones[c].n_steps;
+            p.partials_total += 4 * n_rays;
+            p.max_steps = std::max(p.max_steps, cones[c].n_steps);
+            p.g_end = std::max(p.g_end, 4 * (cones[c].n_steps + max_extra));
+            continue;
+        }
         const int64_t tiles = std::max<int64_t>(1, (N + kTile - 1) / kTile);
         int64_t S = std::max<int64_t>(1, (tiles * kTile + per_item - 1) / per_item);
         S = std::min(S, tiles);
@@ -1078,6 +1100,8 @@ static void fill_cone_table(const FieldSlot *fields, const Cosmo &cosmo, int chr
         C.S = p.S[c];
         C.flags = (f.replicated ? 1 : 0) | (f.eps2 ? 2 : 0) | (f.uniform_mass ? 4 : 0);
         C.total_steps = cones[c].n_steps + b->max_extra;
+        C.grid = fields[cones[c].field_id].is_grid ? 1 : 0;
+        C.g = fields[cones[c].field_id].gd;
     }
 }
 
@@ -1204,7 +1228,11 @@ static int batch_run(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones, const r
     std::vector<unsigned long long> cnt((size_t)(3 * n_cones));
     CK(cudaMemcpy(cnt.data(), BS.cnt, cnt.size() * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     double inter = 0.0;
-    for (int c = 0; c < n_cones; ++c) inter += (double)cnt[3 * c + 2] * (double)ctx->fields[cones[c].field_id].n;
+    // grid cones count one field evaluation per ray and stage
+    for (int c = 0; c < n_cones; ++c) {
+        const FieldSlot &fs = ctx->fields[cones[c].field_id];
+        inter += (double)cnt[3 * c + 2] * (fs.is_grid ? 1.0 : (double)fs.n);
+    }
     ctx->stats.interactions = inter;
     return RT3D_OK;
 }
@@ -1221,8 +1249,6 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
         const rt3d_cone &k = cones[c];
         if (k.field_id < 0 || k.field_id >= RT3D_MAX_FIELDS || !ctx->fields[k.field_id].loaded)
             return fail(ctx, RT3D_ENOFIELD, "cone field not loaded");
-        if (ctx->fields[k.field_id].is_grid)
-            return fail(ctx, RT3D_ENOTIMPL, "the batched trace takes particle fields, not grid fields");
         if (!(k.z_s > 0.0) || k.z_s > 20.0 || k.n_bundles < 1 || !k.theta || k.n_steps < 1 || k.n_steps > 10000000)
             return fail(ctx, RT3D_EINVAL, "cone needs z_s in (0, 20], n_bundles >= 1, theta, n_steps >= 1");
         if (!outs[c].mu) return fail(ctx, RT3D_EINVAL, "null mu output");

@@ -12,6 +12,7 @@
 // %globaltimer watchdog: on expiry the kernel sets an error word and returns,
 // and the host reports RT3D_ETIMEOUT.
 #include "batch_layout.cuh"
+#include "grid_device.cuh"
 #include "force.cuh"
 #include "trace_device.cuh"
 
@@ -176,6 +177,21 @@ __device__ __forceinline__ void batch_item(const BatchCone &C, int4 item, int g,
 #undef RT3D_ITEM
 }
 
+// The grid evaluation of ray block rb of a grid cone into its one split of
+// partials.  Not inlined: its registers stay out of the pair-sum code's
+// allocation.
+__device__ __noinline__ void batch_grid_item(const BatchCone &C, int rb, int RB, int NT)
+{
+    const int64_t st = C.rs.stride;
+    const int64_t r1 = min(C.rs.n_rays, (int64_t)(rb + 1) * RB);
+    for (int64_t i = (int64_t)rb * RB + threadIdx.x; i < r1; i += NT) {
+        float F[4];
+        grid_eval32_any(C.g, C.rs.ys + st, C.rs.ys + 2 * st, C.rs.ys + 3 * st, i, C.rs.nr, F);
+#pragma unroll
+        for (int o = 0; o < 4; ++o) C.partials[(int64_t)o * C.rs.n_rays + i] = make_float2(-F[o], 0.0f);
+    }
+}
+
 template <int P, int NT, int MODE>
 __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
 {
@@ -205,6 +221,10 @@ __global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
             if (item.z < 0) {  // the prism records of NT bundles (FP64)
                 const int64_t b = (int64_t)item.y * NT + threadIdx.x;
                 if (b < C.rs.n_b) bundle_prism(C.f, C.rs, g, b, C.prism);
+                continue;
+            }
+            if (item.w == 1) {  // a grid cone: App. B evaluation of one ray block (one split)
+                batch_grid_item(C, item.y, B.RB, NT);
                 continue;
             }
             batch_item<P, NT, MODE>(C, item, g, s_a, s_b, s_e, s_hl);

@@ -19,13 +19,15 @@ struct BatchCone {
     double z_s, chi_l, s_asinh, mfac;
     int64_t per_split, ray_base, b_base;
     int S, flags, total_steps, kind;
+    int grid;              // 1: the field is a grid (g), read by grid items; S = 1
+    GridDev g;
 };
 
 struct BatchArgs {
     BatchCone *cones;
     int n_cones;
-    const int4 *items;     // (cone, ray block, split, -); split -1: the prism records of a
-                           // block of NT bundles
+    const int4 *items;     // (cone, ray block, split, kind); split -1: the prism records of a
+                           // block of NT bundles; kind 1: grid evaluation of a ray block
     int64_t n_items;
     const int *rb2cone;    // cone of each padded ray block
     int64_t T;             // padded ray count

@@ -26,6 +26,7 @@
 #include <thread>
 #include <vector>
 
+#include "grid_device.cuh"
 #include "rt3d_internal.cuh"
 
 namespace rt3d {
@@ -324,110 +325,19 @@ __global__ void __launch_bounds__(128) k_grid_eval(GridDev g, const double *__re
     }
 }
 
-// The mixed path's evaluation: the same interpolation from the FP32 node
-// table with FP32 weights and sums; the point's cube, node window and
-// fractional offsets come from FP64 coordinates.  Output modes 0 (hi = -F,
+// The mixed path's evaluation (grid_device.cuh): output modes 0 (hi = -F,
 // lo = 0) and 2.
-template <int W>
-__device__ __forceinline__ void spline_weights_f(float u, float (&c)[W])
-{
-    int k = (int)floorf(u);
-    k = k > W - 2 ? W - 2 : k;
-    k = k < 0 ? 0 : k;
-    const float A = (float)(k + 1) - u, B = u - (float)k;
-    const float cA = (A * A * A - A) * (1.0f / 6.0f), cB = (B * B * B - B) * (1.0f / 6.0f);
-#pragma unroll
-    for (int j = 0; j < W; ++j) {
-        float z[W];
-        z[0] = 0.0f;
-        z[W - 1] = 0.0f;
-        if (W >= 3) {
-            float den[W], dp = 0.0f, cp = 0.0f;
-#pragma unroll
-            for (int i = 1; i <= W - 2; ++i) {
-                const float e = (i + 1 == j ? 1.0f : 0.0f) - 2.0f * (i == j ? 1.0f : 0.0f) + (i - 1 == j ? 1.0f : 0.0f);
-                den[i] = 4.0f - cp;
-                cp = 1.0f / den[i];
-                dp = (6.0f * e - dp) / den[i];
-                z[i] = dp;
-            }
-#pragma unroll
-            for (int i = W - 3; i >= 1; --i) z[i] = z[i] - z[i + 1] / den[i];
-        }
-        float zk = z[0], zk1 = z[1];
-#pragma unroll
-        for (int i = 1; i < W - 1; ++i)
-            if (k == i) {
-                zk = z[i];
-                zk1 = z[i + 1];
-            }
-        c[j] = (j == k ? A : 0.0f) + (j == k + 1 ? B : 0.0f) + (cA * zk + cB * zk1);
-    }
-}
-
 template <int NI>
 __global__ void __launch_bounds__(128) k_grid_eval32(GridDev g, const double *__restrict__ px,
                                                      const double *__restrict__ py, const double *__restrict__ pz,
                                                      int64_t n_pts, int mode, void *__restrict__ out,
                                                      const unsigned long long *__restrict__ gate, int group)
 {
-    constexpr int W = 2 * NI;
     if (gate && *gate == 0ull) return;
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n_pts) return;
-    const int n = g.n;
-    const double r[3] = {px[i], py[i], pz[i]};
-    double lo[3] = {g.lo[0], g.lo[1], g.lo[2]};
-    const float *tab = g.tab32;
-    if (g.cubes > 0) {
-        const double x3 = pz[(i / group) * group];
-        double q = floor(x3 / g.L);
-        const int j = q < 0.0 ? 0 : (q > (double)(g.n_rep - 1) ? g.n_rep - 1 : (int)q);
-        double cq = floor((x3 - (double)j * g.L) / g.W);
-        const int c = cq < 0.0 ? 0 : (cq > (double)(g.cubes - 1) ? g.cubes - 1 : (int)cq);
-        lo[0] = -0.5 * g.W;
-        lo[1] = -0.5 * g.W;
-        lo[2] = (double)j * g.L + (double)c * g.W;
-        tab += ((int64_t)j * g.cubes + c) * kGridRec * (int64_t)n * n * n;
-    }
-    double u[3];
-    int s[3];
-    bool inside = true;
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-        u[d] = (r[d] - lo[d]) / g.h;
-        inside = inside && (u[d] >= -g.margin && u[d] <= (double)(n - 1) + g.margin);
-        int sd = inside ? (int)floor(u[d]) - NI + 1 : 0;
-        sd = sd > n - W ? n - W : sd;
-        s[d] = sd < 0 ? 0 : sd;
-    }
-    float F[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-    if (inside) {
-        int k3 = (int)floor(u[2]);
-        k3 = k3 > n - 2 ? n - 2 : k3;
-        k3 = k3 < 0 ? 0 : k3;
-        const float B = (float)(u[2] - (double)k3), A = 1.0f - B;
-        const float cA = (A * A * A - A) * (1.0f / 6.0f), cB = (B * B * B - B) * (1.0f / 6.0f);
-        float c1[W], c2[W];
-        spline_weights_f<W>((float)(u[0] - (double)s[0]), c1);
-        spline_weights_f<W>((float)(u[1] - (double)s[1]), c2);
-#pragma unroll
-        for (int b = 0; b < W; ++b) {
-            float acc[4] = {0.0f, 0.0f, 0.0f, 0.0f};
-#pragma unroll
-            for (int a = 0; a < W; ++a) {
-                const int64_t node = ((int64_t)(s[0] + a) * n + (s[1] + b)) * n + k3;
-                const float4 *p = reinterpret_cast<const float4 *>(tab + kGridRec * node);
-                const float4 v = __ldg(p), y = __ldg(p + 1), w = __ldg(p + 2), z = __ldg(p + 3);
-                acc[0] += c1[a] * (A * v.x + B * w.x + (cA * y.x + cB * z.x));
-                acc[1] += c1[a] * (A * v.y + B * w.y + (cA * y.y + cB * z.y));
-                acc[2] += c1[a] * (A * v.z + B * w.z + (cA * y.z + cB * z.z));
-                acc[3] += c1[a] * (A * v.w + B * w.w + (cA * y.w + cB * z.w));
-            }
-#pragma unroll
-            for (int f = 0; f < 4; ++f) F[f] += c2[b] * acc[f];
-        }
-    }
+    float F[4];
+    grid_eval32_point<NI>(g, px, py, pz, i, group, F);
 #pragma unroll
     for (int f = 0; f < 4; ++f) {
         if (mode == 2)

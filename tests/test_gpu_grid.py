@@ -123,8 +123,6 @@ def test_grid_errors(P):
     with pytest.raises(P.Rt3dError):
         ctx.load_grid(0, pos, -mass, 0.01, [0, 0, 0], 0.1, 16)
     ctx.load_grid(0, pos, mass, 0.01, [0, 0, 0], 0.1, 16)
-    with pytest.raises(P.Rt3dError):  # the batched trace takes particle fields only
-        ctx.trace_batch([dict(field_id=0, z_s=0.2, theta=np.zeros((1, 2)), n_steps=10)])
     ctx.load_particles(1, pos, mass, 0.01)
     buf = np.zeros(4)
     rc = ctx.L.rt3d_grid_nodes(ctx.h, 1, buf.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
@@ -179,3 +177,38 @@ def test_box_grid_errors(P):
         ctx.load_grid_box(0, pos, mass, 0.02, L, rot, shift, 0, 16)
     with pytest.raises(P.Rt3dError):
         ctx.load_grid_box(0, pos + L, mass, 0.02, L, rot, shift, 4, 16)  # outside [0, L)
+
+
+def test_batch_with_grid_cones(P, cosmo):
+    # one persistent launch over an isolated grid, a replicated box on cube
+    # grids and a particle field; each cone against the oracle on its own field
+    cfg, lo, h, n = _nfw_grid_case(n_steps=120, n_side=2)
+    pos, mass, rot, shift, L = _box()
+    gf = G.GridField(cfg["pos"], cfg["mass"], cfg["soft"], lo, h, n, n_int=2)
+    bg = G.BoxGridField(pos, mass, 0.02, L, rot, shift, cubes=4, n=16)
+    W = L / 4
+    chi_s = 2.6 * L
+    z_box = cosmo.z_of_chi(chi_s)
+    g = inputs.rng(12)
+    th_box = g.uniform(-0.3, 0.3, (6, 2)) * W / chi_s
+    kw = dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=cfg["schedule"], lens_chi=cfg["lens_chi"],
+              asinh_s=cfg["asinh_s"])
+    o_grid = oracle.trace(cosmo, gf.field(), cfg["z_s"], cfg["theta"], n_steps=120, **kw)
+    o_box = oracle.trace(cosmo, bg.field(), z_box, th_box, n_steps=90, **kw)
+    o_part = oracle.trace(cosmo, oracle.MassField(cfg["pos"], cfg["mass"], cfg["soft"]), cfg["z_s"], cfg["theta"],
+                          n_steps=120, **kw)
+    ctx = P.Context(0, precision=P.MIXED)
+    ctx.set_cosmology(*cfg["cosmo"])
+    ctx.load_grid(0, cfg["pos"], cfg["mass"], cfg["soft"], lo, h, n, n_int=2)
+    ctx.load_grid_box(1, pos, mass, 0.02, L, rot, shift, 4, 16)
+    ctx.load_particles(2, cfg["pos"], cfg["mass"], cfg["soft"])
+    res = ctx.trace_batch([dict(field_id=0, z_s=cfg["z_s"], theta=cfg["theta"], n_steps=120),
+                           dict(field_id=1, z_s=z_box, theta=th_box, n_steps=90),
+                           dict(field_id=2, z_s=cfg["z_s"], theta=cfg["theta"], n_steps=120)], want_rays=True, **kw)
+    for r, o, tol_mu in ((res[0], o_grid, 1e-6), (res[1], o_box, 1e-6), (res[2], o_part, 1e-4)):
+        assert np.array_equal(r["flags"], o.flags) and np.array_equal(r["steps"], o.steps)
+        assert rel_mu(r["mu"], o.mu).max() < tol_mu
+        assert rel_alpha(r["rays"], o).max() < 1e-5
+    # the grid cones equal the single-field grid trace of the same bundles
+    one = ctx.trace(0, cfg["z_s"], cfg["theta"], n_steps=120, **kw)
+    assert rel_mu(res[0]["mu"], one["mu"]).max() < 1e-12
