@@ -115,6 +115,27 @@ def test_grid_eval_is_zero_outside_the_nodes():
     assert np.all(out == 0.0)
 
 
+def test_grid_eval_margin_extrapolates_the_end_cubics():
+    # natural splines reproduce linear data, also beyond the end nodes, so a
+    # linear field is exact up to the margin; farther out the field is zero
+    n, h, lo = 10, 0.25, np.array([0.5, -1.0, 2.0])
+    x = [lo[d] + h * np.arange(n) for d in range(3)]
+    X = np.meshgrid(*x, indexing="ij")
+    lin = lambda p, f: 0.3 + (f + 1.0) * p[..., 0] - 0.7 * p[..., 1] + 0.2 * (f - 1.5) * p[..., 2]
+    val = np.stack([lin(np.stack(X, -1), f) for f in range(4)])
+    gf = G.GridField(None, None, 0.0, lo, h, n, n_int=2, val=val, margin=1.0)
+    span = (n - 1) * h
+    inside = np.array([lo - 0.9 * h, lo + span + 0.6 * h, lo + [-0.99 * h, 0.5 * span, span + 0.3 * h]])
+    out = gf.eval(inside)
+    want = np.stack([lin(inside, f) for f in range(4)], 1)
+    assert np.allclose(out, want, atol=1e-12)
+    beyond = np.array([lo - [1.01 * h, 0.0, 0.0], lo + [0.0, span + 1.2 * h, 0.0]])
+    assert np.all(gf.eval(beyond) == 0.0)
+    # without a margin the same points just outside the nodes read zero
+    g0 = G.GridField(None, None, 0.0, lo, h, n, n_int=2, val=val)
+    assert np.all(g0.eval(inside[:2]) == 0.0)
+
+
 def test_grid_field_converges_to_the_direct_sum():
     # a Plummer-softened particle: the grid field between the nodes approaches
     # the direct sum as the node spacing shrinks (App. B, Figs. nfwtests2)
