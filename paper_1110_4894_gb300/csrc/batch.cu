@@ -193,7 +193,7 @@ __device__ __noinline__ void batch_grid_item(const BatchCone &C, int rb, int RB,
 }
 
 template <int P, int NT, int MODE>
-__global__ void __launch_bounds__(NT) k_batch_run(BatchArgs B)
+__global__ void __launch_bounds__(NT, MODE == 5 ? 6 : 1) k_batch_run(BatchArgs B)
 {
     __shared__ float4 s_a[kTile];
     __shared__ float4 s_b[kTile];
