@@ -109,6 +109,44 @@ def test_grid_eval_along_x1_is_the_local_natural_spline(n_int):
             assert out[f] == pytest.approx(float(cs(u)), abs=1e-12)
 
 
+@pytest.mark.parametrize("n_int", [1, 2, 3])
+def test_grid_eval_along_x2_is_the_local_natural_spline(n_int):
+    interp = pytest.importorskip("scipy.interpolate")
+    gf, lo, h, n = _grid_from(lambda x, y, z, f: np.sin(1.7 * y + 0.3 * f), n_int=n_int)
+    ys = lo[1] + h * np.arange(n)
+    for u in (0.0, 0.45, 3.5, 7.25, n - 1.0):
+        p = np.array([[lo[0] + 0.77, lo[1] + u * h, lo[2] + 0.9]])
+        s = min(max(int(np.floor(u)) - n_int + 1, 0), n - 2 * n_int)
+        win = np.arange(s, s + 2 * n_int)
+        out = gf.eval(p)[0]
+        for f in range(4):
+            cs = interp.CubicSpline(win, np.sin(1.7 * ys[win] + 0.3 * f), bc_type="natural")
+            assert out[f] == pytest.approx(float(cs(u)), abs=1e-12)
+
+
+def test_grid_eval_of_a_product_field_is_the_tensor_product_of_the_splines():
+    # f(x1, x2, x3) = g1(x1) g2(x2) g3(x3): App. B's three interpolations
+    # factor, so the result is the product of the three one-dimensional splines
+    interp = pytest.importorskip("scipy.interpolate")
+    g1 = lambda x: np.cos(1.3 * x)
+    g2 = lambda y: 1.0 + 0.5 * np.sin(2.1 * y)
+    g3 = lambda z: np.exp(-0.4 * z)
+    gf, lo, h, n = _grid_from(lambda x, y, z, f: (f + 1.0) * g1(x) * g2(y) * g3(z), n_int=2)
+    nodes = [lo[d] + h * np.arange(n) for d in range(3)]
+    rng = np.random.default_rng(9)
+    for _ in range(10):
+        u = rng.uniform(0, n - 1, 3)
+        p = lo + h * u
+        want = 1.0
+        for d, gfun in enumerate((g1, g2)):
+            s = min(max(int(np.floor(u[d])) - 1, 0), n - 4)
+            win = np.arange(s, s + 4)
+            want *= float(interp.CubicSpline(win, gfun(nodes[d][win]), bc_type="natural")(u[d]))
+        want *= float(interp.CubicSpline(np.arange(n), g3(nodes[2]), bc_type="natural")(u[2]))
+        out = gf.eval(p[None, :])[0]
+        assert np.allclose(out, want * np.arange(1.0, 5.0), rtol=1e-11, atol=1e-13)
+
+
 def test_grid_eval_is_zero_outside_the_nodes():
     gf, lo, h, n = _grid_from(lambda x, y, z, f: 1.0 + x * 0.0)
     out = gf.eval([[lo[0] - 1e-9, lo[1] + 0.5, lo[2] + 0.5], [lo[0] + 0.5, lo[1] + 0.5, lo[2] + (n - 1) * h + 1e-9]])
