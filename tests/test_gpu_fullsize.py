@@ -13,7 +13,7 @@ pytestmark = pytest.mark.gpu
 def test_nfw_full_size_sampled(cosmo):
     import paper_1110_4894_gb300 as P
     cfg = inputs.config_c2()
-    ctx = P.Context(0, precision=P.MIXED, time_kernels=1)
+    ctx = P.Context(0, precision=P.MIXED, time_kernels=1, autotune=1)  # as bench.py: the tuner's shape
     ctx.set_cosmology(*cfg["cosmo"])
     gpu_load(ctx, 0, cfg)
     g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
