@@ -571,7 +571,7 @@ int orc_trace(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b,
               const double *theta, const orc_trace_opts *o, double *ray_out,
               double *bundle_out, int32_t *steps_out, double *n_pairs, int nthreads)
 {
-    if (o->n_ring < 2 || o->n_steps < 1 || !(z_s > 0.0)) return -1;
+    if (o->n_ring < 3 || o->n_ring > 8 || o->n_steps < 1 || !(z_s > 0.0)) return -1;
     if (f->grid && f->replicated && f->grid_cubes < 1) return -1;
     const int nr = 1 + o->n_ring;
     const double chi_s = orc_chi(c, z_s);
