@@ -103,7 +103,8 @@ typedef struct {
 } rt3d_volume;
 
 typedef struct {
-    int n_ring;      /* rays on the polygon (2..8); the paper uses 8, default 4 */
+    int n_ring;      /* rays on the polygon (3..8; two rays would be collinear and fix no
+                        Jacobian); the paper uses 8 (Sec. 3.1, Sec. 5.2), default 4 */
     double theta_r;  /* polygon radius (rad) */
     double phase;    /* polygon orientation (rad) */
     int schedule;    /* RT3D_SCHED_* */
@@ -157,15 +158,28 @@ typedef struct {
     int n_steps;
 } rt3d_cone;
 
-/* Create a context on CUDA device cuda_device; opt may be NULL (defaults). */
+/* Create a context on CUDA device cuda_device; opt may be NULL (defaults).
+ * The options select how the method of Sec. 3 is computed: opt->precision
+ * RT3D_MIXED sums the pair terms of Eqs. psi / derivs in FP32 with
+ * compensated accumulation and keeps the ray state of Eq. geodesiceqn, the
+ * background of Sec. 3.5 and the Jacobian of Eq. lensmap in FP64; RT3D_FP64
+ * computes every step in FP64.  RT3D_MIXED meets |dmu/mu| <= 1e-4 on softened
+ * fields; it does not on an unsoftened point lens (eps = 0) traced with
+ * bundles of 1e-3 Einstein radii (Sec. 4.1), whose ring-central deflection
+ * difference is below FP32 resolution: use RT3D_FP64 there.
+ * opt->christoffel selects App. A's symbols as printed or as derived.
+ * Errors: RT3D_EINVAL (no such device, bad option), RT3D_ENOMEM, RT3D_ECUDA. */
 int rt3d_create(rt3d_ctx **out, int cuda_device, const rt3d_options *opt);
-/* Free every device allocation of the context. */
+/* Free every device allocation of the context (the paper has no counterpart:
+ * resource management only).  The context may not be used afterwards. */
 int rt3d_destroy(rt3d_ctx *ctx);
 
 /* Flat LCDM background (Sec. 3.5): |omega_m + omega_l - 1| <= 1e-12, h > 0. */
 int rt3d_set_cosmology(rt3d_ctx *ctx, double omega_m, double omega_l, double h);
 
-/* Copy a particle set to the device as field field_id (0..RT3D_MAX_FIELDS-1,
+/* The mass distribution of Sec. 3.3 (N-body particles, the potential of
+ * Eqs. psi / derivs) and its replication along the line of sight of Sec. 5.2.
+ * Copy a particle set to the device as field field_id (0..RT3D_MAX_FIELDS-1,
  * replacing any previous one).  pos: n*3, mass: n (> 0), soft: n Plummer
  * softening lengths if soft_per_particle, else soft[0] for all (>= 0).
  * Positions are stored as integers on a grid of 2^-e Mpc (the finest that
@@ -194,7 +208,8 @@ typedef struct {
     int mean_subtract;  /* 1: subtract the mean node mass before the convolution */
 } rt3d_grid_opts;
 
-/* Build a gridded field in slot field_id from n particles (pos n*3, mass n,
+/* The grid force path of Sec. 3.3 and App. B (described above).
+ * Build a gridded field in slot field_id from n particles (pos n*3, mass n,
  * one softening length soft for the kernels).  The library copies the
  * inputs; the grid's node table (per node the four values and their x3
  * spline second derivatives: 8 n^3 doubles in an RT3D_FP64 context, the same
@@ -229,19 +244,30 @@ int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, co
 int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                        double soft, const rt3d_volume *vol, int cubes, const rt3d_grid_opts *g);
 
-/* Copy a grid slot's node values to out (host, 4 n^3 doubles, [f][i1][i2][i3]
+/* The node values of the grid of Sec. 3.3 (the field App. B interpolates).
+ * Copy a grid slot's node values to out (host, 4 n^3 doubles, [f][i1][i2][i3]
  * with i3 fastest, f = phi, dphi/dx1, dphi/dx2, dphi/dx3; for a box grid,
  * n_replicas * cubes such blocks, replica-major). */
 int rt3d_grid_nodes(rt3d_ctx *ctx, int field_id, double *out);
 
 /* Trace n_bundles bundles with centres theta (n_bundles*2, tangent-plane
  * angles: direction (theta_x, theta_y, 1)) from the observer to the plane
- * x3 = chi(z_s), and fill out. */
+ * x3 = chi(z_s), and fill out.  Each bundle is a central ray and a polygon of
+ * b->n_ring rays of radius b->theta_r (Sec. 3.1); every ray integrates the
+ * null geodesic equation (Eq. geodesiceqn, App. A symbols) by classical RK4
+ * with fixed affine steps (Sec. 3.4, Eq. RKstepsize read as a node table) and
+ * stops on the plane x3 = chi(z_s) (Sec. 5.1, Eq. raytracedistance) with
+ * linear interpolation; the polygon's source positions give the lens-map
+ * Jacobian (Eq. lensmap) and mu, kappa, gamma (Eq. magnification).  Errors:
+ * RT3D_ENOCOSMO, RT3D_ENOFIELD, RT3D_EINVAL (z_s outside (0, 20], n_bundles
+ * outside [1, 2^28], a non-finite theta, bad options), RT3D_ENOMEM,
+ * RT3D_ECUDA.  Flags per bundle: RT3D_F_*. */
 int rt3d_trace(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_bundles, const double *theta,
                const rt3d_bundle_opts *b, rt3d_bundle_result *out);
 
-/* As rt3d_trace, with device pointers, enqueued on stream (a cudaStream_t;
- * NULL = default stream) without host synchronisation.
+/* The trace of Sec. 3.1 / Sec. 3.4 as rt3d_trace, with device pointers,
+ * enqueued on stream (a cudaStream_t; NULL = default stream) without host
+ * synchronisation; the caller owns the device arrays.
  * d_theta: n_bundles*2; d_bundle_out: n_bundles*6 doubles
  * (mu, kappa, gamma1, gamma2, omega, flags as a double);
  * d_ray_out (optional): n_bundles*(1+n_ring)*8. */
@@ -249,8 +275,32 @@ int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int
                       const double *d_theta, const rt3d_bundle_opts *b, double *d_bundle_out,
                       double *d_ray_out);
 
-/* Trace many independent cones (each with its own field, z_s, bundles and
- * step count) in one persistent launch recorded in a CUDA graph.  A cone's
+/* The trace of Sec. 3.4 in pieces, with device pointers on a stream, for a
+ * caller that wants to interleave its own work between RK4 stages or time them
+ * (the trace itself is the same: rt3d_trace_device is begin + end).
+ * rt3d_trace_begin enqueues the step table (Sec. 3.4, Eq. RKstepsize) and the
+ * bundle initialiser (Sec. 3.1) and picks the pair-sum launch shape; d_theta
+ * (n_bundles*2, device) must stay valid until rt3d_trace_end.
+ * rt3d_trace_advance enqueues the next n_stages RK4 stages (4 per step: pair
+ * sum of Eqs. psi / derivs, the Sec. 3.3 mean-density prism of mean-
+ * subtracted boxes, the geodesic update of Eq. geodesiceqn); *stages_left
+ * (may be NULL) receives the stages still to run, extra steps (max_extra)
+ * included; stages past the end are no-ops.
+ * rt3d_trace_end enqueues the remaining stages and the bundle reducer (Eq.
+ * lensmap), writing d_bundle_out and d_ray_out as rt3d_trace_device.
+ * One trace is open per context; its state lives in the context.
+ * rt3d_trace_begin, rt3d_trace, rt3d_trace_device, rt3d_trace_batch,
+ * rt3d_born, rt3d_schedule, and loading into the trace's field slot close it
+ * (advance / end then return RT3D_EINVAL).  Enqueue every piece on one stream
+ * (or streams ordered after it).  rt3d_get_stats counts from rt3d_trace_begin. */
+int rt3d_trace_begin(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_bundles,
+                     const double *d_theta, const rt3d_bundle_opts *b);
+int rt3d_trace_advance(rt3d_ctx *ctx, void *stream, int n_stages, int *stages_left);
+int rt3d_trace_end(rt3d_ctx *ctx, void *stream, double *d_bundle_out, double *d_ray_out);
+
+/* Many lines of sight of Sec. 5 (each cone a mass distribution of Sec. 3.3
+ * or 5.2 traced as in Sec. 3.4, with its own field, z_s, bundles and step
+ * count) in one persistent launch recorded in a CUDA graph.  A cone's
  * field may be a particle field or a grid (isolated or cube-tiled box); all
  * cones share the bundle options b, each with its own n_steps.  An RT3D_FP64
  * context traces the cones one after another through rt3d_trace.
@@ -290,18 +340,20 @@ int rt3d_shear_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const doubl
 int rt3d_born(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_bundles, const double *theta,
               const rt3d_bundle_opts *b, double *out);
 
-/* phi and grad phi (comoving, with mean subtraction when enabled) at n
- * points: out = n*4 (phi, dphi/dx1, dphi/dx2, dphi/dx3).  rep: replica per
+/* The pair sum of Eqs. psi / derivs (with the mean-density subtraction of
+ * Sec. 3.3 when enabled): phi and grad phi (comoving) at n points: out = n*4 (phi, dphi/dx1, dphi/dx2, dphi/dx3).  rep: replica per
  * point (replicated fields; NULL = 0).  Uses the context's precision. */
 int rt3d_potential(rt3d_ctx *ctx, int field_id, int64_t n, const double *pts, const int32_t *rep,
                    double *out);
 
-/* Step table of a trace: chi_s = chi(z_s) and the n_steps affine-parameter
- * steps dlam (int of a^2 dchi between nodes on the unperturbed ray). */
+/* Step table of a trace (Sec. 3.4, Eq. RKstepsize; chi_s of Sec. 5.1, Eq.
+ * raytracedistance): chi_s = chi(z_s) and the n_steps affine-parameter steps
+ * dlam (int of a^2 dchi between nodes on the unperturbed ray). */
 int rt3d_schedule(rt3d_ctx *ctx, double z_s, int kind, int n_steps, double chi_l, double s,
                   double *dlam_out, double *chi_s_out);
 
-/* muPDF of a device bundle-result array as written by rt3d_trace_device
+/* muPDF (Sec. 5.3, Eq. weighthisto) of a device bundle-result array as
+ * written by rt3d_trace_device
  * (n*6 doubles: mu at offset 0, flags at offset 5), enqueued on stream.
  * d_counts, d_wfix: device [bins] uint64; d_scalars: device 8 doubles
  * (n_used, n_under, n_over, n_neg, n_bad, W_total, mean_w, sigma_w). */
@@ -341,18 +393,28 @@ int rt3d_watchdog_selftest(rt3d_ctx *ctx, double limit_s);
  *
  * Arguments: ctx with field field_id loaded; stream = cudaStream_t (NULL =
  * default stream); d_pts = device n*3 doubles laid out as all x1, then all x2,
- * then all x3 (comoving Mpc); d_rep = device n int32 replica indices or NULL
- * (replica 0); d_out = device n*4 doubles (phi, dphi/dx1, dphi/dx2, dphi/dx3
- * per point).  The call only enqueues work on stream. */
+ * then all x3 (comoving Mpc, finite); d_rep = device n int32 replica indices
+ * in [0, n_replicas) of the field (an isolated field has one, index 0) or
+ * NULL (replica 0); d_out = device n*4 doubles (phi, dphi/dx1, dphi/dx2,
+ * dphi/dx3 per point).  The call only enqueues work on stream, so the device
+ * arrays are not checked on the host: a point whose replica index is out of
+ * range or whose coordinates are not finite takes part in no pair sum and
+ * gets NaN in all four outputs, and the other points are unaffected.  Points
+ * are summed in blocks of consecutive indices, and a block makes one pass over
+ * the particles for every replica its points use: group points by replica
+ * (sorted rep) for the cost of one pass per point. */
 #define RT3D_NOALLOC_SCRATCH_BYTES (32u << 20)
 #define RT3D_NOALLOC_MAX_DEVICES 64
 int rt3d_potential_device_noalloc(rt3d_ctx *ctx, void *stream, int field_id, int64_t n,
                                   const double *d_pts, const int32_t *d_rep, double *d_out);
 
-/* Counters of the last trace or batch. */
+/* Counters of the last trace or batch (the paper has no counterpart:
+ * interactions and device time, for the throughput measurement). */
 int rt3d_get_stats(rt3d_ctx *ctx, rt3d_stats *out);
 
+/* Text of a status code (the paper has no counterpart). */
 const char *rt3d_status_string(int status);
+/* Message of the context's last failed call (the paper has no counterpart). */
 const char *rt3d_last_error(rt3d_ctx *ctx);
 
 #ifdef __cplusplus

@@ -103,6 +103,9 @@ def lib(build=True):
         "rt3d_trace_device": ([vp, vp, C.c_int, C.c_double, C.c_int64, vp, C.POINTER(BundleOpts), vp, vp], C.c_int),
         "rt3d_trace_batch": ([vp, C.c_int, C.POINTER(Cone), C.POINTER(BundleOpts), C.POINTER(BundleResult)],
                              C.c_int),
+        "rt3d_trace_begin": ([vp, vp, C.c_int, C.c_double, C.c_int64, vp, C.POINTER(BundleOpts)], C.c_int),
+        "rt3d_trace_advance": ([vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
+        "rt3d_trace_end": ([vp, vp, vp, vp], C.c_int),
         "rt3d_histogram": ([vp, C.c_int64, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)], C.c_int),
         "rt3d_shear_histogram": ([vp, C.c_int64, _dp, _dp, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)],
                                  C.c_int),
@@ -258,6 +261,23 @@ class Context:
         self._check(self.L.rt3d_trace_device(self.h, C.c_void_p(stream), int(field_id), float(z_s), int(n_bundles),
                                              C.c_void_p(d_theta), C.byref(o), C.c_void_p(d_bundle_out),
                                              C.c_void_p(d_ray_out) if d_ray_out else None))
+
+    def trace_begin(self, stream, field_id, z_s, n_bundles, d_theta, **kw):
+        """rt3d_trace_begin: open a trace in pieces (step table, initialiser) on stream."""
+        o = self.bundle_opts(**kw)
+        self._check(self.L.rt3d_trace_begin(self.h, C.c_void_p(stream), int(field_id), float(z_s), int(n_bundles),
+                                            C.c_void_p(d_theta), C.byref(o)))
+
+    def trace_advance(self, stream, n_stages):
+        """rt3d_trace_advance: enqueue the next n_stages RK4 stages; returns the stages left."""
+        left = C.c_int(0)
+        self._check(self.L.rt3d_trace_advance(self.h, C.c_void_p(stream), int(n_stages), C.byref(left)))
+        return left.value
+
+    def trace_end(self, stream, d_bundle_out, d_ray_out=None):
+        """rt3d_trace_end: the remaining stages and the bundle reducer."""
+        self._check(self.L.rt3d_trace_end(self.h, C.c_void_p(stream), C.c_void_p(d_bundle_out),
+                                          C.c_void_p(d_ray_out) if d_ray_out else None))
 
     def trace_batch(self, cones, want_rays=False, **kw):
         """cones: list of dicts with field_id, z_s, theta, n_steps."""

@@ -129,8 +129,25 @@ struct FieldSlot {
     GridDev gd;
 };
 
+// A trace open on the context: the ray state lives in the context's scratch
+// between rt3d_trace_begin and rt3d_trace_end, so one trace is open at a time.
+struct OpenTrace {
+    bool open = false;
+    const FieldSlot *fs = nullptr;
+    const double *d_theta = nullptr;
+    int64_t n_b = 0;
+    rt3d_bundle_opts b{};
+    TraceParams tp{};
+    ForceShape sh{};
+    RayState rs{};
+    bool fp64 = false, use_prism = false, timed = false;
+    int next = 0, total = 0;  // next global stage (4 per RK4 step) and their count
+    int64_t launches = 0, flaunch = 0;
+};
+
 struct rt3d_ctx {
     int device = 0;
+    int n_sm = 152;  // streaming multiprocessors of the device (queried at create)
     rt3d_options opt{};
     std::string err;
     bool have_cosmo = false;
@@ -151,6 +168,7 @@ struct rt3d_ctx {
     int hist_cap = 0;
     double *d_io = nullptr;                    // staging for potential / histogram inputs
     size_t d_io_n = 0;
+    OpenTrace trace;  // the trace between rt3d_trace_begin and rt3d_trace_end
     // launch shapes chosen by the autotuner, per size class
     std::map<std::tuple<int, int, int, int, int, int>, ForceShape> tuned;
     // batched trace: device scratch, the captured graph and its key
@@ -270,6 +288,10 @@ extern "C" int rt3d_create(rt3d_ctx **out, int dev, const rt3d_options *opt)
     int rc = RT3D_OK;
     do {
         if (cudaSetDevice(dev) != cudaSuccess) { rc = RT3D_ECUDA; break; }
+        if (cudaDeviceGetAttribute(&ctx->n_sm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || ctx->n_sm < 1) {
+            rc = RT3D_ECUDA;
+            break;
+        }
         if (cudaStreamCreateWithFlags(&ctx->stream, cudaStreamNonBlocking) != cudaSuccess) { rc = RT3D_ECUDA; break; }
         if (cudaEventCreate(&ctx->ev0) != cudaSuccess || cudaEventCreate(&ctx->ev1) != cudaSuccess) { rc = RT3D_ECUDA; break; }
         if (cudaMalloc((void **)&ctx->scr.misc, 16 * sizeof(double)) != cudaSuccess) { rc = RT3D_ENOMEM; break; }
@@ -363,6 +385,9 @@ extern "C" int rt3d_set_cosmology(rt3d_ctx *ctx, double om, double ol, double h)
 extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                                    const double *soft, int soft_pp, const rt3d_volume *vol)
 {
+    if (ctx && field_id >= 0 && field_id < RT3D_MAX_FIELDS && ctx->trace.open &&
+        ctx->trace.fs == &ctx->fields[field_id])
+        ctx->trace.open = false;  // the open trace's field is replaced
     if (!ctx) return RT3D_EINVAL;
     if (field_id < 0 || field_id >= RT3D_MAX_FIELDS) return fail(ctx, RT3D_EINVAL, "field id out of range");
     if (n < 0 || (n > 0 && (!pos || !mass)) || (!soft && n > 0)) return fail(ctx, RT3D_EINVAL, "null particle arrays");
@@ -557,9 +582,9 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
     if (ctx->opt.splits > 0) {
         S = ctx->opt.splits;
     } else {
-        // about five waves of resident blocks (152 SMs x ~5 blocks): many
+        // about five waves of resident blocks (SMs x ~5 blocks): many
         // small blocks balance the SMs better than one exact wave
-        const int64_t target = 152 * 5 * 5;
+        const int64_t target = (int64_t)ctx->n_sm * 5 * 5;
         S = (int)std::max<int64_t>(1, (target + nrb - 1) / nrb);
     }
     const int tiles = force_max_splits(sh, n_particles);
@@ -622,11 +647,11 @@ static int ilog2(int64_t v)
     return l;
 }
 
-static ForceShape with_splits(ForceShape sh, int64_t n_points, int64_t n_particles, int waves)
+static ForceShape with_splits(const rt3d_ctx *ctx, ForceShape sh, int64_t n_points, int64_t n_particles, int waves)
 {
     const int64_t per_block = rays_per_block(sh);
     const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
-    const int64_t slots = 152 * std::max(1, 640 / sh.NT);
+    const int64_t slots = (int64_t)ctx->n_sm * std::max(1, 640 / sh.NT);
     int S = (int)std::max<int64_t>(1, (waves * slots + nrb - 1) / nrb);
     const int tiles = force_max_splits(sh, n_particles);
     S = std::min(S, tiles);
@@ -648,7 +673,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
                                      ilog2(n), ilog2(std::max<int64_t>(1, fs.n)));
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        out = with_splits(it->second, n, fs.n, it->second.splits);  // splits slot holds the wave count
+        out = with_splits(ctx, it->second, n, fs.n, it->second.splits);  // splits slot holds the wave count
         return RT3D_OK;
     }
     std::vector<ForceShape> cand;
@@ -677,7 +702,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
                 s.R = p[0];
                 s.NT = p[1];
             }
-            cand.push_back(with_splits(s, n, fs.n, w));
+            cand.push_back(with_splits(ctx, s, n, fs.n, w));
             waves.push_back(w);
         }
     if (cand.empty()) {
@@ -722,7 +747,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
 static int check_bundle_opts(rt3d_ctx *ctx, const rt3d_bundle_opts *b)
 {
     if (!b) return fail(ctx, RT3D_EINVAL, "null bundle options");
-    if (b->n_ring < 2 || b->n_ring > 8) return fail(ctx, RT3D_EINVAL, "n_ring must be 2..8");
+    if (b->n_ring < 3 || b->n_ring > 8) return fail(ctx, RT3D_EINVAL, "n_ring must be 3..8");
     if (!(b->theta_r > 0.0) || !isfinite(b->theta_r) || !isfinite(b->phase)) return fail(ctx, RT3D_EINVAL, "bad theta_r/phase");
     if (b->n_steps < 1 || b->n_steps > 10000000) return fail(ctx, RT3D_EINVAL, "n_steps out of range");
     if (b->max_extra < 0 || b->max_extra > 64) return fail(ctx, RT3D_EINVAL, "max_extra must be 0..64");
@@ -774,7 +799,6 @@ static RayState make_state(rt3d_ctx *ctx, int64_t n_b, int nr)
     return rs;
 }
 
-// enqueue one full trace on st: schedule, init, RK4 stages, reduce
 // force shape of a grid-path trace: one "split" of interpolated values, no
 // mass factor (variant 6 names the grid path in the statistics)
 static ForceShape grid_shape()
@@ -788,18 +812,21 @@ static ForceShape grid_shape()
     return sh;
 }
 
-static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t n_b, const double *d_theta,
-                         const rt3d_bundle_opts *b, double *d_bout, double *d_rout, cudaStream_t st, bool timed)
+// schedule (S0), bundle initialiser (S1), launch shape; the trace is then open
+static int trace_begin(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t n_b, const double *d_theta,
+                       const rt3d_bundle_opts *b, cudaStream_t st, bool timed)
 {
-    const bool fp64 = ctx->opt.precision == RT3D_FP64;
+    OpenTrace &T = ctx->trace;
+    T = OpenTrace{};
+    T.fp64 = ctx->opt.precision == RT3D_FP64;
     const int nr = 1 + b->n_ring;
     const int64_t n_rays = n_b * nr;
-    ForceShape sh = fs.is_grid ? grid_shape() : choose_shape(ctx, fs.df, n_rays, fp64, nr);
-    int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
+    T.sh = fs.is_grid ? grid_shape() : choose_shape(ctx, fs.df, n_rays, T.fp64, nr);
+    int rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, T.sh);
     if (rc) return rc;
-    RayState rs = make_state(ctx, n_b, nr);
-    bool tune_pending = ctx->opt.autotune != 0 && !fs.is_grid;
-    TraceParams tp;
+    T.rs = make_state(ctx, n_b, nr);
+    const bool tune_pending = ctx->opt.autotune != 0 && !fs.is_grid;
+    TraceParams &tp = T.tp;
     tp.cosmo = ctx->cosmo;
     tp.chi_s = 0.0;
     tp.n_ring = b->n_ring;
@@ -809,64 +836,104 @@ static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t
     tp.n_steps = b->n_steps;
     tp.max_extra = b->max_extra;
     Scratch &s = ctx->scr;
-    int64_t launches = 0, flaunch = 0;
     ctx->tev_used = 0;
     CK(launch_schedule(ctx->cosmo, z_s, b->schedule, b->n_steps, b->lens_chi, b->asinh_s, s.dlam, s.misc, st));
-    CK(launch_init(tp, fs.df, d_theta, rs, s.counters, st));
-    launches += 2;
+    CK(launch_init(tp, fs.df, d_theta, T.rs, s.counters, st));
+    T.launches = 2;
     if (tune_pending) {  // rays now sit at the observer: time shapes on this field
-        rc = tuned_shape(ctx, fs, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, rs.rep, nr, n_rays, fp64, st, sh);
+        rc = tuned_shape(ctx, fs, T.rs.ys + n_rays, T.rs.ys + 2 * n_rays, T.rs.ys + 3 * n_rays, T.rs.rep, nr, n_rays,
+                         T.fp64, st, T.sh);
         if (rc) return rc;
-        rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, sh);
+        rc = ensure_trace_scratch(ctx, n_b, nr, b->n_steps, T.sh);
         if (rc) return rc;
-        rs = make_state(ctx, n_b, nr);
+        T.rs = make_state(ctx, n_b, nr);
     }
     // mean-subtracted boxes: the prism field once per bundle and stage (value,
     // gradient, Hessian), expanded to the bundle's other rays
-    const bool use_prism = !fs.is_grid && fs.df.replicated && fs.df.mean_subtract;
-    if (use_prism) CK(grow(s.prism, s.prism_n, (size_t)(kPrismRec * n_b)));
-    const int total = b->n_steps + b->max_extra;
-    for (int step = 0; step < total; ++step) {
-        for (int stage = 0; stage < 4; ++stage) {
-            const int g = step * 4 + stage;
-            const unsigned long long *gate = step >= b->n_steps ? s.counters + ((step - 1) & 1) : nullptr;
-            cudaEvent_t e0 = nullptr, e1 = nullptr;
-            if (timed && !gate) {
-                e0 = timing_event(ctx);
-                e1 = timing_event(ctx);
-                if (e0) CK(cudaEventRecord(e0, st));
-            }
-            if (fs.is_grid)
-                CK(launch_grid_eval(fs.gd, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays, n_rays,
-                                    fp64 ? 1 : 0, s.partials, gate, st, nr));
-            else
-                CK(run_force(ctx, fs.df, rs.ys + n_rays, rs.ys + 2 * n_rays, rs.ys + 3 * n_rays,
-                             rs.rep + (g & 1) * n_b, nr, n_rays, sh, fp64, s.partials, gate, st));
-            if (e1) CK(cudaEventRecord(e1, st));
-            if (use_prism) {
-                CK(launch_prism(tp, fs.df, rs, step, stage, s.counters, s.prism, st));
-                ++launches;
-            }
-            CK(launch_stage(tp, fs.df, rs, sh, fp64, s.partials, s.dlam, s.misc, step, stage, s.counters, st,
-                            use_prism ? s.prism : nullptr));
-            launches += 2;
-            flaunch += gate ? 0 : 1;
+    T.use_prism = !fs.is_grid && fs.df.replicated && fs.df.mean_subtract;
+    if (T.use_prism) CK(grow(s.prism, s.prism_n, (size_t)(kPrismRec * n_b)));
+    T.fs = &fs;
+    T.d_theta = d_theta;
+    T.n_b = n_b;
+    T.b = *b;
+    T.timed = timed;
+    T.next = 0;
+    T.total = 4 * (b->n_steps + b->max_extra);
+    T.open = true;
+    ctx->stats_pending = false;
+    return RT3D_OK;
+}
+
+// the next n global RK4 stages (S2-S6): pair sum (or grid evaluation), the
+// prism of mean-subtracted boxes, the integrator stage
+static int trace_advance(rt3d_ctx *ctx, int n, cudaStream_t st)
+{
+    OpenTrace &T = ctx->trace;
+    const FieldSlot &fs = *T.fs;
+    const int64_t n_rays = T.rs.n_rays;
+    const int nr = T.rs.nr;
+    Scratch &s = ctx->scr;
+    const int stop = std::min(T.total, T.next + n);
+    for (; T.next < stop; ++T.next) {
+        const int g = T.next, step = g / 4, stage = g % 4;
+        // extra steps past the table run only while some ray is not across
+        const unsigned long long *gate = step >= T.b.n_steps ? s.counters + ((step - 1) & 1) : nullptr;
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (T.timed && !gate) {
+            e0 = timing_event(ctx);
+            e1 = timing_event(ctx);
+            if (e0) CK(cudaEventRecord(e0, st));
         }
+        if (fs.is_grid)
+            CK(launch_grid_eval(fs.gd, T.rs.ys + n_rays, T.rs.ys + 2 * n_rays, T.rs.ys + 3 * n_rays, n_rays,
+                                T.fp64 ? 1 : 0, s.partials, gate, st, nr));
+        else
+            CK(run_force(ctx, fs.df, T.rs.ys + n_rays, T.rs.ys + 2 * n_rays, T.rs.ys + 3 * n_rays,
+                         T.rs.rep + (g & 1) * T.n_b, nr, n_rays, T.sh, T.fp64, s.partials, gate, st));
+        if (e1) CK(cudaEventRecord(e1, st));
+        if (T.use_prism) {
+            CK(launch_prism(T.tp, fs.df, T.rs, step, stage, s.counters, s.prism, st));
+            ++T.launches;
+        }
+        CK(launch_stage(T.tp, fs.df, T.rs, T.sh, T.fp64, s.partials, s.dlam, s.misc, step, stage, s.counters, st,
+                        T.use_prism ? s.prism : nullptr));
+        T.launches += 2;
+        T.flaunch += gate ? 0 : 1;
     }
-    CK(launch_reduce(tp, d_theta, rs, s.misc, d_bout, d_rout, st));
-    launches += 1;
-    ctx->stats.launches = launches;
-    ctx->stats.force_launches = flaunch;
-    ctx->stats.steps = total;
-    ctx->stats.rays_per_thread = sh.R;
-    ctx->stats.threads_per_block = sh.NT;
-    ctx->stats.splits = sh.splits;
-    ctx->stats.cluster = sh.cl;
-    ctx->stats.variant = sh.variant;
+    ctx->stats.launches = T.launches;
+    ctx->stats.force_launches = T.flaunch;
+    ctx->stats.steps = (T.next + 3) / 4;
+    ctx->stats.rays_per_thread = T.sh.R;
+    ctx->stats.threads_per_block = T.sh.NT;
+    ctx->stats.splits = T.sh.splits;
+    ctx->stats.cluster = T.sh.cl;
+    ctx->stats.variant = T.sh.variant;
     // grid path: one field evaluation per ray and stage counts as one
     ctx->last_npart = fs.is_grid ? 1.0 : (double)fs.n;
     ctx->stats_pending = true;
     return RT3D_OK;
+}
+
+// the remaining stages, then the bundle reducer (S7); the trace is closed
+static int trace_end(rt3d_ctx *ctx, double *d_bout, double *d_rout, cudaStream_t st)
+{
+    OpenTrace &T = ctx->trace;
+    int rc = trace_advance(ctx, T.total - T.next, st);
+    if (rc) return rc;
+    CK(launch_reduce(T.tp, T.d_theta, T.rs, ctx->scr.misc, d_bout, d_rout, st));
+    T.launches += 1;
+    ctx->stats.launches = T.launches;
+    T.open = false;
+    return RT3D_OK;
+}
+
+// enqueue one full trace on st: schedule, init, RK4 stages, reduce
+static int enqueue_trace(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t n_b, const double *d_theta,
+                         const rt3d_bundle_opts *b, double *d_bout, double *d_rout, cudaStream_t st, bool timed)
+{
+    int rc = trace_begin(ctx, fs, z_s, n_b, d_theta, b, st, timed);
+    if (rc) return rc;
+    return trace_end(ctx, d_bout, d_rout, st);
 }
 
 static int finish_stats(rt3d_ctx *ctx)
@@ -899,6 +966,7 @@ extern "C" int rt3d_trace(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, 
                           const rt3d_bundle_opts *b, rt3d_bundle_result *out)
 {
     if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
     int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
     if (rc) return rc;
     if (!theta || !out || !out->mu) return fail(ctx, RT3D_EINVAL, "null theta or result arrays");
@@ -946,6 +1014,7 @@ extern "C" int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, doub
                                  double *d_ray_out)
 {
     if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
     int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
     if (rc) return rc;
     if (!d_theta || !d_bundle_out) return fail(ctx, RT3D_EINVAL, "null device arrays");
@@ -953,6 +1022,45 @@ extern "C" int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, doub
     cudaStream_t st = (cudaStream_t)stream;
     return enqueue_trace(ctx, ctx->fields[field_id], z_s, n_b, d_theta, b, d_bundle_out, d_ray_out, st,
                          ctx->opt.time_kernels != 0);
+}
+
+extern "C" int rt3d_trace_begin(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_b,
+                                const double *d_theta, const rt3d_bundle_opts *b)
+{
+    if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;
+    int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
+    if (rc) return rc;
+    if (!d_theta) return fail(ctx, RT3D_EINVAL, "null device theta");
+    CK(cudaSetDevice(ctx->device));
+    return trace_begin(ctx, ctx->fields[field_id], z_s, n_b, d_theta, b, (cudaStream_t)stream,
+                       ctx->opt.time_kernels != 0);
+}
+
+extern "C" int rt3d_trace_advance(rt3d_ctx *ctx, void *stream, int n_stages, int *stages_left)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (!ctx->trace.open) return fail(ctx, RT3D_EINVAL, "no open trace (rt3d_trace_begin first)");
+    if (n_stages < 0) return fail(ctx, RT3D_EINVAL, "n_stages must be >= 0");
+    CK(cudaSetDevice(ctx->device));
+    int rc = trace_advance(ctx, n_stages, (cudaStream_t)stream);
+    if (rc) {
+        ctx->trace.open = false;
+        return rc;
+    }
+    if (stages_left) *stages_left = ctx->trace.total - ctx->trace.next;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_trace_end(rt3d_ctx *ctx, void *stream, double *d_bundle_out, double *d_ray_out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    if (!ctx->trace.open) return fail(ctx, RT3D_EINVAL, "no open trace (rt3d_trace_begin first)");
+    if (!d_bundle_out) return fail(ctx, RT3D_EINVAL, "null device bundle output");
+    CK(cudaSetDevice(ctx->device));
+    int rc = trace_end(ctx, d_bundle_out, d_ray_out, (cudaStream_t)stream);
+    ctx->trace.open = false;
+    return rc;
 }
 
 // ---------------------------------------------------------------------------
@@ -1241,6 +1349,7 @@ extern "C" int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *con
                                 rt3d_bundle_result *outs)
 {
     if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
     if (n_cones < 1 || !cones || !outs) return fail(ctx, RT3D_EINVAL, "need n_cones >= 1, cones and outputs");
     int rc = check_bundle_opts(ctx, b);
     if (rc) return rc;
@@ -1483,6 +1592,9 @@ extern "C" int rt3d_histogram_device(rt3d_ctx *ctx, void *stream, int64_t n, con
 extern "C" int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                               double soft, const rt3d_grid_opts *g)
 {
+    if (ctx && field_id >= 0 && field_id < RT3D_MAX_FIELDS && ctx->trace.open &&
+        ctx->trace.fs == &ctx->fields[field_id])
+        ctx->trace.open = false;  // the open trace's field is replaced
     if (!ctx) return RT3D_EINVAL;
     if (field_id < 0 || field_id >= RT3D_MAX_FIELDS) return fail(ctx, RT3D_EINVAL, "field id out of range");
     if (!g) return fail(ctx, RT3D_EINVAL, "null grid options");
@@ -1527,6 +1639,9 @@ extern "C" int rt3d_load_grid(rt3d_ctx *ctx, int field_id, int64_t n, const doub
 extern "C" int rt3d_load_grid_box(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos, const double *mass,
                                   double soft, const rt3d_volume *vol, int cubes, const rt3d_grid_opts *g)
 {
+    if (ctx && field_id >= 0 && field_id < RT3D_MAX_FIELDS && ctx->trace.open &&
+        ctx->trace.fs == &ctx->fields[field_id])
+        ctx->trace.open = false;  // the open trace's field is replaced
     if (!ctx) return RT3D_EINVAL;
     if (field_id < 0 || field_id >= RT3D_MAX_FIELDS) return fail(ctx, RT3D_EINVAL, "field id out of range");
     if (!g || !vol || !vol->replicated) return fail(ctx, RT3D_EINVAL, "a replicated volume and grid options are needed");
@@ -1609,6 +1724,7 @@ extern "C" int rt3d_born(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, c
                          const rt3d_bundle_opts *b, double *out)
 {
     if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
     int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
     if (rc) return rc;
     if (!theta || !out) return fail(ctx, RT3D_EINVAL, "null theta or output");
@@ -1623,7 +1739,7 @@ extern "C" int rt3d_born(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, c
     const int K = (int)std::max<int64_t>(1, std::min<int64_t>(n + 1, ((int64_t)1 << 18) / n_b));
     const int64_t blocks = ((int64_t)K * n_b + 511) / 512;
     const int64_t tiles = std::max<int64_t>(1, (fs.n + kTile - 1) / kTile);
-    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (152 * 4 * 5 + blocks - 1) / blocks));
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)ctx->n_sm * 4 * 5 + blocks - 1) / blocks));
     Scratch &sc = ctx->scr;
     CK(grow(sc.theta, sc.theta_n, (size_t)(2 * n_b)));
     CK(grow(sc.bout, sc.bout_n, (size_t)(6 * n_b)));
@@ -1698,6 +1814,7 @@ extern "C" int rt3d_schedule(rt3d_ctx *ctx, double z_s, int kind, int n_steps, d
                              double *dlam_out, double *chi_s_out)
 {
     if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
     if (!ctx->have_cosmo) return fail(ctx, RT3D_ENOCOSMO, "set the cosmology first");
     if (!(z_s > 0.0) || n_steps < 1 || !dlam_out || (kind != RT3D_SCHED_UNIFORM && kind != RT3D_SCHED_ASINH) ||
         (kind == RT3D_SCHED_ASINH && !(s > 0.0)))

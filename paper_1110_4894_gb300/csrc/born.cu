@@ -66,7 +66,7 @@ __global__ void __launch_bounds__(NT) k_hess(ForceArgs A)
     const int64_t base = (int64_t)blockIdx.x * (NT * R);
     const int split = blockIdx.y;
     int myrep[R], rmin, rmax;
-    block_replica_range<R, NT>(A, base, myrep, rmin, rmax);
+    block_replica_range<R, NT>(A, f.n_rep, base, myrep, rmin, rmax);
     float hi[R][3], lo[R][3];
 #pragma unroll
     for (int k = 0; k < R; ++k)
@@ -76,11 +76,12 @@ __global__ void __launch_bounds__(NT) k_hess(ForceArgs A)
     const int64_t p1 = min(f.n, p0 + A.per_split);
     const float dlt = (float)f.delta;
     for (int j = rmin; j <= rmax; ++j) {
+        if (!block_uses_replica<R>(myrep, j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((A.px[base] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((A.py[base] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((A.pz[base] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(A.px[base], o[0], f.inv_delta);
+        const long long ay = anchor_q(A.py[base], o[1], f.inv_delta);
+        const long long az = anchor_q(A.pz[base], o[2], f.inv_delta);
         float rx[R], ry[R], rz[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {

@@ -60,9 +60,25 @@ __device__ __forceinline__ void two_sum_into(float &hi, float &lo, float x)
     lo += err;
 }
 
+// grid coordinate of a block's anchor: the offset of x from the frame origin
+// o, rounded to the grid; 0 (the frame origin itself) when x is not finite or
+// lies beyond 2^62 grid units, so that one bad point cannot spoil the offsets
+// of the other points of its block (a NaN fails the comparison)
+__device__ __forceinline__ long long anchor_q(double x, double o, double inv_delta)
+{
+    const double q = (x - o) * inv_delta;
+    return fabs(q) < 4.0e18 ? __double2ll_rn(q) : 0ll;
+}
+
+// replica index r of a point, or -1 (the point takes part in no replica's
+// pass and its sums stay zero) when r is outside [0, n_rep)
+__device__ __forceinline__ int checked_replica(int r, int n_rep) { return (r >= 0 && r < n_rep) ? r : -1; }
+
+// Replica range [rmin, rmax] of the block's points (rmin > rmax when no point
+// has a valid replica).  Indices outside [0, n_rep) are left out.
 template <int R, int NT>
-__device__ __forceinline__ void block_replica_range(const ForceArgs &A, int64_t base, int myrep[R], int &rmin,
-                                                    int &rmax)
+__device__ __forceinline__ void block_replica_range(const ForceArgs &A, int n_rep, int64_t base, int myrep[R],
+                                                    int &rmin, int &rmax)
 {
     __shared__ int s_rmin, s_rmax;
     if (threadIdx.x == 0) {
@@ -75,14 +91,27 @@ __device__ __forceinline__ void block_replica_range(const ForceArgs &A, int64_t 
         const int64_t i = base + (int64_t)k * NT + threadIdx.x;
         myrep[k] = -1;
         if (i < A.n) {
-            myrep[k] = A.rep ? A.rep[i / A.group] : 0;
-            atomicMin(&s_rmin, myrep[k]);
-            atomicMax(&s_rmax, myrep[k]);
+            myrep[k] = checked_replica(A.rep ? A.rep[i / A.group] : 0, n_rep);
+            if (myrep[k] >= 0) {
+                atomicMin(&s_rmin, myrep[k]);
+                atomicMax(&s_rmax, myrep[k]);
+            }
         }
     }
     __syncthreads();
     rmin = s_rmin;
     rmax = s_rmax;
+}
+
+// true in every thread of the block when some thread holds a point of replica
+// j (a block barrier: every thread of the block must call it)
+template <int R>
+__device__ __forceinline__ bool block_uses_replica(const int myrep[R], int j)
+{
+    int mine = 0;
+#pragma unroll
+    for (int k = 0; k < R; ++k) mine |= myrep[k] == j;
+    return __syncthreads_or(mine) != 0;
 }
 
 template <int R, int NT, bool REPL, bool PEPS>
@@ -96,7 +125,7 @@ __global__ void __launch_bounds__(NT) k_force_mixed(ForceArgs A)
     const int64_t base = (int64_t)blockIdx.x * (NT * R);
     const int split = blockIdx.y;
     int myrep[R], rmin, rmax;
-    block_replica_range<R, NT>(A, base, myrep, rmin, rmax);
+    block_replica_range<R, NT>(A, f.n_rep, base, myrep, rmin, rmax);
 
     float hi[R][4], lo[R][4];
 #pragma unroll
@@ -108,11 +137,12 @@ __global__ void __launch_bounds__(NT) k_force_mixed(ForceArgs A)
     const int64_t p1 = min(f.n, p0 + A.per_split);
     const float dlt = (float)f.delta;
     for (int j = rmin; j <= rmax; ++j) {
+        if (!block_uses_replica<R>(myrep, j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((A.px[base] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((A.py[base] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((A.pz[base] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(A.px[base], o[0], f.inv_delta);
+        const long long ay = anchor_q(A.py[base], o[1], f.inv_delta);
+        const long long az = anchor_q(A.pz[base], o[2], f.inv_delta);
         float rx[R], ry[R], rz[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {
@@ -220,7 +250,7 @@ __device__ __forceinline__ void packed_block_sum(const DevField &f, const double
     A.group = group;
     A.n = n;
     int myrep[R], rmin, rmax;
-    block_replica_range<R, NT>(A, base, myrep, rmin, rmax);
+    block_replica_range<R, NT>(A, f.n_rep, base, myrep, rmin, rmax);
 
     float2 phi[P], hx[P], hy[P], hz[P], lx[P], ly[P], lz[P];
 #pragma unroll
@@ -230,11 +260,12 @@ __device__ __forceinline__ void packed_block_sum(const DevField &f, const double
     const float dlt = (float)f.delta;
     const float2 E2u = make_float2(f.eps2u, f.eps2u);
     for (int j = rmin; j <= rmax; ++j) {
+        if (!block_uses_replica<R>(myrep, j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((px[base] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((py[base] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((pz[base] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(px[base], o[0], f.inv_delta);
+        const long long ay = anchor_q(py[base], o[1], f.inv_delta);
+        const long long az = anchor_q(pz[base], o[2], f.inv_delta);
         // negated ray offsets: d = particle + (-ray)
         float2 nx[P], ny[P], nz[P];
 #pragma unroll
@@ -378,8 +409,8 @@ __device__ __forceinline__ void bundle_block_sum(const DevField &f, const double
         s_rmax = INT_MIN;
     }
     __syncthreads();
-    const int myrep = valid ? (rep ? rep[b] : 0) : -1;
-    if (valid) {
+    const int myrep = valid ? checked_replica(rep ? rep[b] : 0, f.n_rep) : -1;
+    if (myrep >= 0) {
         atomicMin(&s_rmin, myrep);
         atomicMax(&s_rmax, myrep);
     }
@@ -411,11 +442,12 @@ __device__ __forceinline__ void bundle_block_sum(const DevField &f, const double
     const float dlt = (float)f.delta;
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
     for (int j = rmin; j <= rmax; ++j) {
+        if (!__syncthreads_or(myrep == j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((px[ia] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((py[ia] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((pz[ia] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(px[ia], o[0], f.inv_delta);
+        const long long ay = anchor_q(py[ia], o[1], f.inv_delta);
+        const long long az = anchor_q(pz[ia], o[2], f.inv_delta);
         float nx = -1e30f, ny = -1e30f, nz = -1e30f;  // far sentinel
         if (valid && myrep == j) {
             nx = -(float)(((px[ic] - o[0]) * f.inv_delta - (double)ax) * f.delta);
@@ -553,8 +585,8 @@ __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const doubl
     int myrep[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        myrep[h] = valid[h] ? (rep ? rep[bb[h]] : 0) : -1;
-        if (valid[h]) {
+        myrep[h] = valid[h] ? checked_replica(rep ? rep[bb[h]] : 0, f.n_rep) : -1;
+        if (myrep[h] >= 0) {
             atomicMin(&s_rmin, myrep[h]);
             atomicMax(&s_rmax, myrep[h]);
         }
@@ -589,11 +621,12 @@ __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const doubl
     const float2 E2u = make_float2(f.eps2u, f.eps2u);
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
     for (int j = rmin; j <= rmax; ++j) {
+        if (!block_uses_replica<2>(myrep, j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((px[ia] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((py[ia] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((pz[ia] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(px[ia], o[0], f.inv_delta);
+        const long long ay = anchor_q(py[ia], o[1], f.inv_delta);
+        const long long az = anchor_q(pz[ia], o[2], f.inv_delta);
         float nc[2][3];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -750,8 +783,8 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     int myrep[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        myrep[h] = valid[h] ? (rep ? rep[bb[h]] : 0) : -1;
-        if (valid[h]) {
+        myrep[h] = valid[h] ? checked_replica(rep ? rep[bb[h]] : 0, f.n_rep) : -1;
+        if (myrep[h] >= 0) {
             atomicMin(&s_rmin, myrep[h]);
             atomicMax(&s_rmax, myrep[h]);
         }
@@ -788,11 +821,12 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     const float2 E2u = make_float2(f.eps2u, f.eps2u);
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
     for (int j = rmin; j <= rmax; ++j) {
+        if (!block_uses_replica<2>(myrep, j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((px[ia] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((py[ia] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((pz[ia] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(px[ia], o[0], f.inv_delta);
+        const long long ay = anchor_q(py[ia], o[1], f.inv_delta);
+        const long long az = anchor_q(pz[ia], o[2], f.inv_delta);
         float nc[2][3];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
@@ -1038,7 +1072,7 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
     const int64_t base = (int64_t)blockIdx.x * (NT * R);
     const int split = blockIdx.y;
     int myrep[R], rmin, rmax;
-    block_replica_range<R, NT>(A, base, myrep, rmin, rmax);
+    block_replica_range<R, NT>(A, f.n_rep, base, myrep, rmin, rmax);
     double acc[R][4];
 #pragma unroll
     for (int k = 0; k < R; ++k)
@@ -1047,11 +1081,12 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
     const int64_t p0 = (int64_t)split * A.per_split;
     const int64_t p1 = min(f.n, p0 + A.per_split);
     for (int j = rmin; j <= rmax; ++j) {
+        if (!block_uses_replica<R>(myrep, j)) continue;  // no point of this block is in replica j
         double o[3];
         frame_origin(f, j, o);
-        const long long ax = __double2ll_rn((A.px[base] - o[0]) * f.inv_delta);
-        const long long ay = __double2ll_rn((A.py[base] - o[1]) * f.inv_delta);
-        const long long az = __double2ll_rn((A.pz[base] - o[2]) * f.inv_delta);
+        const long long ax = anchor_q(A.px[base], o[0], f.inv_delta);
+        const long long ay = anchor_q(A.py[base], o[1], f.inv_delta);
+        const long long az = anchor_q(A.pz[base], o[2], f.inv_delta);
         double rx[R], ry[R], rz[R];
 #pragma unroll
         for (int k = 0; k < R; ++k) {

@@ -389,8 +389,8 @@ void grid_free(GridDev &g)
 
 static unsigned blocks_for(int64_t m)
 {
-    const int64_t b = (m + 255) / 256;
-    return (unsigned)(b < 152 * 64 ? (b > 0 ? b : 1) : 152 * 64);
+    const int64_t b = (m + 255) / 256, cap = (int64_t)device_sm_count() * 64;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
 }
 
 namespace {

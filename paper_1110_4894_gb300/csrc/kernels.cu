@@ -81,9 +81,21 @@ cudaError_t launch_init(const TraceParams &tp, const DevField &f, const double *
 // which keeps four times more loads in flight), then one thread per ray runs
 // the FP64 stage update with whole warps active.
 constexpr int kStageRays = 64;
-// from this many rays on, one ray per thread still gives every SM several
-// blocks of 256
-constexpr int kStageWideRays = 152 * 4 * 256;
+// from this many rays on (four blocks of 256 per SM), one ray per thread
+// still gives every SM several blocks
+static int64_t stage_wide_rays() { return (int64_t)device_sm_count() * 4 * 256; }
+
+int device_sm_count()
+{
+    static int cache[64] = {0};
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 152;
+    if (dev >= 0 && dev < 64 && cache[dev] > 0) return cache[dev];
+    int sms = 0;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) return 152;
+    if (dev >= 0 && dev < 64) cache[dev] = sms;
+    return sms;
+}
 
 // the bundles' prism records of this stage (mean-subtracted boxes), read by
 // every ray of the bundle in k_stage
@@ -167,7 +179,7 @@ cudaError_t launch_stage(const TraceParams &tp, const DevField &f, RayState rs, 
 {
     const int S = partial_splits(sh);
     const double mfac = partial_mass_factor(f, sh);
-    if (S <= 8 || rs.n_rays >= (int64_t)kStageWideRays) {
+    if (S <= 8 || rs.n_rays >= stage_wide_rays()) {
         const int64_t blocks = (rs.n_rays + 255) / 256;
         k_stage_wide<<<(unsigned)blocks, 256, 0, st>>>(tp, f, rs, S, fp64 ? 1 : 0, mfac, d_partials, d_dlam, d_misc,
                                                        step, stage, d_counters, d_prism);
@@ -187,8 +199,16 @@ __global__ void k_field_points(DevField f, int S, int fp64, double mfac, const v
     const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const double p[3] = {pts[i], pts[n + i], pts[2 * n + i]};
+    const int r = rep ? rep[i] : 0;
     double F[4];
-    gather_field(f, S, fp64 != 0, partials, n, i, rep ? rep[i] : 0, p, mfac, F);
+    if (r < 0 || r >= f.n_rep || !isfinite(p[0]) || !isfinite(p[1]) || !isfinite(p[2])) {
+        // a replica index outside [0, n_rep) or a non-finite point: the pair
+        // sum skipped it, and its result is NaN rather than a silent value
+#pragma unroll
+        for (int o = 0; o < 4; ++o) out[4 * i + o] = __longlong_as_double(0x7ff8000000000000ll);
+        return;
+    }
+    gather_field(f, S, fp64 != 0, partials, n, i, r, p, mfac, F);
 #pragma unroll
     for (int o = 0; o < 4; ++o) out[4 * i + o] = F[o];
 }

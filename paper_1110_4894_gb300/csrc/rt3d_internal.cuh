@@ -295,6 +295,10 @@ struct Scratch {
     size_t prism_n = 0;
 };
 
+// streaming multiprocessors of the current device (queried once per device;
+// 152 on GB300), for grid sizes counted in waves of resident blocks
+int device_sm_count();
+
 // kernels (launch wrappers; return cudaError_t of the launch)
 // fill the a(t) table of c (n nodes, spacing h) at d_tab
 cudaError_t launch_atab(const Cosmo &c, int n, double h, double *d_tab, cudaStream_t st);

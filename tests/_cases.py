@@ -22,7 +22,7 @@ def gpu_load(ctx, fid, cfg):
 
 def trace_kw(cfg):
     return dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=cfg["schedule"], n_steps=cfg["n_steps"],
-                lens_chi=cfg.get("lens_chi", 0.0), asinh_s=cfg.get("asinh_s", 1.0))
+                lens_chi=cfg.get("lens_chi", 0.0), asinh_s=cfg.get("asinh_s", 1.0), phase=cfg.get("phase", 0.0))
 
 
 def run_oracle(cfg, theta, cosmo=None, christoffel=0, nthreads=None):

@@ -63,3 +63,30 @@ def test_oracle_and_library_share_nothing():
         if f.endswith((".c", ".h", ".py")):
             txt = open(os.path.join(ROOT, "oracle", f)).read()
             assert "rt3d" not in txt and "paper_1110_4894_gb300" not in txt, f
+
+
+def declarations_with_comments():
+    """(name, the comment block right above its declaration) for every
+    entry point of include/*.h"""
+    out = []
+    for h in os.listdir(os.path.join(ROOT, "include")):
+        if not h.endswith(".h"):
+            continue
+        txt = open(os.path.join(ROOT, "include", h)).read()
+        for m in re.finditer(r"^(?:int|const char \*)\s*(rt3d_[a-z_]+)\s*\(", txt, flags=re.M):
+            head = txt[:m.start()]
+            end = head.rfind("*/")
+            start = head.rfind("/*", 0, end)
+            between = head[end + 2:]
+            # only #defines may sit between the comment and the declaration
+            assert all(l.strip() == "" or l.startswith("#define") for l in between.splitlines()), m.group(1)
+            out.append((m.group(1), head[start:end]))
+    return out
+
+
+def test_every_declaration_cites_its_passage():
+    decl = declarations_with_comments()
+    assert len(decl) == len(declared())
+    cite = re.compile(r"\b(Sec\.|Eqs?\.|App\.|Fig\.)")
+    for name, comment in decl:
+        assert cite.search(comment) or "no counterpart" in comment, name

@@ -29,3 +29,32 @@ def test_nfw_full_size_sampled(cosmo):
     st = ctx.stats()
     # every active ray meets every particle at every stage
     assert st["interactions"] >= nb * 5 * 100000 * 4 * cfg["n_steps"] * 0.99
+
+
+def test_nfw_full_size_ring_of_eight_sampled(cosmo):
+    """The paper's bundle (8 rays on a polygon around the central ray, Sec.
+    3.1 and Sec. 5.2) on the full NFW workload: mixed precision on all 4096
+    bundles against the oracle on 8 sampled bundles, and the all-FP64 path
+    on those 8 bundles against the oracle to rounding."""
+    import paper_1110_4894_gb300 as P
+    cfg = inputs.config_c2()
+    cfg["n_ring"] = 8
+    cfg["phase"] = 0.2
+    ctx = P.Context(0, precision=P.MIXED, autotune=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    nb = cfg["theta"].shape[0]
+    assert np.all(g["flags"] & (P.F_NOCROSS | P.F_NONFINITE) == 0)
+    idx = np.linspace(0, nb - 1, 8).astype(int)
+    o = run_oracle(cfg, cfg["theta"][idx], cosmo)
+    assert np.array_equal(g["flags"][idx], o.flags)
+    assert rel_mu(g["mu"][idx], o.mu).max() < 1e-4
+    assert rel_alpha(g["rays"][idx], o).max() < 1e-5
+    c64 = P.Context(0, precision=P.FP64)
+    c64.set_cosmology(*cfg["cosmo"])
+    gpu_load(c64, 0, cfg)
+    g64 = c64.trace(0, cfg["z_s"], cfg["theta"][idx], want_rays=True, **trace_kw(cfg))
+    assert np.array_equal(g64["flags"], o.flags) and np.array_equal(g64["steps"], o.steps)
+    assert rel_mu(g64["mu"], o.mu).max() < 1e-9
+    assert rel_alpha(g64["rays"], o).max() < 1e-9

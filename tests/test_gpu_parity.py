@@ -139,8 +139,13 @@ def _c2_small(n_particles=20000, n_side=4, n_steps=300):
 
 
 @pytest.mark.parametrize("precision", PRECISIONS)
-def test_c2_small_nfw(P, cosmo, precision):
+@pytest.mark.parametrize("n_ring", [4, 8])
+def test_c2_small_nfw(P, cosmo, precision, n_ring):
+    # rings of 8 are the paper's bundle (Sec. 3.1, Sec. 5.2); phase turns the polygon
     cfg = _c2_small()
+    cfg["n_ring"] = n_ring
+    if n_ring == 8:
+        cfg["phase"] = 0.3
     ctx = ctx_prec(P, precision)
     gpu_load(ctx, 0, cfg)
     g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
@@ -267,6 +272,8 @@ def test_errors_are_reported(P):
     with pytest.raises(P.Rt3dError):
         ctx.trace(0, 0.5, np.zeros((1, 2)), n_ring=1)
     with pytest.raises(P.Rt3dError):
+        ctx.trace(0, 0.5, np.zeros((1, 2)), n_ring=2)  # collinear: no Jacobian
+    with pytest.raises(P.Rt3dError):
         ctx.trace(0, 0.5, np.full((1, 2), np.nan))
 
 
@@ -305,3 +312,68 @@ def test_autotuned_shape_keeps_parity(P, cosmo):
     o = run_oracle(cfg, cfg["theta"], cosmo)
     assert rel_mu(g["mu"], o.mu).max() < MU_GATE
     assert rel_alpha(g["rays"], o).max() < ALPHA_GATE
+
+
+@pytest.mark.parametrize("box", [False, True])
+def test_trace_in_pieces_matches_whole_trace(P, cosmo, box):
+    """rt3d_trace_begin / advance / end run the same kernels in the same order
+    as rt3d_trace_device: results are bit-identical, whatever the pieces."""
+    import torch
+    if box:
+        b = _small_box()
+        z_s = 0.02
+        half = (0.5 * b["L"] - 2.0) / cosmo.chi(z_s)
+        cfg = dict(b, replicated=True, mean_subtract=True, cosmo=(0.3, 0.7, 0.7), z_s=z_s, n_ring=4,
+                   theta_r=math.radians(1 / 3600), schedule=0, n_steps=40)
+        theta = inputs.bundle_grid(-half, half, 4)
+    else:
+        cfg = _c2_small(n_particles=3000, n_side=4, n_steps=60)
+        theta = cfg["theta"]
+    ctx = ctx_for(P, P.MIXED)
+    gpu_load(ctx, 0, cfg)
+    nb = theta.shape[0]
+    d_theta = torch.from_numpy(np.ascontiguousarray(theta)).cuda()
+    ref = torch.zeros(nb * 6, dtype=torch.float64, device="cuda")
+    rays_ref = torch.zeros(nb * 5 * 8, dtype=torch.float64, device="cuda")
+    sp = torch.cuda.current_stream().cuda_stream
+    kw = trace_kw(cfg)
+    ctx.trace_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), ref.data_ptr(), rays_ref.data_ptr(), **kw)
+    torch.cuda.synchronize()
+    inter_ref = ctx.stats()["interactions"]
+    out = torch.zeros_like(ref)
+    rays = torch.zeros_like(rays_ref)
+    ctx.trace_begin(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), **kw)
+    total = 4 * (kw["n_steps"] + 16)
+    left = ctx.trace_advance(sp, 1)
+    assert left == total - 1
+    left = ctx.trace_advance(sp, 7)
+    assert left == total - 8
+    left = ctx.trace_advance(sp, 101)
+    assert left == total - 109
+    ctx.trace_end(sp, out.data_ptr(), rays.data_ptr())
+    torch.cuda.synchronize()
+    assert torch.equal(out, ref) and torch.equal(rays, rays_ref)
+    assert ctx.stats()["interactions"] == inter_ref
+    o = run_oracle(cfg, theta, cosmo)
+    assert rel_mu(out.view(nb, 6)[:, 0].cpu().numpy(), o.mu).max() < MU_GATE
+
+
+def test_trace_in_pieces_errors(P):
+    import torch
+    cfg = _c2_small(n_particles=500, n_side=2, n_steps=20)
+    ctx = ctx_for(P, P.MIXED)
+    gpu_load(ctx, 0, cfg)
+    sp = torch.cuda.current_stream().cuda_stream
+    d_theta = torch.from_numpy(np.ascontiguousarray(cfg["theta"])).cuda()
+    out = torch.zeros(cfg["theta"].shape[0] * 6, dtype=torch.float64, device="cuda")
+    with pytest.raises(P.Rt3dError) as e:
+        ctx.trace_advance(sp, 4)
+    assert e.value.code == -1
+    ctx.trace_begin(sp, 0, cfg["z_s"], cfg["theta"].shape[0], d_theta.data_ptr(), **trace_kw(cfg))
+    ctx.trace_advance(sp, 4)
+    ctx.schedule(0.5, 0, 10)  # reuses the step table: closes the open trace
+    with pytest.raises(P.Rt3dError):
+        ctx.trace_advance(sp, 4)
+    with pytest.raises(P.Rt3dError):
+        ctx.trace_end(sp, out.data_ptr())
+    torch.cuda.synchronize()

@@ -82,3 +82,49 @@ def test_noalloc_matches_potential_replicated():
                                      d_out.data_ptr())
     assert e.value.code == -1
     ctx.close()
+
+
+def test_noalloc_bad_points_give_nan_and_spare_the_rest():
+    """Replica indices outside [0, n_replicas) and non-finite points arrive
+    in device memory, where the host cannot check them: the kernels skip them
+    and write NaN for exactly those points; every other point, including the
+    ones that share a block with a bad first point, keeps its value."""
+    import torch
+
+    import paper_1110_4894_gb300 as P
+    ctx = P.Context(0)
+    ctx.set_cosmology()
+    L = inputs.box_length(20.0 / 0.7)
+    pos, mass, _ = inputs.halo_box(3000, L, 8, seed=78)
+    rot, shift = inputs.replicas(4, L, seed=78)
+    ctx.load_particles(3, pos, mass, 0.02, replicated=True, box_length=L, rot=rot, shift=shift, mean_subtract=True)
+    g = inputs.rng(10)
+    m = 600
+    rep = np.sort(g.integers(0, 4, m)).astype(np.int32)
+    pts = np.stack([g.uniform(-0.5, 0.5, m) * L, g.uniform(-0.5, 0.5, m) * L, (rep + g.random(m)) * L], 1)
+    ref = ctx.potential(3, pts, rep)
+    bad_rep = {5: -1, 300: 4, 301: 1 << 30}
+    bad_pt = [0, 450]  # index 0 is the anchor of the first block of points
+    rep_d, pts_d = rep.copy(), pts.copy()
+    for i, r in bad_rep.items():
+        rep_d[i] = r
+    pts_d[0, 1] = np.nan
+    pts_d[450, 2] = np.inf
+    stream = torch.cuda.current_stream()
+    d_pts = torch.from_numpy(np.ascontiguousarray(pts_d.T)).cuda()
+    d_rep = torch.from_numpy(rep_d).cuda()
+    d_out = torch.zeros((m * 4,), dtype=torch.float64, device="cuda")
+    ctx.potential_device_noalloc(stream.cuda_stream, 3, m, d_pts.data_ptr(), d_rep.data_ptr(), d_out.data_ptr())
+    torch.cuda.synchronize()
+    out = d_out.cpu().numpy().reshape(m, 4)
+    bad = sorted(list(bad_rep) + bad_pt)
+    assert np.all(np.isnan(out[bad]))
+    good = np.setdiff1d(np.arange(m), bad)
+    assert np.all(np.isfinite(out[good]))
+    sc = np.linalg.norm(ref[:, 1:], axis=1).max()
+    # the first block lost its anchor and measures offsets from the replica
+    # frame's origin instead (FP32 rounding of ~L): a looser bound there
+    assert np.all(np.abs(out[good, 1:] - ref[good, 1:]) < 1e-3 * sc)
+    far = good[good >= 256]
+    assert np.all(np.abs(out[far, 1:] - ref[far, 1:]) < 1e-5 * sc)
+    ctx.close()
