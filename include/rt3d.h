@@ -295,7 +295,10 @@ int rt3d_trace_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int
  * (or streams ordered after it).  rt3d_get_stats counts from rt3d_trace_begin. */
 int rt3d_trace_begin(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_bundles,
                      const double *d_theta, const rt3d_bundle_opts *b);
+/* The next n_stages RK4 stages of the open trace (Sec. 3.4), as above. */
 int rt3d_trace_advance(rt3d_ctx *ctx, void *stream, int n_stages, int *stages_left);
+/* The rest of the open trace and its bundle reducer (Sec. 3.4, Eq. lensmap),
+ * as above; the trace is closed. */
 int rt3d_trace_end(rt3d_ctx *ctx, void *stream, double *d_bundle_out, double *d_ray_out);
 
 /* Many lines of sight of Sec. 5 (each cone a mass distribution of Sec. 3.3
@@ -314,6 +317,19 @@ int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones,
  * non-finite entries are excluded; flags may be NULL. */
 int rt3d_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, const int32_t *flags,
                    const rt3d_hist_opts *o, rt3d_hist *out);
+
+/* The muPDF (Sec. 5.3, Eq. weighthisto) or shear PDF of the union of n_parts
+ * disjoint sets of bundles -- the ranks of a run over several GPUs, each of
+ * which binned its own bundles with the same bins and range -- from the
+ * parts' histograms: counts and fixed-point weights add exactly, as do the
+ * integer counters; the weighted mean is sum W_p mean_p / W and the weighted
+ * spread comes from sum W_p (sigma_p^2 + (mean_p - mean)^2) / W (compensated
+ * sums).  parts: n_parts histograms (host; counts, wfix of bins each); out:
+ * caller-owned counts and wfix of bins, scalars written.  A host computation:
+ * no device is touched, so it also runs where no GPU is present (ctx may be
+ * NULL; then no error message is kept).  Errors: RT3D_EINVAL (null arrays,
+ * n_parts or bins < 1, a negative or non-finite scalar). */
+int rt3d_histogram_combine(rt3d_ctx *ctx, int n_parts, int bins, const rt3d_hist *parts, rt3d_hist *out);
 
 /* Shear PDF (Sec. 5.4, Fig. RBMvsMudShear) of n bundles: bins uniform in
  * log10|gamma|, |gamma| = sqrt(gamma1^2 + gamma2^2), over [o->mu_min,

@@ -7,5 +7,5 @@ library cannot be loaded, every entry point raises.
 """
 from ._binding import (  # noqa: F401
     CHRISTOFFEL_DERIVED, CHRISTOFFEL_PAPER, FP64, F_NEGPARITY, F_NOCROSS, F_NONFINITE, MIXED,
-    SCHED_ASINH, SCHED_UNIFORM, Rt3dError, Context, lib, library_path,
+    SCHED_ASINH, SCHED_UNIFORM, Rt3dError, Context, histogram_combine, lib, library_path,
 )

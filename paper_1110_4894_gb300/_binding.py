@@ -107,6 +107,7 @@ def lib(build=True):
         "rt3d_trace_advance": ([vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rt3d_trace_end": ([vp, vp, vp, vp], C.c_int),
         "rt3d_histogram": ([vp, C.c_int64, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)], C.c_int),
+        "rt3d_histogram_combine": ([vp, C.c_int, C.c_int, C.POINTER(Hist), C.POINTER(Hist)], C.c_int),
         "rt3d_shear_histogram": ([vp, C.c_int64, _dp, _dp, _dp, _ip, C.POINTER(HistOpts), C.POINTER(Hist)],
                                  C.c_int),
         "rt3d_histogram_device": ([vp, vp, C.c_int64, vp, C.POINTER(HistOpts), vp, vp, vp], C.c_int),
@@ -132,6 +133,36 @@ def lib(build=True):
 
 def _p(a, ct=C.c_double):
     return None if a is None else a.ctypes.data_as(C.POINTER(ct))
+
+
+_HIST_KEYS = ("n_used", "n_under", "n_over", "n_neg", "n_bad", "W_total", "mean_w", "sigma_w")
+
+
+def histogram_combine(parts):
+    """rt3d_histogram_combine: the histogram of the union of disjoint sets of
+    bundles from the parts' (counts, wfix, scalars); a host call of the
+    library that needs no GPU and no context."""
+    L = lib()
+    keep = []
+    arr = (Hist * len(parts))()
+    bins = None
+    for i, (c, w, sc) in enumerate(parts):
+        c = np.ascontiguousarray(c, np.uint64)
+        w = np.ascontiguousarray(np.asarray(w).view(np.uint64) if np.asarray(w).dtype == np.int64 else w, np.uint64)
+        if bins is None:
+            bins = c.shape[0]
+        if c.shape[0] != bins or w.shape[0] != bins:
+            raise ValueError("parts have different bin counts")
+        keep += [c, w]
+        arr[i] = Hist(_p(c, C.c_uint64), _p(w, C.c_uint64), *[int(sc[k]) for k in _HIST_KEYS[:5]],
+                      *[float(sc[k]) for k in _HIST_KEYS[5:]])
+    counts = np.zeros(bins, np.uint64)
+    wfix = np.zeros(bins, np.uint64)
+    h = Hist(_p(counts, C.c_uint64), _p(wfix, C.c_uint64))
+    rc = L.rt3d_histogram_combine(None, len(parts), int(bins), arr, C.byref(h))
+    if rc != 0:
+        raise Rt3dError(rc, "rt3d_histogram_combine failed: %s" % L.rt3d_status_string(rc).decode())
+    return counts, wfix, {k: getattr(h, k) for k in _HIST_KEYS}
 
 
 class Context:

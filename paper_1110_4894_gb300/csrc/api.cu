@@ -676,6 +676,22 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
         out = with_splits(ctx, it->second, n, fs.n, it->second.splits);  // splits slot holds the wave count
         return RT3D_OK;
     }
+    // Launches beyond 2^37 interactions (~50 ms) are timed on a proxy: the
+    // first rays (whole bundles, at most 16 waves of the largest block) against
+    // a prefix of the particles (whole tiles), so that each timing launch stays
+    // near 2^37 interactions.  Candidates cost the same per interaction on the
+    // proxy as on the whole launch; the chosen shape is then sized for the
+    // whole launch by its wave count.
+    DevField dft = fs.df;
+    int64_t n_t = n;
+    const double cap = 137438953472.0;
+    if ((double)n * (double)fs.n > cap) {
+        const int64_t nb = n / group;
+        const int64_t nb_t = std::min<int64_t>(nb, (int64_t)ctx->n_sm * 16 * 256);
+        n_t = nb_t * group;
+        const int64_t np_t = std::max<int64_t>(kTile, (int64_t)(cap / (double)n_t) / kTile * kTile);
+        dft.n = std::min<int64_t>(dft.n, np_t);
+    }
     std::vector<ForceShape> cand;
     std::vector<int> waves;
     const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
@@ -702,7 +718,12 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
                 s.R = p[0];
                 s.NT = p[1];
             }
-            cand.push_back(with_splits(ctx, s, n, fs.n, w));
+            s = with_splits(ctx, s, n_t, dft.n, w);
+            bool dup = false;  // the same launch under another wave count
+            for (const auto &c2 : cand)
+                dup |= c2.variant == s.variant && c2.R == s.R && c2.NT == s.NT && c2.cl == s.cl && c2.splits == s.splits;
+            if (dup) continue;
+            cand.push_back(s);
             waves.push_back(w);
         }
     if (cand.empty()) {
@@ -710,7 +731,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
         return RT3D_OK;
     }
     size_t need = 0;
-    for (auto &s : cand) need = std::max(need, partials_bytes(s, n, fp64));
+    for (auto &s : cand) need = std::max(need, partials_bytes(s, n_t, fp64));
     CK(grow(*(char **)&ctx->scr.partials, ctx->scr.partials_bytes, need));
     cudaEvent_t e0, e1;
     CK(cudaEventCreate(&e0));
@@ -718,10 +739,10 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     float best = 1e30f;
     size_t bi = 0;
     for (size_t c = 0; c < cand.size(); ++c) {
-        CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
+        CK(run_force(ctx, dft, px, py, pz, rep, group, n_t, cand[c], fp64, ctx->scr.partials, nullptr, st));
         for (int rep_t = 0; rep_t < 3; ++rep_t) {  // best of three: candidates are often within 1-2 %
             CK(cudaEventRecord(e0, st));
-            CK(run_force(ctx, fs.df, px, py, pz, rep, group, n, cand[c], fp64, ctx->scr.partials, nullptr, st));
+            CK(run_force(ctx, dft, px, py, pz, rep, group, n_t, cand[c], fp64, ctx->scr.partials, nullptr, st));
             CK(cudaEventRecord(e1, st));
             CK(cudaEventSynchronize(e1));
             float ms = 0.0f;
@@ -737,7 +758,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     ForceShape keep = cand[bi];
     keep.splits = waves[bi];
     ctx->tuned[key] = keep;
-    out = cand[bi];
+    out = n_t == n && dft.n == fs.df.n ? cand[bi] : with_splits(ctx, keep, n, fs.n, waves[bi]);
     return RT3D_OK;
 }
 
@@ -1567,6 +1588,65 @@ extern "C" int rt3d_shear_histogram(rt3d_ctx *ctx, int64_t n, const double *mu, 
     out->W_total = o8[5];
     out->mean_w = o8[6];
     out->sigma_w = o8[7];
+    return RT3D_OK;
+}
+
+// Sum of x into (s, c) by Neumaier's compensated addition.
+static void neumaier_add(double &s, double &c, double x)
+{
+    const double t = s + x;
+    c += fabs(s) >= fabs(x) ? (s - t) + x : (x - t) + s;
+    s = t;
+}
+
+extern "C" int rt3d_histogram_combine(rt3d_ctx *ctx, int n_parts, int bins, const rt3d_hist *parts, rt3d_hist *out)
+{
+    if (n_parts < 1 || bins < 1 || !parts || !out || !out->counts || !out->wfix)
+        return fail(ctx, RT3D_EINVAL, "need n_parts >= 1, bins >= 1, parts and output arrays");
+    for (int p = 0; p < n_parts; ++p) {
+        const rt3d_hist &h = parts[p];
+        if (!h.counts || !h.wfix) return fail(ctx, RT3D_EINVAL, "null counts or weights in a part");
+        if (h.n_used < 0 || h.n_under < 0 || h.n_over < 0 || h.n_neg < 0 || h.n_bad < 0 || !(h.W_total >= 0.0) ||
+            !isfinite(h.W_total) || !isfinite(h.mean_w) || !(h.sigma_w >= 0.0) || !isfinite(h.sigma_w))
+            return fail(ctx, RT3D_EINVAL, "a part's scalars are negative or not finite");
+    }
+    std::vector<uint64_t> c((size_t)bins, 0), w((size_t)bins, 0);
+    rt3d_hist r{};
+    double W = 0.0, Wc = 0.0, M = 0.0, Mc = 0.0;
+    for (int p = 0; p < n_parts; ++p) {
+        const rt3d_hist &h = parts[p];
+        for (int k = 0; k < bins; ++k) {
+            c[k] += h.counts[k];
+            w[k] += h.wfix[k];
+        }
+        r.n_used += h.n_used;
+        r.n_under += h.n_under;
+        r.n_over += h.n_over;
+        r.n_neg += h.n_neg;
+        r.n_bad += h.n_bad;
+        neumaier_add(W, Wc, h.W_total);
+        neumaier_add(M, Mc, h.W_total * h.mean_w);
+    }
+    W += Wc;
+    const double mean = W > 0.0 ? (M + Mc) / W : 0.0;
+    // spread of the union: each part's weighted square deviation about its own
+    // mean plus its weight times the square distance of that mean from the union's
+    double V = 0.0, Vc = 0.0;
+    for (int p = 0; p < n_parts; ++p) {
+        const rt3d_hist &h = parts[p];
+        const double d = h.mean_w - mean;
+        neumaier_add(V, Vc, h.W_total * (h.sigma_w * h.sigma_w + d * d));
+    }
+    r.W_total = W;
+    r.mean_w = mean;
+    r.sigma_w = W > 0.0 ? sqrt((V + Vc) / W) : 0.0;
+    r.counts = out->counts;
+    r.wfix = out->wfix;
+    for (int k = 0; k < bins; ++k) {
+        out->counts[k] = c[k];
+        out->wfix[k] = w[k];
+    }
+    *out = r;
     return RT3D_OK;
 }
 

@@ -1,11 +1,11 @@
 """Host-side logic of a run over several GPUs (one process per GPU).
 
 Bundles are independent lines of sight, so a multi-GPU run splits them
-between ranks and needs one exchange at the end: the muPDF.  Counts and
-fixed-point weights add exactly (integers); the weighted moments are
-recombined from each rank's (n_used, W, mean_w, sigma_w): with w = 1/|mu|,
-sum w |mu| = n_used and sum w |mu|^2 = sum |mu| = sigma^2 W + 2 mean n - mean^2 W.
-Nothing here runs on the data path of a trace.
+between ranks and needs one exchange at the end: the muPDF.  Every rank
+gathers every rank's histogram and the library's rt3d_histogram_combine
+rebuilds the histogram of the union (counts and fixed-point weights exactly,
+the weighted moments from each rank's weight, mean and spread).  Nothing here
+runs on the data path of a trace.
 """
 import numpy as np
 
@@ -19,43 +19,39 @@ def shard_range(n, rank, world):
     return lo, lo + q + (1 if rank < r else 0)
 
 
-def _moment_sums(sc):
-    n, W, m, s = sc["n_used"], sc["W_total"], sc["mean_w"], sc["sigma_w"]
-    return np.array([n, sc["n_under"], sc["n_over"], sc["n_neg"], sc["n_bad"], W,
-                     s * s * W + 2.0 * m * n - m * m * W], np.float64)
-
-
-def _from_sums(v):
-    n, W, S2 = v[0], v[5], v[6]
-    mean = n / W if W > 0 else 0.0
-    var = (S2 - 2.0 * mean * n + mean * mean * W) / W if W > 0 else 0.0
-    return dict(n_used=int(v[0]), n_under=int(v[1]), n_over=int(v[2]), n_neg=int(v[3]), n_bad=int(v[4]),
-                W_total=W, mean_w=mean, sigma_w=float(np.sqrt(max(var, 0.0))))
-
-
 def combine_histograms(parts):
     """the muPDF of the union of the ranks' bundles from per-rank
-    (counts, wfix, scalars); exact for counts and weights"""
-    counts = sum(np.asarray(c, np.uint64) for c, _, _ in parts)
-    wfix = sum(np.asarray(w, np.uint64) for _, w, _ in parts)
-    return counts, wfix, _from_sums(sum(_moment_sums(sc) for _, _, sc in parts))
+    (counts, wfix, scalars), by the library's rt3d_histogram_combine (exact
+    for counts and weights; moments from each part's weight, mean and spread)"""
+    from ._binding import histogram_combine
+    return histogram_combine(parts)
 
 
 def allreduce_histogram(counts, wfix, sc, group=None, device=None):
-    """combine_histograms across a torch.distributed process group: two
-    integer sums and one FP64 sum (device: where the tensors live, e.g. the
-    rank's GPU for nccl; None = CPU, for gloo)"""
+    """combine_histograms across a torch.distributed process group: every
+    rank gathers every rank's histogram (two integer vectors and eight
+    scalars) and combines them with the library (device: where the exchanged
+    tensors live, e.g. the rank's GPU for nccl; None = CPU, for gloo)"""
     import torch
     import torch.distributed as dist
-    ts = [torch.from_numpy(np.asarray(counts, np.int64).copy()),
-          torch.from_numpy(np.asarray(wfix, np.uint64).view(np.int64).copy()),
-          torch.from_numpy(_moment_sums(sc))]
+    from ._binding import _HIST_KEYS
+    world = dist.get_world_size(group)
+    c = torch.from_numpy(np.asarray(counts, np.uint64).view(np.int64).copy())
+    w = torch.from_numpy(np.asarray(wfix, np.uint64).view(np.int64).copy())
+    v = torch.tensor([float(sc[k]) for k in _HIST_KEYS], dtype=torch.float64)
     if device is not None:
-        ts = [t.to(device) for t in ts]
-    for t in ts:
-        dist.all_reduce(t, op=dist.ReduceOp.SUM, group=group)
-    c, w, m = (t.cpu().numpy() for t in ts)
-    return c.astype(np.uint64), w.view(np.uint64), _from_sums(m)
+        c, w, v = c.to(device), w.to(device), v.to(device)
+    gathered = []
+    for t in (c, w, v):
+        out = [torch.empty_like(t) for _ in range(world)]
+        dist.all_gather(out, t, group=group)
+        gathered.append([o.cpu().numpy() for o in out])
+    parts = []
+    for r in range(world):
+        vals = gathered[2][r]
+        scr = {k: (int(vals[i]) if i < 5 else float(vals[i])) for i, k in enumerate(_HIST_KEYS)}
+        parts.append((gathered[0][r].view(np.uint64), gathered[1][r].view(np.uint64), scr))
+    return combine_histograms(parts)
 
 
 def rank_lines_of_sight(theta, rank):

@@ -93,3 +93,32 @@ def test_ranks_trace_different_lines_of_sight():
         assert len(sets[a]) == len(th)
         for b in range(a):
             assert not (sets[a] & sets[b])
+
+
+def test_combine_shear_histograms_equals_the_whole():
+    # the shear PDF's weighted mean is not n_used / W: the combination must
+    # use each part's own mean and spread
+    g = inputs.rng(23)
+    n = 4000
+    gam = np.exp(g.uniform(np.log(1e-3), np.log(0.5), n))
+    ang = g.uniform(0, 2 * np.pi, n)
+    g1, g2 = gam * np.cos(ang), gam * np.sin(ang)
+    mu = np.exp(g.uniform(np.log(0.5), np.log(5.0), n))
+    flags = np.zeros(n, np.int32)
+    whole = oracle.shear_histogram(mu, g1, g2, flags, 64, 1e-3, 1.0)
+    parts = []
+    for r in range(4):
+        lo, hi = shard_range(n, r, 4)
+        parts.append(oracle.shear_histogram(mu[lo:hi], g1[lo:hi], g2[lo:hi], flags[lo:hi], 64, 1e-3, 1.0))
+    _check(combine_histograms(parts), whole)
+
+
+def test_combine_rejects_bad_parts():
+    import paper_1110_4894_gb300 as P
+    mu, flags = _mu(200)
+    c, w, sc = oracle.histogram(mu, flags, 10, 0.5, 5.0)
+    bad = dict(sc, W_total=-1.0)
+    with pytest.raises(P.Rt3dError):
+        combine_histograms([(c, w, sc), (c, w, bad)])
+    with pytest.raises(ValueError):
+        combine_histograms([(c, w, sc), (c[:5], w[:5], sc)])
