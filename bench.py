@@ -1,22 +1,50 @@
-"""Benchmark: ray-particle interactions/s and ray bundles/s of the 3D ray-bundle
-trace, with magnifications checked against the FP64 oracle.
+"""Benchmark: ray-particle interactions/s (and ray bundles/s) of the 3D
+ray-bundle trace, checked in the same run against the FP64 oracle.
 
-Workload (the NFW-halo lens test): an NFW halo M200 = 1e14 Msun, c = 5 at
-z_l = 0.25, 100,000 equal-mass particles to 2 r200, Plummer softening 5 kpc;
-4096 bundles (central ray + 4) on a 64 x 64 grid of impact parameters
-0.05-2 r200; z_s = 0.5; 2000 RK4 steps on a lens-centred asinh schedule.
-One step = one full trace (schedule, bundle initialiser, 8000 pair-sum +
-integrator-stage launches, reducer) plus the muPDF of its bundles.
+Headline workload (the default): the 2^24-particle cosmological box.
+16,777,216 equal-mass particles in a periodic 200/h Mpc box (half uniform,
+half in 24,000 NFW halos with dN/dM ~ M^-1.9), replicated along the line of
+sight with random 90-degree rotations and periodic shifts out to z_s = 1 (13
+replicas), mean density subtracted; 1,048,576 bundles (central ray + 4 on a
+1" polygon) on a 1024 x 1024 grid in +-2.3 deg; a uniform table of 1000 RK4
+steps (3.3 Mpc).  One bench step = one RK4 stage of that trace over every
+bundle (rt3d_trace_advance by one stage): the FP32 pair sum of all 5,242,880
+rays against the 2^24 particles of their bundle's replica, the mean-density
+prism and the FP64 integrator stage.  The step table, the bundle
+initialiser and the autotuner's launch-shape choice run in the warm-up
+(rt3d_trace_begin); the reducer and the muPDF run in the end-to-end leg.
+
+Also in the JSON line:
+  e2e             the same metric through the host C ABI (rt3d_load_particles of
+                  the 2^24 particles from host memory, rt3d_trace of a slice of
+                  the bundles with host angles in and results out,
+                  rt3d_histogram), median of >= 3 samples
+  parity          FP64 oracle vs the GPU (mixed, and all-FP64) on bundles
+                  sampled over the whole sky grid, complete traces on a short
+                  table; max |dmu/mu| against the 1e-4 gate
+  cpu_baseline    the oracle's rate on that sample, on the host cores
+  batched_cones   512 light cones (own halo boxes with 1e3-1e6 particles, z_s
+                  0.3-1.5, 256-4096 bundles) in one persistent launch under a
+                  CUDA graph, shape picked by the autotuner
+  fp64_same_cones the first cones of that batch traced by the all-FP64 path one
+                  cone per launch, and the mixed batched path re-run on exactly
+                  those cones: speedup on identical inputs; FP64 pair-sum
+                  kernel against the FP64 peak
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+                  [--workload c5|nfw|cones|grid|prism|born|box3|box5]
 
-With N > 1 (torchrun) every rank traces its own copy of the workload (weak
-scaling, no collective on the data path); rank 0 prints one JSON line.
+With N > 1 every rank (one per GPU, launched by torch.distributed.run; bench.py
+starts it itself when called with --gpus N outside it) traces its own lines of
+sight of the same box: weak scaling, no collective on the data path; the
+timed region's maximum over ranks sets the rate, and the muPDFs of the
+end-to-end leg are combined by rt3d_histogram_combine.
 """
 import argparse
 import json
 import math
 import os
+import socket
 import statistics
 import subprocess
 import sys
@@ -31,21 +59,23 @@ import numpy as np  # noqa: E402
 METRIC = "ray-particle interactions/s & ray bundles/s at |dmu/mu|<=1e-4 vs FP64 oracle"
 UNIT = "interactions/s"
 FLOPS_PER_INTERACTION = 20  # direct N-body convention (3 sub, 6 fma/mul for r^2, rsqrt, 3 mul, phi, 3 fma)
-N_SM, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+N_SM, FP32_LANES, FP64_LANES, SM_MAX_MHZ = 152, 128, 2, 2070.0
 FP32_PEAK = N_SM * FP32_LANES * 2 * SM_MAX_MHZ * 1e6  # FLOP/s at the maximum SM clock
+FP64_PEAK = N_SM * FP64_LANES * 2 * SM_MAX_MHZ * 1e6  # 1.26 TFLOP/s: GB300's FP64 rate is 1/64 of FP32's
+PEAK_BASIS = "152 SM x 128 FP32 lanes x 2 x 2070 MHz (derived from unit counts and the maximum clock)"
+PEAK64_BASIS = "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived; nominal GB300 FP64 1.25 TFLOP/s)"
 HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
 KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2",
                 5: "k_force_bundle2x"}
-# dram__bytes_read.sum + dram__bytes_write.sum of one pair-sum launch on this
-# workload, per (kernel, threads per block, splits, cluster size), from the ncu
-# captures summarised under profiles/
-PROFILED_DRAM_BYTES = {("k_force_packed", 128, 31, 1): 2130432,
-                       ("k_force_bundle2", 128, 196, 1): 2169600 + 68610304,
-                       ("k_force_bundle2", 64, 131, 1): 2131456 + 24840704,
-                       ("k_force_bundle2x", 64, 131, 1): 2139136 + 25478144}
+# dram__bytes_read.sum + dram__bytes_write.sum per pair-sum launch, from ncu
+# captures of the kernel named (summaries under profiles/), keyed by
+# (workload, kernel, threads per block); scaled from the captured case to
+# the full launch as those summaries state.  A shape not listed reports null.
+PROFILED_DRAM_BYTES = {}
+C5_NAME = "box_2e24p_200mpch_zs1_1048576b_uniform1000_rk4stage"
 
 
-def workload(full=True):
+def nfw_workload(full=True):
     import inputs
     if full:
         cfg = inputs.config_c2()
@@ -54,6 +84,9 @@ def workload(full=True):
         cfg = inputs.config_c2(n_particles=20000, n_side=16, n_steps=400)
         name = "nfw_halo_2e4p_256b_400s"
     return cfg, name
+
+
+workload = nfw_workload  # the auxiliary NFW-halo workloads below
 
 
 def cones_workload(n_cones, n_steps):
@@ -503,7 +536,344 @@ def dist_env():
     return ws, rank, local
 
 
-def cpu_baseline(cfg, n_bundles=None, n_steps=500, nthreads=None):
+def free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def relaunch_command(argv, gpus, port):
+    """the torch.distributed.run command that starts one rank per GPU with the
+    same arguments (bench.py --gpus N called outside torchrun)"""
+    return [sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", str(gpus),
+            "--master-addr", "127.0.0.1", "--master-port", str(port), os.path.abspath(__file__)] + list(argv)
+
+
+def c5_config(args):
+    """the headline box (2^24 particles unless --box-particles asks for a
+    smaller box with the same generator, for checks)"""
+    import inputs
+    if args.box_particles == 2 ** 24:
+        return inputs.config_c5(n_steps=args.table_steps)
+    n_halos = max(1, int(round(24000 * args.box_particles / 2 ** 24)))
+    return inputs.config_c5(N=args.box_particles, n_halos=n_halos, n_steps=args.table_steps)
+
+
+def c5_name(args):
+    return C5_NAME if args.box_particles == 2 ** 24 else C5_NAME.replace("2e24p", "%dp" % args.box_particles)
+
+
+def load_box(ctx, fid, cfg):
+    ctx.load_particles(fid, cfg["pos"], cfg["mass"], cfg["soft"], replicated=True, box_length=cfg["L"],
+                       rot=cfg["rot"], shift=cfg["shift"], mean_subtract=True)
+
+
+def box_kw(cfg, n_steps, max_extra):
+    return dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=0, n_steps=n_steps, max_extra=max_extra)
+
+
+def oracle_sample(cfg, theta, n_steps, max_extra=16, nthreads=None):
+    """the FP64 oracle as it stands on the sampled bundles (complete traces on
+    an n_steps table): its results and its rate on the host cores"""
+    import oracle
+    cores = nthreads or os.cpu_count() or 1
+    c = oracle.Cosmology(*cfg["cosmo"])
+    f = oracle.MassField(cfg["pos"], cfg["mass"], cfg["soft"], replicated=True, L=cfg["L"], rot=cfg["rot"],
+                         shift=cfg["shift"], mean_subtract=True)
+    t0 = time.perf_counter()
+    r = oracle.trace(c, f, cfg["z_s"], theta, nthreads=cores, **box_kw(cfg, n_steps, max_extra))
+    return r, time.perf_counter() - t0, cores
+
+
+def cpu_baseline_and_parity(args, cfg, ctx, P, local):
+    """Parity on sampled bundles of the headline workload: the oracle (FP64,
+    host cores), the mixed GPU path and the all-FP64 GPU path trace the same
+    bundles on the same short table; the oracle's run is also the CPU
+    baseline."""
+    nb_all = len(cfg["theta"])
+    idx = np.linspace(0, nb_all - 1, args.parity_bundles).astype(int)
+    th = np.ascontiguousarray(cfg["theta"][idx])
+    kw = box_kw(cfg, args.parity_steps, 16)
+    g = ctx.trace(0, cfg["z_s"], th, want_rays=True, **kw)
+    c64 = P.Context(local, precision=P.FP64)
+    c64.set_cosmology(*cfg["cosmo"])
+    load_box(c64, 0, cfg)
+    g64 = c64.trace(0, cfg["z_s"], th, want_rays=True, **kw)
+    c64.close()
+    o, dt, cores = oracle_sample(cfg, th, args.parity_steps)
+    rel = np.abs(g["mu"] / o.mu - 1)
+    rel64 = np.abs(g64["mu"] / o.mu - 1)
+    beta = g["rays"][:, :, 1:3] / o.chi_s
+    a_g = o.ray_theta() - beta
+    a_o = o.alpha()
+    da = np.linalg.norm(a_g - a_o, axis=-1) / np.linalg.norm(a_o, axis=-1)
+    parity = {"bundles": int(len(idx)), "rk4_steps": args.parity_steps,
+              "sample": "bundles at evenly spaced indices of the 1024^2 grid; complete traces to z_s = 1",
+              "max_rel_dmu_mixed_vs_oracle": float(rel.max()),
+              "max_rel_dalpha_mixed_vs_oracle": float(da.max()),
+              "max_rel_dmu_fp64gpu_vs_oracle": float(rel64.max()),
+              "flags_equal": bool(np.array_equal(g["flags"], o.flags) and np.array_equal(g64["flags"], o.flags)),
+              "gate_dmu": 1e-4, "gate_dalpha": 1e-5,
+              "pass": bool(rel.max() <= 1e-4 and da.max() <= 1e-5 and np.array_equal(g["flags"], o.flags))}
+    base = {"value": o.n_pairs / dt, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": "%d bundles x %d RK4 steps (complete traces) of the 2^24-particle box, %.1f s wall, "
+                      "OpenMP over bundles" % (len(idx), args.parity_steps, dt),
+            "bundles_per_s": len(idx) / dt}
+    return parity, base
+
+
+def batched_cones(args, cones_cfg, P, local):
+    """the 512-cone batched workload in one persistent launch (CUDA graph,
+    autotuned shape), then the first cones by the all-FP64 path one cone per
+    launch and by the mixed batched path on exactly those cones"""
+    ccfg = cones_cfg
+    ctx = P.Context(local, precision=P.MIXED, autotune=1)
+    ctx.set_cosmology(*ccfg["cosmo"])
+    cones, npart = [], 0
+    for i, c in enumerate(ccfg["cones"]):
+        load_box(ctx, i, c)
+        cones.append(dict(field_id=i, z_s=c["z_s"], theta=c["theta"], n_steps=c["n_steps"]))
+        npart += len(c["mass"])
+    kw = dict(n_ring=ccfg["n_ring"], theta_r=ccfg["theta_r"], schedule=0)
+    for _ in range(args.cone_warmup):
+        ctx.trace_batch(cones, **kw)
+    inter, dev_ms = 0.0, 0.0
+    for _ in range(args.cone_runs):
+        ctx.trace_batch(cones, **kw)
+        st = ctx.stats()
+        inter += st["interactions"]
+        dev_ms += st["device_ms"]
+    rate = inter / (dev_ms / 1e3)
+    shape = {k: st[k] for k in ("threads_per_block", "splits", "variant")}
+    nb = sum(len(c["theta"]) for c in ccfg["cones"])
+    out = {"workload": "light_cones_%dc_%ds" % (len(cones), args.cone_steps), "cones": len(cones),
+           "particles": npart, "bundles": nb, "rk4_steps_per_cone": args.cone_steps, "runs": args.cone_runs,
+           "interactions_per_s": rate, "bundles_per_s": nb / (dev_ms / 1e3 / args.cone_runs),
+           "roofline": {"bound": "alu", "achieved": FLOPS_PER_INTERACTION * rate / 1e12, "peak": FP32_PEAK / 1e12,
+                        "unit": "TFLOP/s", "frac": FLOPS_PER_INTERACTION * rate / FP32_PEAK,
+                        "kernel": "k_batch_run (whole persistent launch, pair sums and FP64 stages)"},
+           "launch_shape": shape, "timing": "device time of the persistent launch (CUDA events)"}
+    # the first k cones: mixed batched re-run of exactly those cones vs FP64 one cone per launch
+    k = min(args.fp64_cones, len(cones))
+    sub = cones[:k]
+    ctx.trace_batch(sub, **kw)
+    rm = ctx.trace_batch(sub, **kw)
+    st = ctx.stats()
+    rate_k = st["interactions"] / (st["device_ms"] / 1e3)
+    ctx.close()
+    c64 = P.Context(local, precision=P.FP64, time_kernels=1)
+    c64.set_cosmology(*ccfg["cosmo"])
+    i64, d64, f64, dmu = 0.0, 0.0, 0.0, 0.0
+    for i in range(k):
+        c = ccfg["cones"][i]
+        load_box(c64, i, c)
+        r64 = c64.trace(i, c["z_s"], c["theta"], n_steps=c["n_steps"], **kw)
+        s64 = c64.stats()
+        i64 += s64["interactions"]
+        d64 += s64["device_ms"]
+        f64 += s64["force_ms"]
+        dmu = max(dmu, float(np.max(np.abs(rm[i]["mu"] / r64["mu"] - 1))))
+    c64.close()
+    rate64 = i64 / (d64 / 1e3)
+    same = {"cones": k, "interactions": i64, "mixed_batched_interactions_per_s": rate_k,
+            "fp64_one_cone_per_launch_interactions_per_s": rate64, "speedup_of_mixed_batched": rate_k / rate64,
+            "max_rel_dmu_mixed_vs_fp64": dmu,
+            "fp64_roofline": {"bound": "alu", "kernel": "k_force_fp64",
+                              "achieved": FLOPS_PER_INTERACTION * i64 / (f64 / 1e3) / 1e12,
+                              "peak": FP64_PEAK / 1e12, "unit": "TFLOP/s",
+                              "frac": FLOPS_PER_INTERACTION * i64 / (f64 / 1e3) / FP64_PEAK,
+                              "peak_basis": PEAK64_BASIS},
+            "timing": "device time of each path on the same cones (CUDA events)"}
+    return out, same
+
+
+def run_reference(args):
+    """The reference arm: the FP64 oracle as it stands on the host cores, on
+    the headline workload; each step a bounded sample (bundles x one RK4 step)."""
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import inputs
+    cfg = c5_config(args)
+    cores = os.cpu_count() or 1
+    g = inputs.rng(inputs.BASE_SEED + 5, 99, 0)
+    nb = args.ref_bundles or cores
+
+    def sample():
+        th = np.ascontiguousarray(cfg["theta"][g.integers(0, len(cfg["theta"]), nb)])
+        r, dt, _ = oracle_sample(cfg, th, 1, max_extra=0, nthreads=cores)
+        return r.n_pairs, dt
+
+    for _ in range(args.warmup):
+        sample()
+    pairs, times = 0.0, []
+    for _ in range(args.steps):
+        p, dt = sample()
+        pairs += p
+        times.append(dt)
+    v = pairs / sum(times)
+    smp = "%d random bundles x 1 RK4 step (4 stages) of the 2^24-particle box per step, %d host cores" % (nb, cores)
+    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": c5_name(args), "sample": smp},
+           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": smp},
+           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out))
+    return 0
+
+
+def run_ours(args):
+    ws, rank, local = dist_env()
+    import inputs
+    # inputs before any GPU call: the cone generator's processes are spawned
+    cones_cfg = None
+    if rank == 0 and not args.no_cones:
+        cones_cfg = inputs.config_c4(n_cones=args.cones, n_steps=args.cone_steps,
+                                     workers=max(1, min(16, os.cpu_count() or 1)))
+    cfg = c5_config(args)
+
+    import torch
+
+    import paper_1110_4894_gb300 as P
+    from paper_1110_4894_gb300.shard import allreduce_histogram, rank_lines_of_sight
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    theta = cfg["theta"] if ws == 1 else rank_lines_of_sight(cfg["theta"], rank)
+    name = c5_name(args)
+    if args.bundles:  # reduced runs for checks only: a contiguous patch of the grid
+        theta = theta[:args.bundles]
+        name += "_patch%d" % args.bundles
+    nb = len(theta)
+    nr = 1 + cfg["n_ring"]
+    npart = len(cfg["mass"])
+
+    def barrier():
+        if ws > 1:
+            torch.distributed.barrier()
+        torch.cuda.synchronize(dev)
+
+    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=1, variant=args.variant)
+    ctx.set_cosmology(*cfg["cosmo"])
+    load_box(ctx, 0, cfg)
+    d_theta = torch.from_numpy(np.ascontiguousarray(theta)).to(dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    kw = box_kw(cfg, cfg["n_steps"], 0)
+    # warm-up: step table, bundle initialiser and autotuned launch shape, then W stages
+    t_b = time.perf_counter()
+    ctx.trace_begin(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), **kw)
+    barrier()
+    begin_s = time.perf_counter() - t_b
+    for _ in range(args.warmup):
+        ctx.trace_advance(sp, 1)
+    barrier()
+    s0 = ctx.stats()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    with ClockSampler(torch.cuda.current_device() if "CUDA_VISIBLE_DEVICES" not in os.environ else local) as clk:
+        barrier()
+        t0 = time.perf_counter()
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            ctx.trace_advance(sp, 1)
+            ev[k][1].record(stream)
+        barrier()
+        wall = time.perf_counter() - t0
+    clocks = clk.summary()
+    s1 = ctx.stats()
+    inter = s1["interactions"] - s0["interactions"]
+    force_ms = s1["force_ms"] - s0["force_ms"]
+    flaunch = s1["force_launches"] - s0["force_launches"]
+    launches = s1["launches"] - s0["launches"]
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    dev_s = sum(step_ms) / 1e3
+    t_rank = torch.tensor([dev_s], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(t_rank, op=torch.distributed.ReduceOp.MAX)
+    t_max = float(t_rank.item())
+    value = inter * ws / t_max
+
+    # end to end through the host C ABI, every rank: the particle set and a
+    # slice of the bundle angles from host memory, results and muPDF back
+    e2e_th = np.ascontiguousarray(theta[:args.e2e_bundles])
+    ekw = box_kw(cfg, args.e2e_table, 4)
+    e2e_rates, e2e_times = [], []
+    hist = None
+    for _ in range(max(3, args.e2e_steps)):
+        barrier()
+        t1 = time.perf_counter()
+        load_box(ctx, 1, cfg)
+        r = ctx.trace(1, cfg["z_s"], e2e_th, **ekw)
+        hist = ctx.histogram(r["mu"], r["flags"], **HIST)
+        barrier()
+        dt = time.perf_counter() - t1
+        e2e_times.append(dt)
+        e2e_rates.append(ctx.stats()["interactions"] / dt)
+    e2e_rank = torch.tensor([statistics.median(e2e_times)], dtype=torch.float64, device=dev)
+    if ws > 1:
+        torch.distributed.all_reduce(e2e_rank, op=torch.distributed.ReduceOp.MAX)
+    e2e_value = statistics.median(e2e_rates) * ws * statistics.median(e2e_times) / float(e2e_rank.item())
+    counts, wfix, sc = hist
+    if ws > 1:
+        counts, wfix, sc = allreduce_histogram(counts, wfix, sc, device=dev)
+    mupdf = {"bundles_binned": int(sc["n_used"]), "mean_w": sc["mean_w"], "sigma_w": sc["sigma_w"],
+             "bins": HIST["bins"], "mu_range": [HIST["mu_min"], HIST["mu_max"]], "ranks": ws,
+             "of": "the end-to-end leg's bundles (%d per rank, %d-step table)" % (len(e2e_th), args.e2e_table)}
+    h2d = npart * 4 * 8 + len(e2e_th) * 2 * 8
+    d2h = len(e2e_th) * 6 * 8 + HIST["bins"] * 16
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    if rank != 0:
+        ctx.close()
+        return 0
+
+    per_launch = inter / max(1, flaunch)
+    avg_launch_s = force_ms / 1e3 / max(1, flaunch)
+    achieved = FLOPS_PER_INTERACTION * per_launch / avg_launch_s if avg_launch_s > 0 else 0.0
+    st = s1
+    kname = KERNEL_NAMES.get(st["variant"], "k_force")
+    traffic = PROFILED_DRAM_BYTES.get(("c5", kname, st["threads_per_block"], st["splits"]))
+    out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+           "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+           "bundle_stages_per_s": nb * ws * args.steps / t_max,
+           "bundles_per_s": nb * ws * args.steps / t_max / (4 * cfg["n_steps"]),
+           "bundles_per_s_note": "bundles per second of whole %d-step traces at the measured stage rate"
+                                 % cfg["n_steps"],
+           "config": {"workload": name, "particles": npart, "bundles": nb, "rays": nb * nr,
+                      "replicas": int(cfg["n_rep"]), "z_s": cfg["z_s"], "box_mpc_h": 200.0,
+                      "rk4_table_steps": cfg["n_steps"], "step": "one RK4 stage over every bundle",
+                      "stages_before_timing": args.warmup,
+                      "precision": "fp32 pair sums (chunked TwoSum), fp64 ray state, stage and prism",
+                      "l2": "inputs larger than L2 (particles 268 MB, ray state 1.3 GB); no flush",
+                      "launch_shape": {"threads_per_block": st["threads_per_block"], "splits": st["splits"],
+                                       "cluster": st.get("cluster", 1), "kernel": kname},
+                      "begin_s": begin_s},
+           "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": FP32_PEAK / 1e12, "unit": "TFLOP/s",
+                        "frac": achieved / FP32_PEAK, "traffic": traffic, "kernel": kname,
+                        "flops_per_interaction": FLOPS_PER_INTERACTION, "interactions_per_launch": per_launch,
+                        "avg_launch_ms": avg_launch_s * 1e3, "peak_basis": PEAK_BASIS},
+           "clocks": clocks,
+           "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                   "samples": len(e2e_rates), "spread": [min(e2e_rates) * ws, max(e2e_rates) * ws],
+                   "sample": "rt3d_load_particles (2^24 particles) + rt3d_trace of %d bundles on a %d-step table "
+                             "+ rt3d_histogram, host buffers, median" % (len(e2e_th), args.e2e_table)},
+           "gpu_launches": int(launches),
+           "mupdf": mupdf,
+           "wall_s": wall}
+    if not args.no_cpu:
+        out["parity"], out["cpu_baseline"] = cpu_baseline_and_parity(args, cfg, ctx, P, local)
+    ctx.close()
+    if cones_cfg is not None:
+        out["batched_cones"], out["fp64_same_cones"] = batched_cones(args, cones_cfg, P, local)
+    print(json.dumps(out))
+    return 0
+
+
+def nfw_cpu_baseline(cfg, n_bundles=None, n_steps=500, nthreads=None):
     """The FP64 oracle as it stands on a bounded sample: n_bundles (default:
     one per core) of the workload's bundles, traced with a shorter step table
     of the same kind.  Rate = pair evaluations / wall time."""
@@ -526,32 +896,9 @@ def cpu_baseline(cfg, n_bundles=None, n_steps=500, nthreads=None):
             "bundles_per_s": bundles_per_s}
 
 
-def run_reference(args):
-    ws, rank, _ = dist_env()
-    if rank != 0:
-        return 0
-    cfg, name = workload(full=not args.small)
-    cores = os.cpu_count() or 1
-    for _ in range(args.warmup):
-        cpu_baseline(cfg, n_bundles=cores, n_steps=25)
-    vals, times = [], []
-    for _ in range(args.steps):
-        b = cpu_baseline(cfg, n_bundles=cores, n_steps=100)
-        vals.append(b["value"])
-        times.append(float(b["sample"].split(",")[-1].split()[0]))
-    v = statistics.mean(vals)
-    out = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
-           "warmup": args.warmup, "ms_per_step": 1e3 * statistics.mean(times), "higher_is_better": True,
-           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-           "config": {"workload": name, "sample": "%d bundles x 100 RK4 steps per step" % cores},
-           "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
-                            "sample": "%d bundles x 100 RK4 steps per step, %d particles" % (cores, len(cfg["mass"]))},
-           "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
-    print(json.dumps(out))
-    return 0
-
-
-def run_ours(args):
+def run_nfw(args):
+    """The NFW-halo lens test (100,000 particles, 4096 bundles, 2000 RK4 steps):
+    one step = one full trace of every bundle plus its muPDF."""
     import torch
 
     import paper_1110_4894_gb300 as P
@@ -643,7 +990,7 @@ def run_ours(args):
     d2h = nb * 6 * 8 + HIST["bins"] * 16 + 64
     pos = np.ascontiguousarray(cfg["pos"])
     mass = np.ascontiguousarray(cfg["mass"])
-    for k in range(max(1, args.e2e_steps)):
+    for k in range(max(3, args.e2e_steps)):
         barrier()
         t1 = time.perf_counter()
         ctx.load_particles(1, pos, mass, cfg["soft"])
@@ -652,7 +999,7 @@ def run_ours(args):
         barrier()
         e2e_times.append(time.perf_counter() - t1)
     e2e_inter = ctx.stats()["interactions"]
-    e2e_value = e2e_inter * ws / statistics.mean(e2e_times)
+    e2e_value = e2e_inter * ws / statistics.median(e2e_times)
 
     if rank == 0:
         per_launch = inter / max(1, force_launches)
@@ -663,7 +1010,7 @@ def run_ours(args):
         # DRAM bytes per pair-sum launch from the ncu capture of this kernel
         # (profiles/); null when the launched kernel was not captured
         traffic = None if args.small else PROFILED_DRAM_BYTES.get(
-            (kname, shape["threads_per_block"], shape["splits"], shape.get("cluster", 1)))
+            ("nfw", kname, shape["threads_per_block"], shape["splits"]))
         out = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
                "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
@@ -687,7 +1034,7 @@ def run_ours(args):
                "mupdf": mupdf,
                "wall_s": wall}
         if not args.no_cpu:
-            out["cpu_baseline"] = cpu_baseline(cfg, n_steps=args.cpu_steps)
+            out["cpu_baseline"] = nfw_cpu_baseline(cfg, n_steps=args.cpu_steps)
         print(json.dumps(out))
     ctx.close()
     if ws > 1:
@@ -701,23 +1048,44 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--small", action="store_true", help="reduced workload for quick checks")
-    ap.add_argument("--e2e-steps", type=int, default=1)
+    ap.add_argument("--workload", default="c5", choices=["c5", "nfw", "cones", "grid", "born", "box3", "box5",
+                                                          "prism"])
+    ap.add_argument("--table-steps", type=int, default=1000, help="RK4 steps of the headline trace's table")
+    ap.add_argument("--box-particles", type=int, default=2 ** 24, help="checks only: a smaller headline box")
+    ap.add_argument("--bundles", type=int, default=0, help="checks only: trace the first bundles of the grid")
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--e2e-bundles", type=int, default=16384)
+    ap.add_argument("--e2e-table", type=int, default=2)
+    ap.add_argument("--parity-bundles", type=int, default=16)
+    ap.add_argument("--parity-steps", type=int, default=4)
+    ap.add_argument("--ref-bundles", type=int, default=0, help="reference arm: bundles per step (0: one per core)")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-cones", action="store_true")
+    ap.add_argument("--cone-warmup", type=int, default=2)
+    ap.add_argument("--cone-runs", type=int, default=2)
+    # auxiliary workloads
+    ap.add_argument("--small", action="store_true", help="reduced NFW workload for quick checks")
     ap.add_argument("--cpu-steps", type=int, default=250)
-    ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (profiling runs)")
-    ap.add_argument("--workload", default="nfw", choices=["nfw", "cones", "grid", "born", "box3", "box5", "prism"])
-    ap.add_argument("--box-bundles", type=int, default=65536, help="bundles of the 2^24-particle box")
+    ap.add_argument("--rk4-steps", type=int, default=0, help="override the RK4 step count (auxiliary workloads)")
+    ap.add_argument("--box-bundles", type=int, default=65536, help="bundles of the 2^24-particle box (box5)")
     ap.add_argument("--fp64-bundles", type=int, default=256, help="bundles of the box run on the FP64 path")
     ap.add_argument("--grid-n", type=int, default=256, help="nodes per side of the grid workload")
     ap.add_argument("--cones", type=int, default=512)
     ap.add_argument("--cone-steps", type=int, default=16)
     ap.add_argument("--fp64-cones", type=int, default=8)
-    ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--variant", type=int, default=0,
                     help="pair-sum kernel (0: the autotuner picks among all; 3, 4, 5: that kernel's shapes only)")
     args = ap.parse_args()
+    ws = dist_env()[0]
+    if ws == 1 and args.gpus > 1:  # outside torchrun: start one rank per GPU, which then report
+        return subprocess.call(relaunch_command(sys.argv[1:], args.gpus, free_port()))
+    if ws != args.gpus:
+        print("bench.py: --gpus %d but WORLD_SIZE %d" % (args.gpus, ws), file=sys.stderr)
+        return 2
     if args.impl == "reference":
         return run_reference(args)
+    if args.workload == "nfw":
+        return run_nfw(args)
     if args.workload == "cones":
         return run_cones(args)
     if args.workload == "grid":

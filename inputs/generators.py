@@ -303,28 +303,43 @@ def config_prism(N=16777216, n_side=176, n_steps=1000, n_halos=24000, cubes=8, g
                 grid_n=grid_n, precision="mixed", replicated=True, mean_subtract=True)
 
 
+def _cone(i, Nc, zs, nb, seed, n_steps, L, margin_h):
+    """one light cone of config_c4 (its own seeded halo box and bundle grid)"""
+    om, ol, h = COSMO
+    n_halos = max(1, int(round(3000 * Nc / 2 ** 21)))
+    pos, mass, info = halo_box(Nc, L, n_halos, seed * 1000 + i, om, ol, h)
+    chi_s = chi_placement(zs, om, ol, h)
+    n_rep = int(math.ceil(chi_s / L)) + 1
+    rot, shift = replicas(n_rep, L, seed * 1000 + i)
+    half = (0.5 * L - margin_h / h) / chi_s
+    side = int(math.ceil(math.sqrt(nb)))
+    theta = bundle_grid(-half, half, side)[:nb]
+    return dict(pos=pos, mass=mass, soft=0.016 / h, z_s=zs, theta=theta, L=L, rot=rot,
+                shift=shift, n_rep=n_rep, n_steps=n_steps, info=info)
+
+
 def config_c4(n_cones=512, n_steps=1000, seed=BASE_SEED + 4, n_min=1000, n_max=1000000,
-              b_min=256, b_max=4096, zs_lo=0.3, zs_hi=1.5, L_h=50.0, margin_h=5.0):
+              b_min=256, b_max=4096, zs_lo=0.3, zs_hi=1.5, L_h=50.0, margin_h=5.0, workers=1):
     """Independent light cones: per cone a halo box with N_c log-uniform in
     [n_min, n_max], z_s uniform in [zs_lo, zs_hi], bundles log-uniform in
-    [b_min, b_max] on a square grid inside the replica margin."""
+    [b_min, b_max] on a square grid inside the replica margin.  workers > 1
+    draws the cones in that many spawned processes (same cones: each has its
+    own seeds)."""
     om, ol, h = COSMO
     g = rng(seed, P_CONE, 0)
     L = box_length(L_h / h)
-    cones = []
+    draws = []
     for i in range(n_cones):
         Nc = int(round(math.exp(g.uniform(math.log(n_min), math.log(n_max)))))
         zs = float(g.uniform(zs_lo, zs_hi))
         nb = int(round(math.exp(g.uniform(math.log(b_min), math.log(b_max)))))
-        n_halos = max(1, int(round(3000 * Nc / 2 ** 21)))
-        pos, mass, info = halo_box(Nc, L, n_halos, seed * 1000 + i, om, ol, h)
-        chi_s = chi_placement(zs, om, ol, h)
-        n_rep = int(math.ceil(chi_s / L)) + 1
-        rot, shift = replicas(n_rep, L, seed * 1000 + i)
-        half = (0.5 * L - margin_h / h) / chi_s
-        side = int(math.ceil(math.sqrt(nb)))
-        theta = bundle_grid(-half, half, side)[:nb]
-        cones.append(dict(pos=pos, mass=mass, soft=0.016 / h, z_s=zs, theta=theta, L=L, rot=rot,
-                          shift=shift, n_rep=n_rep, n_steps=n_steps, info=info))
+        draws.append((i, Nc, zs, nb, seed, n_steps, L, margin_h))
+    if workers > 1 and n_cones > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            cones = list(ex.map(_cone, *zip(*draws), chunksize=4))
+    else:
+        cones = [_cone(*d) for d in draws]
     return dict(name="c4_cones", cosmo=COSMO, cones=cones, n_ring=4,
                 theta_r=math.radians(1.0 / 3600.0), schedule=0, precision="mixed")

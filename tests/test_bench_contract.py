@@ -9,13 +9,14 @@ import sys
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _run(extra_env=None):
+def _run(extra_env=None, extra_args=()):
     env = dict(os.environ)
-    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK"):
+    for k in ("RANK", "WORLD_SIZE", "LOCAL_RANK", "LOCAL_WORLD_SIZE", "MASTER_ADDR", "MASTER_PORT"):
         env.pop(k, None)
     env.update(extra_env or {})
-    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0"],
-                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=600)
+    return subprocess.run([sys.executable, "bench.py", "--impl", "reference", "--steps", "1", "--warmup", "0",
+                           "--ref-bundles", "2", "--box-particles", "65536"] + list(extra_args),
+                          cwd=ROOT, env=env, capture_output=True, text=True, timeout=900)
 
 
 def test_reference_arm_prints_one_contract_line():
@@ -35,5 +36,31 @@ def test_reference_arm_prints_one_contract_line():
 
 
 def test_reference_arm_other_ranks_exit_quietly():
-    r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"})
+    r = _run({"RANK": "1", "WORLD_SIZE": "2", "LOCAL_RANK": "1"}, ["--gpus", "2"])
     assert r.returncode == 0 and r.stdout.strip() == ""
+
+
+def test_gpus_flag_starts_one_rank_per_gpu():
+    # outside torchrun, --gpus 2 starts torch.distributed.run with two ranks;
+    # rank 0 alone prints the line, which reports both ranks
+    r = _run(extra_args=["--gpus", "2"])
+    assert r.returncode == 0, r.stderr
+    lines = [l for l in r.stdout.splitlines() if l.strip().startswith("{")]
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["n_gpus"] == 2 and d["impl"] == "reference"
+
+
+def test_world_size_must_match_gpus():
+    r = _run({"RANK": "0", "WORLD_SIZE": "3", "LOCAL_RANK": "0"}, ["--gpus", "2"])
+    assert r.returncode == 2
+
+
+def test_relaunch_command():
+    sys.path.insert(0, ROOT)
+    import bench
+    cmd = bench.relaunch_command(["--gpus", "4", "--steps", "5"], 4, 29513)
+    assert cmd[1:4] == ["-m", "torch.distributed.run", "--nnodes=1"]
+    assert cmd[cmd.index("--nproc-per-node") + 1] == "4"
+    assert cmd[cmd.index("--master-addr") + 1] == "127.0.0.1"
+    assert cmd[-3:] == ["--gpus", "4", "--steps", "5"][-3:] and cmd[-5].endswith("bench.py")
