@@ -72,6 +72,10 @@ class HistOpts(C.Structure):
     _fields_ = [("bins", C.c_int), ("mu_min", C.c_double), ("mu_max", C.c_double)]
 
 
+class MPOpts(C.Structure):
+    _fields_ = [("n_ring", C.c_int), ("theta_r", C.c_double), ("phase", C.c_double), ("slices", C.c_int)]
+
+
 F_NOCROSS, F_NONFINITE, F_NEGPARITY = 1, 2, 4
 
 _dp = C.POINTER(C.c_double)
@@ -123,6 +127,11 @@ def lib():
         L.orc_grid_y2.restype = None
         L.orc_grid_eval.argtypes = [C.POINTER(Grid), _dp, _dp]
         L.orc_grid_eval.restype = None
+        L.orc_rect_deflection.argtypes = [_dp, _dp, _dp, _dp]
+        L.orc_rect_deflection.restype = None
+        L.orc_multiplane.argtypes = [pc, C.POINTER(Field), C.c_double, C.c_int64, _dp, C.POINTER(MPOpts), _dp, _dp,
+                                     _dp, C.POINTER(C.c_int), _dp, C.c_int]
+        L.orc_multiplane.restype = C.c_int
         _lib = L
     return _lib
 
@@ -349,3 +358,72 @@ def replica_world(field, j):
     out = np.zeros((field.pos.shape[0], 3))
     lib().orc_replica_world(C.byref(field.f), int(j), _p(out))
     return out
+
+
+def rect_deflection(lo, hi, x):
+    """int over the rectangle [lo, hi] of (x - x') / |x - x'|^2 d^2x' (unit
+    surface density), at the points x (n, 2)"""
+    lo, hi = (np.ascontiguousarray(v, np.float64) for v in (lo, hi))
+    x = np.ascontiguousarray(x, np.float64).reshape(-1, 2)
+    out = np.zeros_like(x)
+    for i in range(x.shape[0]):
+        xi = np.ascontiguousarray(x[i])
+        o = np.zeros(2)
+        lib().orc_rect_deflection(_p(lo), _p(hi), _p(xi), _p(o))
+        out[i] = o
+    return out
+
+
+class MultiPlaneResult:
+    def __init__(self, xs, bundles, planes, n_pairs, chi_s, theta, n_ring, theta_r, phase):
+        self.xs = xs              # (n_b, nr, 2) comoving source-plane positions
+        self.bundles = bundles    # (n_b, 6) mu, kappa, gamma1, gamma2, omega, flags
+        self.planes = planes      # (n_planes, 4) chi, z, particles, slab thickness
+        self.n_pairs = n_pairs
+        self.chi_s = chi_s
+        self.theta = theta
+        self.n_ring, self.theta_r, self.phase = n_ring, theta_r, phase
+
+    mu = property(lambda self: self.bundles[:, 0])
+    kappa = property(lambda self: self.bundles[:, 1])
+    gamma1 = property(lambda self: self.bundles[:, 2])
+    gamma2 = property(lambda self: self.bundles[:, 3])
+    omega = property(lambda self: self.bundles[:, 4])
+    flags = property(lambda self: self.bundles[:, 5].astype(np.int32))
+
+    def beta(self):
+        return self.xs / self.chi_s
+
+    def ray_theta(self):
+        nr = 1 + self.n_ring
+        th = np.zeros((self.theta.shape[0], nr, 2))
+        th[:, 0] = self.theta
+        for k in range(1, nr):
+            ang = self.phase + 2.0 * np.pi * (k - 1) / self.n_ring
+            th[:, k, 0] = self.theta[:, 0] + self.theta_r * np.cos(ang)
+            th[:, k, 1] = self.theta[:, 1] + self.theta_r * np.sin(ang)
+        return th
+
+    def alpha(self):
+        return self.ray_theta() - self.beta()
+
+
+def multiplane(cosmo, field, z_s, theta, n_ring=4, theta_r=1e-6, phase=0.0, slices=1, nthreads=None):
+    """the multiple lens-plane comparison system (Sec. 3.1): bundles traced
+    through the field's projected slabs (see orc.c for the readings)"""
+    theta = np.ascontiguousarray(theta, np.float64).reshape(-1, 2)
+    n_b = theta.shape[0]
+    nr = 1 + n_ring
+    xs = np.zeros((n_b, nr, 2))
+    bundles = np.zeros((n_b, 6))
+    cap = (field.n_rep if field.replicated else 1) * slices
+    planes = np.zeros((max(cap, 1), 4))
+    npl = C.c_int(0)
+    pairs = C.c_double(0.0)
+    o = MPOpts(int(n_ring), float(theta_r), float(phase), int(slices))
+    rc = lib().orc_multiplane(C.byref(cosmo.c), C.byref(field.f), float(z_s), n_b, _p(theta), C.byref(o), _p(xs),
+                              _p(bundles), _p(planes), C.byref(npl), C.byref(pairs), nthreads or default_threads())
+    if rc != 0:
+        raise ValueError("orc_multiplane failed: %d" % rc)
+    return MultiPlaneResult(xs, bundles, planes[:npl.value].copy(), pairs.value, cosmo.chi(z_s), theta, n_ring,
+                            theta_r, phase)

@@ -876,3 +876,235 @@ int orc_born(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b, co
     free(x); free(dl); free(wt);
     return 0;
 }
+
+/* ------------------------------------------------------------------------ */
+/* multiple lens-plane comparison system (Sec. 3.1 "Multiple lens plane     */
+/* methods"; Eqs. defangleB, lenseqn, defangle): the mass between observer  */
+/* and source is cut into slabs along x3, each slab projected onto a plane  */
+/* at its centre; a ray travels straight between planes and is deflected    */
+/* only at them, by the matter of that plane.                               */
+/* READING (planes): replicated fields: replica j's range [jL, (j+1)L) in  */
+/* `slices` slabs of equal thickness, each cut at the source plane x3 =     */
+/* chi_s; isolated fields: the particles' x3 range in `slices` slabs (one   */
+/* particle, or slices = 1 with all particles at one x3: one plane there).  */
+/* Particles beyond the source plane or behind the observer are left out.   */
+/* READING (deflection): the projected Plummer particle deflects by the     */
+/* thin-lens angle of Eq. defangleB for its Plummer-sphere surface density: */
+/*   alpha_hat(x) = 4 mu_G (1 + z_k) sum_p m_p (x - x_p)/(|x - x_p|^2 + e_p^2) */
+/* in comoving transverse coordinates (x = (1 + z_k) xi), which makes the  */
+/* recursion below the multi-plane lens equation of Sec. 3.1 in a flat     */
+/* universe (D_ij = (chi_j - chi_i) / (1 + z_j)).                            */
+/* READING (mean): mean-subtracted boxes also remove the deflection of the  */
+/* slab's uniform mean surface density rho_bar * thickness over the square  */
+/* |x1|, |x2| < L/2 (the 2D analogue of the 3D path's prism).                */
+/* READING (propagation): tangent-plane slopes as in the 3D trace's initial */
+/* conditions; x(chi) = x_k + (chi - chi_k) theta between planes and        */
+/* theta -> theta - alpha_hat at plane k (small angles).                    */
+/* ------------------------------------------------------------------------ */
+/* g(u, v) = u atan(v/u) + (v/2) ln(u^2 + v^2): d^2 g / du dv = u / (u^2 + v^2) */
+static double rect_g(double u, double v)
+{
+    double q = u * u + v * v;
+    if (q == 0.0) return 0.0;
+    double a = u != 0.0 ? u * atan(v / u) : 0.0;
+    return a + 0.5 * v * log(q);
+}
+
+void orc_rect_deflection(const double lo[2], const double hi[2], const double x[2], double out[2])
+{
+    /* int over [lo, hi] of (x - x') / |x - x'|^2 d^2x', with u = x - x' */
+    double u1 = x[0] - lo[0], u0 = x[0] - hi[0];
+    double v1 = x[1] - lo[1], v0 = x[1] - hi[1];
+    out[0] = rect_g(u1, v1) - rect_g(u0, v1) - rect_g(u1, v0) + rect_g(u0, v0);
+    out[1] = rect_g(v1, u1) - rect_g(v1, u0) - rect_g(v0, u1) + rect_g(v0, u0);
+}
+
+typedef struct {
+    double chi, z, lo, hi;  /* plane position, its redshift, slab [lo, hi) */
+    int rep;                /* replica (replicated fields) */
+    int64_t n;              /* particles on the plane */
+    double *x;              /* n*2 transverse positions */
+    double *m, *e2;         /* n masses, n softening^2 */
+} mp_plane;
+
+static void mp_free(mp_plane *pl, int np)
+{
+    for (int k = 0; k < np; ++k) {
+        free(pl[k].x);
+        free(pl[k].m);
+        free(pl[k].e2);
+    }
+    free(pl);
+}
+
+/* the planes of field f up to chi_s (see the readings above); returns the
+ * count, or -1 on a bad option, -2 on allocation failure */
+static int mp_planes(const orc_cosmo *c, const orc_field *f, double chi_s, int slices, mp_plane **out)
+{
+    *out = NULL;
+    if (slices < 1 || f->grid) return -1;
+    int nrep = f->replicated ? f->n_rep : 1;
+    int np = nrep * slices;
+    mp_plane *pl = (mp_plane *)calloc((size_t)np, sizeof(mp_plane));
+    if (!pl) return -2;
+    double xlo = 0.0, xhi = 0.0;
+    if (!f->replicated && f->n > 0) {
+        xlo = xhi = f->pos[2];
+        for (int64_t i = 1; i < f->n; ++i) {
+            if (f->pos[3 * i + 2] < xlo) xlo = f->pos[3 * i + 2];
+            if (f->pos[3 * i + 2] > xhi) xhi = f->pos[3 * i + 2];
+        }
+    }
+    double *w = (double *)malloc(sizeof(double) * 3 * (size_t)(f->n > 0 ? f->n : 1));
+    int64_t *cnt = (int64_t *)calloc((size_t)slices, sizeof(int64_t));
+    if (!w || !cnt) { free(w); free(cnt); mp_free(pl, np); return -2; }
+    int used = 0;
+    for (int j = 0; j < nrep; ++j) {
+        double a, b;
+        if (f->replicated) {
+            replica_world(f, j, w);
+            a = (double)j * f->L;
+            b = a + f->L;
+        } else {
+            memcpy(w, f->pos, sizeof(double) * 3 * (size_t)f->n);
+            a = xlo;
+            b = xhi;
+        }
+        double d = (b - a) / (double)slices;
+        /* slab of each particle; -1: outside [0, chi_s) or the replica */
+        memset(cnt, 0, sizeof(int64_t) * (size_t)slices);
+        for (int64_t i = 0; i < f->n; ++i) {
+            double x3 = w[3 * i + 2];
+            int s = d > 0.0 ? (int)floor((x3 - a) / d) : 0;
+            if (s >= slices) s = slices - 1;  /* the particle at the far end of an isolated range */
+            if (s < 0 || x3 < 0.0 || x3 >= chi_s || (f->replicated && (x3 < a || x3 >= b))) continue;
+            cnt[s]++;
+        }
+        for (int s = 0; s < slices; ++s) {
+            double lo = d > 0.0 ? a + d * (double)s : a, hi = d > 0.0 ? a + d * (double)(s + 1) : a;
+            if (hi > chi_s) hi = chi_s;
+            if (lo < 0.0) lo = 0.0;
+            if (f->replicated ? !(hi > lo) : (cnt[s] == 0)) continue;
+            mp_plane *p = pl + used++;
+            p->lo = lo;
+            p->hi = hi;
+            p->chi = 0.5 * (lo + hi);
+            p->z = orc_z_of_chi(c, p->chi);
+            p->rep = j;
+            p->n = 0;
+            p->x = (double *)malloc(sizeof(double) * 2 * (size_t)(cnt[s] > 0 ? cnt[s] : 1));
+            p->m = (double *)malloc(sizeof(double) * (size_t)(cnt[s] > 0 ? cnt[s] : 1));
+            p->e2 = (double *)malloc(sizeof(double) * (size_t)(cnt[s] > 0 ? cnt[s] : 1));
+            if (!p->x || !p->m || !p->e2) { free(w); free(cnt); mp_free(pl, np); return -2; }
+            for (int64_t i = 0; i < f->n; ++i) {
+                double x3 = w[3 * i + 2];
+                int s2 = d > 0.0 ? (int)floor((x3 - a) / d) : 0;
+                if (s2 >= slices) s2 = slices - 1;
+                if (s2 != s || x3 < 0.0 || x3 >= chi_s || (f->replicated && (x3 < a || x3 >= b))) continue;
+                double e = f->soft ? f->soft[i] : f->soft_scalar;
+                p->x[2 * p->n] = w[3 * i];
+                p->x[2 * p->n + 1] = w[3 * i + 1];
+                p->m[p->n] = f->mass[i];
+                p->e2[p->n] = e * e;
+                p->n++;
+            }
+        }
+    }
+    free(w);
+    free(cnt);
+    /* planes in order of distance (isolated slabs and replicas already are) */
+    *out = pl;
+    return used;
+}
+
+int orc_multiplane(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b, const double *theta,
+                   const orc_mp_opts *o, double *ray_out, double *bundle_out, double *planes_out,
+                   int *n_planes, double *n_pairs, int nthreads)
+{
+    if (o->n_ring < 3 || o->n_ring > 8 || !(z_s > 0.0) || o->slices < 1) return -1;
+    const int nr = 1 + o->n_ring;
+    const double chi_s = orc_chi(c, z_s);
+    mp_plane *pl = NULL;
+    int np = mp_planes(c, f, chi_s, o->slices, &pl);
+    if (np < 0) return np;
+    double rho_bar = 0.0;
+    if (f->replicated && f->mean_subtract) {
+        nsum mt = {0, 0};
+        for (int64_t i = 0; i < f->n; ++i) nadd(&mt, f->mass[i]);
+        rho_bar = nval(mt) / (f->L * f->L * f->L);
+    }
+    const double mu4 = 4.0 * orc_mu_G();
+    double total = 0.0;
+#pragma omp parallel for schedule(dynamic, 1) num_threads(nthreads > 0 ? nthreads : 1) reduction(+ : total)
+    for (int64_t b = 0; b < n_b; ++b) {
+        double th[9][2], x[9][2], xs[18], dth[16];
+        th[0][0] = theta[2 * b];
+        th[0][1] = theta[2 * b + 1];
+        for (int k = 1; k < nr; ++k) {
+            double ang = o->phase + 2.0 * M_PI * (double)(k - 1) / (double)o->n_ring;
+            th[k][0] = th[0][0] + o->theta_r * cos(ang);
+            th[k][1] = th[0][1] + o->theta_r * sin(ang);
+        }
+        for (int k = 1; k < nr; ++k) {
+            dth[2 * (k - 1)] = th[k][0] - th[0][0];
+            dth[2 * (k - 1) + 1] = th[k][1] - th[0][1];
+        }
+        for (int k = 0; k < nr; ++k) {
+            double t[2] = {th[k][0], th[k][1]}, chi = 0.0;
+            x[k][0] = x[k][1] = 0.0;
+            for (int q = 0; q < np; ++q) {
+                const mp_plane *p = pl + q;
+                x[k][0] += (p->chi - chi) * t[0];
+                x[k][1] += (p->chi - chi) * t[1];
+                chi = p->chi;
+                nsum ax = {0, 0}, ay = {0, 0};
+                for (int64_t i = 0; i < p->n; ++i) {
+                    double dx = x[k][0] - p->x[2 * i], dy = x[k][1] - p->x[2 * i + 1];
+                    double w = p->m[i] / (dx * dx + dy * dy + p->e2[i]);
+                    nadd(&ax, w * dx);
+                    nadd(&ay, w * dy);
+                }
+                total += (double)p->n;
+                double a[2] = {nval(ax), nval(ay)};
+                if (rho_bar > 0.0) {
+                    double sig = rho_bar * (p->hi - p->lo);
+                    double lo[2] = {-0.5 * f->L, -0.5 * f->L}, hi[2] = {0.5 * f->L, 0.5 * f->L}, r[2];
+                    orc_rect_deflection(lo, hi, x[k], r);
+                    a[0] -= sig * r[0];
+                    a[1] -= sig * r[1];
+                }
+                double g = mu4 * (1.0 + p->z);
+                t[0] -= g * a[0];
+                t[1] -= g * a[1];
+            }
+            x[k][0] += (chi_s - chi) * t[0];
+            x[k][1] += (chi_s - chi) * t[1];
+            xs[2 * k] = x[k][0];
+            xs[2 * k + 1] = x[k][1];
+            if (ray_out) {
+                ray_out[((size_t)b * nr + k) * 2] = x[k][0];
+                ray_out[((size_t)b * nr + k) * 2 + 1] = x[k][1];
+            }
+        }
+        double J[6];
+        orc_bundle_jacobian(o->n_ring, th[0], dth, xs, chi_s, J);
+        int flags = 0;
+        for (int q = 0; q < 2 * nr; ++q)
+            if (!isfinite(xs[q])) flags |= ORC_F_NONFINITE;
+        if (!isfinite(J[0])) flags |= ORC_F_NONFINITE;
+        if (J[0] < 0.0) flags |= ORC_F_NEGPARITY;
+        J[5] = (double)flags;
+        for (int q = 0; q < 6; ++q) bundle_out[(size_t)b * 6 + q] = J[q];
+    }
+    if (planes_out)
+        for (int q = 0; q < np; ++q) {
+            planes_out[4 * q] = pl[q].chi;
+            planes_out[4 * q + 1] = pl[q].z;
+            planes_out[4 * q + 2] = (double)pl[q].n;
+            planes_out[4 * q + 3] = pl[q].hi - pl[q].lo;
+        }
+    if (n_planes) *n_planes = np;
+    if (n_pairs) *n_pairs = total;
+    mp_free(pl, f->replicated ? f->n_rep * o->slices : o->slices);
+    return 0;
+}

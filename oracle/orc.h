@@ -177,6 +177,28 @@ int orc_shear_histogram(int64_t n, const double *mu, const double *g1, const dou
                         const int32_t *flags, const orc_hist_opts *o, uint64_t *counts,
                         uint64_t *wfix, double *scalars);
 
+/* ---- multiple lens-plane comparison system (Sec. 3.1; Eqs. defangleB, lenseqn) */
+typedef struct {
+    int n_ring;         /* rays on the bundle polygon */
+    double theta_r;     /* polygon radius, rad */
+    double phase;       /* polygon orientation, rad */
+    int slices;         /* slabs (planes) per replica, or per isolated field */
+} orc_mp_opts;
+
+/* deflection integral of a uniform unit surface density over the rectangle
+ * [lo, hi]: out = int (x - x') / |x - x'|^2 d^2x' */
+void orc_rect_deflection(const double lo[2], const double hi[2], const double x[2], double out[2]);
+
+/* Bundles traced through the lens planes of f (see orc.c for the readings).
+ * ray_out (optional): n_b*(1+n_ring)*2 comoving source-plane positions;
+ * bundle_out: n_b*6 (mu, kappa, gamma1, gamma2, omega, flags);
+ * planes_out (optional, room for n_rep*slices or slices planes): per plane
+ * (chi, z, particles, slab thickness); *n_planes: planes used;
+ * *n_pairs: (ray, particle) deflection terms. */
+int orc_multiplane(const orc_cosmo *c, const orc_field *f, double z_s, int64_t n_b, const double *theta,
+                   const orc_mp_opts *o, double *ray_out, double *bundle_out, double *planes_out,
+                   int *n_planes, double *n_pairs, int nthreads);
+
 #ifdef __cplusplus
 }
 #endif
