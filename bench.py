@@ -479,6 +479,84 @@ def run_box(args):
     return 0
 
 
+def run_multiplane(args):
+    """The comparison of Sec. 5.4 on the 2^21-particle box (z_s = 0.5): the
+    multiple lens-plane system (one plane per replica at its centre, Sec. 3.1)
+    on all 65,536 bundles, timed as the metric (one step = one multi-plane
+    trace of every bundle: plane table, deflection pair sums, updates,
+    reducer); then the 3D trace (1000 uniform RK4 steps) on the first
+    --mp-3d-bundles bundles of the same grid, and both methods' muPDF and
+    shear statistics on those bundles (<mu>_w, sigma_w, |gamma|)."""
+    import torch
+
+    import inputs
+    import paper_1110_4894_gb300 as P
+    cfg = inputs.config_c3(n_steps=1000)
+    dev = torch.device("cuda", 0)
+    nb = cfg["theta"].shape[0]
+    ctx = P.Context(0, precision=P.MIXED, autotune=1, time_kernels=1)
+    ctx.set_cosmology(*cfg["cosmo"])
+    ctx.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"], replicated=True, box_length=cfg["L"], rot=cfg["rot"],
+                       shift=cfg["shift"], mean_subtract=True)
+    d_theta = torch.from_numpy(np.ascontiguousarray(cfg["theta"])).to(dev)
+    d_bout = torch.zeros(nb * 6, dtype=torch.float64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    sp = stream.cuda_stream
+    kw = dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"])
+    for _ in range(args.warmup):
+        ctx.multiplane_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), d_bout.data_ptr(), slices=args.mp_slices,
+                              **kw)
+    torch.cuda.synchronize()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    inter = 0.0
+    with ClockSampler(0) as clk:
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            ctx.multiplane_device(sp, 0, cfg["z_s"], nb, d_theta.data_ptr(), d_bout.data_ptr(),
+                                  slices=args.mp_slices, **kw)
+            ev[k][1].record(stream)
+            inter += ctx.stats()["interactions"]
+    clocks = clk.summary()
+    dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
+    mp_all = d_bout.view(nb, 6).cpu().numpy()
+    # one-to-one: the 3D trace and the lens planes on the same bundles
+    k = min(nb, args.mp_3d_bundles)
+    th = np.ascontiguousarray(cfg["theta"][:k])
+    t0 = time.perf_counter()
+    r3 = ctx.trace(0, cfg["z_s"], th, n_steps=cfg["n_steps"], schedule=0, **kw)
+    t3 = time.perf_counter() - t0
+    i3 = ctx.stats()["interactions"]
+    rm = ctx.multiplane(0, cfg["z_s"], th, slices=args.mp_slices, **kw)
+
+    def stats(r):
+        c, w, sc = ctx.histogram(r["mu"], r["flags"], **HIST)
+        gam = np.hypot(r["gamma1"], r["gamma2"])
+        wt = 1.0 / np.abs(r["mu"])
+        return {"bundles": int(sc["n_used"]), "mean_w": sc["mean_w"], "sigma_w": sc["sigma_w"],
+                "mu_p5_p50_p95": [float(v) for v in np.percentile(r["mu"], [5, 50, 95])],
+                "gamma_mean_w": float(np.sum(wt * gam) / np.sum(wt)),
+                "gamma_p50_p95": [float(v) for v in np.percentile(gam, [50, 95])]}
+
+    all_mp = {"mu": mp_all[:, 0], "gamma1": mp_all[:, 2], "gamma2": mp_all[:, 3],
+              "flags": mp_all[:, 5].astype(np.int32)}
+    out = {"metric": "ray-particle interactions/s (multiple lens planes)", "value": inter / dev_s,
+           "unit": "interactions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
+           "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
+           "vs_baseline": None, "dtype": "f32", "data": "synthetic", "bundles_per_s": nb * args.steps / dev_s,
+           "config": {"workload": "box_2e21p_100mpch_zs0.5_65536b_planes%d" % args.mp_slices,
+                      "particles": len(cfg["mass"]), "bundles": nb, "replicas": int(cfg["n_rep"]),
+                      "planes_per_replica": args.mp_slices},
+           "multiplane_all_bundles": stats(all_mp),
+           "one_to_one": {"bundles": k, "rk4_steps_3d": cfg["n_steps"], "trace_3d_s": t3,
+                          "trace_3d_interactions_per_s": i3 / t3,
+                          "3d": stats(r3), "multiplane": stats(rm),
+                          "median_abs_mu_mp_over_mu_3d_minus_1": float(np.median(np.abs(rm["mu"] / r3["mu"] - 1))),
+                          "corr_mu_minus_1": float(np.corrcoef(rm["mu"] - 1, r3["mu"] - 1)[0, 1])},
+           "clocks": clocks}
+    print(json.dumps(out))
+    return 0
+
+
 def trace_kw(cfg):
     return dict(n_ring=cfg["n_ring"], theta_r=cfg["theta_r"], schedule=cfg["schedule"], n_steps=cfg["n_steps"],
                 lens_chi=cfg["lens_chi"], asinh_s=cfg["asinh_s"])
@@ -594,7 +672,15 @@ def cpu_baseline_and_parity(args, cfg, ctx, P, local):
     idx = np.linspace(0, nb_all - 1, args.parity_bundles).astype(int)
     th = np.ascontiguousarray(cfg["theta"][idx])
     kw = box_kw(cfg, args.parity_steps, 16)
-    g = ctx.trace(0, cfg["z_s"], th, want_rays=True, **kw)
+    # the mixed path traces the aligned group of 256 consecutive bundles (one
+    # or two thread blocks, compact on the sky as in the full run) around each
+    # sample, as one launch; the samples are compared
+    grp = 256
+    starts = (idx // grp) * grp
+    sel = np.concatenate([np.arange(a, min(a + grp, nb_all)) for a in starts])
+    pos_in = np.searchsorted(sel, idx)
+    gg = ctx.trace(0, cfg["z_s"], np.ascontiguousarray(cfg["theta"][sel]), want_rays=True, **kw)
+    g = {"mu": gg["mu"][pos_in], "flags": gg["flags"][pos_in], "rays": gg["rays"][pos_in]}
     c64 = P.Context(local, precision=P.FP64)
     c64.set_cosmology(*cfg["cosmo"])
     load_box(c64, 0, cfg)
@@ -608,7 +694,8 @@ def cpu_baseline_and_parity(args, cfg, ctx, P, local):
     a_o = o.alpha()
     da = np.linalg.norm(a_g - a_o, axis=-1) / np.linalg.norm(a_o, axis=-1)
     parity = {"bundles": int(len(idx)), "rk4_steps": args.parity_steps,
-              "sample": "bundles at evenly spaced indices of the 1024^2 grid; complete traces to z_s = 1",
+              "sample": "bundles at evenly spaced indices of the 1024^2 grid, each traced by the GPU within its "
+                        "aligned group of 256 grid neighbours; complete traces to z_s = 1",
               "max_rel_dmu_mixed_vs_oracle": float(rel.max()),
               "max_rel_dalpha_mixed_vs_oracle": float(da.max()),
               "max_rel_dmu_fp64gpu_vs_oracle": float(rel64.max()),
@@ -1049,7 +1136,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c5", choices=["c5", "nfw", "cones", "grid", "born", "box3", "box5",
-                                                          "prism"])
+                                                          "prism", "multiplane"])
+    ap.add_argument("--mp-slices", type=int, default=1, help="multiplane: planes per replica")
+    ap.add_argument("--mp-3d-bundles", type=int, default=4096, help="multiplane: bundles also traced in 3D")
     ap.add_argument("--table-steps", type=int, default=1000, help="RK4 steps of the headline trace's table")
     ap.add_argument("--box-particles", type=int, default=2 ** 24, help="checks only: a smaller headline box")
     ap.add_argument("--bundles", type=int, default=0, help="checks only: trace the first bundles of the grid")
@@ -1086,6 +1175,8 @@ def main():
         return run_reference(args)
     if args.workload == "nfw":
         return run_nfw(args)
+    if args.workload == "multiplane":
+        return run_multiplane(args)
     if args.workload == "cones":
         return run_cones(args)
     if args.workload == "grid":

@@ -311,6 +311,40 @@ int rt3d_trace_end(rt3d_ctx *ctx, void *stream, double *d_bundle_out, double *d_
 int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones,
                      const rt3d_bundle_opts *b, rt3d_bundle_result *outs);
 
+/* ---- the multiple lens-plane comparison system (Sec. 3.1) ----------------
+ * The paper's comparison method: the mass between observer and source is cut
+ * into slabs along x3 -- each replica of a box into `slices` slabs of equal
+ * thickness, the last one cut at the source plane x3 = chi(z_s); an isolated
+ * field's x3 range into `slices` slabs -- and each slab is projected onto a
+ * plane at its centre (Sec. 3.1: "projected onto a plane ... usually placed at
+ * the centre of the box"; slices = 1 is that).  A ray travels straight from
+ * plane to plane and is deflected only at them, by the matter of that plane:
+ * the thin-lens angle of Eq. defangleB of each projected Plummer particle,
+ *   alpha_hat(x) = 4 G/c^2 (1 + z_k) sum_p m_p (x - x_p) / (|x - x_p|^2 + eps^2)
+ * in comoving transverse coordinates, which makes the propagation the
+ * multi-plane lens equation of Sec. 3.1 (flat universe); a mean-subtracted box
+ * also removes the deflection of the slab's uniform mean surface density over
+ * the replica's square cross-section.  Particles beyond the source plane are
+ * left out.  The bundles (b->n_ring, theta_r, phase; the step options are not
+ * used) and the least-squares Jacobian are those of rt3d_trace, so mu, kappa,
+ * gamma and the muPDF of rt3d_histogram compare one to one with the 3D trace
+ * (Sec. 5.4, Figs. RBMvsMudMag, RBMvsMudShear).  The pair sums are FP32 with
+ * compensated accumulation (RT3D_MIXED) or FP64 (RT3D_FP64); the ray state,
+ * deflection update and Jacobian are FP64.  out->ray_state (optional) holds
+ * per ray (0, x1, x2, chi_s, 0, slope1, slope2, 1) at the source plane;
+ * out->ray_steps (optional) is zeroed.  Errors: as rt3d_trace, plus
+ * RT3D_ENOTIMPL for grid fields and RT3D_EINVAL for slices outside
+ * [1, 4096] or more than 65536 planes. */
+int rt3d_multiplane(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_bundles, const double *theta,
+                    const rt3d_bundle_opts *b, int slices, rt3d_bundle_result *out);
+
+/* The lens-plane system of Sec. 3.1 as rt3d_multiplane with device arrays
+ * (d_theta n_bundles*2; d_bundle_out n_bundles*6 as rt3d_trace_device;
+ * d_ray_out optional n_bundles*(1+n_ring)*8), enqueued on stream. */
+int rt3d_multiplane_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_bundles,
+                           const double *d_theta, const rt3d_bundle_opts *b, int slices, double *d_bundle_out,
+                           double *d_ray_out);
+
 /* muPDF of n magnifications (Eq. weighthisto): bins uniform in log10|mu|
  * (bin = floor((log10|mu| - log10 mu_min) / dl) in FP64), counts and
  * fixed-point weights round(2^32/|mu|); flagged (NOCROSS / NONFINITE) and

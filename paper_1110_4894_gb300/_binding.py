@@ -103,6 +103,10 @@ def lib(build=True):
         "rt3d_trace_device": ([vp, vp, C.c_int, C.c_double, C.c_int64, vp, C.POINTER(BundleOpts), vp, vp], C.c_int),
         "rt3d_trace_batch": ([vp, C.c_int, C.POINTER(Cone), C.POINTER(BundleOpts), C.POINTER(BundleResult)],
                              C.c_int),
+        "rt3d_multiplane": ([vp, C.c_int, C.c_double, C.c_int64, _dp, C.POINTER(BundleOpts), C.c_int,
+                             C.POINTER(BundleResult)], C.c_int),
+        "rt3d_multiplane_device": ([vp, vp, C.c_int, C.c_double, C.c_int64, vp, C.POINTER(BundleOpts), C.c_int, vp,
+                                    vp], C.c_int),
         "rt3d_trace_begin": ([vp, vp, C.c_int, C.c_double, C.c_int64, vp, C.POINTER(BundleOpts)], C.c_int),
         "rt3d_trace_advance": ([vp, vp, C.c_int, C.POINTER(C.c_int)], C.c_int),
         "rt3d_trace_end": ([vp, vp, vp, vp], C.c_int),
@@ -292,6 +296,32 @@ class Context:
         self._check(self.L.rt3d_trace_device(self.h, C.c_void_p(stream), int(field_id), float(z_s), int(n_bundles),
                                              C.c_void_p(d_theta), C.byref(o), C.c_void_p(d_bundle_out),
                                              C.c_void_p(d_ray_out) if d_ray_out else None))
+
+    def multiplane(self, field_id, z_s, theta, slices=1, want_rays=False, **kw):
+        """rt3d_multiplane: the bundles through the field's lens planes (Sec. 3.1);
+        the same result dict as trace ("rays": (n, nr, 8) source-plane states)."""
+        theta = np.ascontiguousarray(theta, np.float64).reshape(-1, 2)
+        nb = theta.shape[0]
+        o = self.bundle_opts(**kw)
+        nr = 1 + o.n_ring
+        r = {k: np.zeros(nb) for k in ("mu", "kappa", "gamma1", "gamma2", "omega")}
+        r["flags"] = np.zeros(nb, np.int32)
+        rays = np.zeros((nb, nr, 8)) if want_rays else None
+        res = BundleResult(_p(r["mu"]), _p(r["kappa"]), _p(r["gamma1"]), _p(r["gamma2"]), _p(r["omega"]),
+                           _p(r["flags"], C.c_int32), _p(rays) if want_rays else None, None)
+        self._check(self.L.rt3d_multiplane(self.h, int(field_id), float(z_s), nb, _p(theta), C.byref(o),
+                                           int(slices), C.byref(res)))
+        if want_rays:
+            r["rays"] = rays
+        return r
+
+    def multiplane_device(self, stream, field_id, z_s, n_bundles, d_theta, d_bundle_out, slices=1, d_ray_out=None,
+                          **kw):
+        """rt3d_multiplane_device: enqueue the lens-plane system with device pointers."""
+        o = self.bundle_opts(**kw)
+        self._check(self.L.rt3d_multiplane_device(self.h, C.c_void_p(stream), int(field_id), float(z_s),
+                                                  int(n_bundles), C.c_void_p(d_theta), C.byref(o), int(slices),
+                                                  C.c_void_p(d_bundle_out), C.c_void_p(d_ray_out) if d_ray_out else None))
 
     def trace_begin(self, stream, field_id, z_s, n_bundles, d_theta, **kw):
         """rt3d_trace_begin: open a trace in pieces (step table, initialiser) on stream."""

@@ -127,6 +127,7 @@ struct FieldSlot {
     int64_t n = 0;
     bool is_grid = false;  // grid path: phi and grad phi interpolated from nodes
     GridDev gd;
+    double x3_lo = 0.0, x3_hi = 0.0;  // x3 range of an isolated field's particles (lens planes)
 };
 
 // A trace open on the context: the ray state lives in the context's scratch
@@ -322,6 +323,7 @@ extern "C" int rt3d_destroy(rt3d_ctx *ctx)
     cudaFree(s.bout);
     cudaFree(s.rout);
     cudaFree(s.prism);
+    cudaFree(s.planes);
     cudaFree(ctx->atab);
     cudaFree(ctx->d_hist_u64);
     cudaFree(ctx->d_hist_f64);
@@ -525,6 +527,13 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
         f.uniform_mass = umass ? 1 : 0;
         f.m_uniform = umass ? kMuG * mass[0] * mscale : 0.0;
         slot.n = n;
+        if (!repl && n > 0) {
+            slot.x3_lo = slot.x3_hi = pos[2];
+            for (int64_t i = 1; i < n; ++i) {
+                slot.x3_lo = std::min(slot.x3_lo, pos[3 * i + 2]);
+                slot.x3_hi = std::max(slot.x3_hi, pos[3 * i + 2]);
+            }
+        }
         slot.loaded = true;
     } while (0);
     cudaFree(d_pos);
@@ -1082,6 +1091,115 @@ extern "C" int rt3d_trace_end(rt3d_ctx *ctx, void *stream, double *d_bundle_out,
     int rc = trace_end(ctx, d_bundle_out, d_ray_out, (cudaStream_t)stream);
     ctx->trace.open = false;
     return rc;
+}
+
+// ---------------------------------------------------------------------------
+// multiple lens-plane comparison system (Sec. 3.1)
+// ---------------------------------------------------------------------------
+static void unpack_bundles(const double *bo, int64_t nb, rt3d_bundle_result *out);
+
+static int check_mp_args(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, const rt3d_bundle_opts *b, int slices)
+{
+    int rc = check_trace_args(ctx, field_id, z_s, n_b, b);
+    if (rc) return rc;
+    if (ctx->fields[field_id].is_grid)
+        return fail(ctx, RT3D_ENOTIMPL, "the lens-plane system projects particle fields, not grid fields");
+    if (slices < 1 || slices > 4096) return fail(ctx, RT3D_EINVAL, "slices must be 1..4096");
+    const FieldSlot &fs = ctx->fields[field_id];
+    if ((int64_t)(fs.df.replicated ? fs.df.n_rep : 1) * slices > 65536)
+        return fail(ctx, RT3D_EINVAL, "at most 65536 lens planes");
+    return RT3D_OK;
+}
+
+static int enqueue_multiplane(rt3d_ctx *ctx, const FieldSlot &fs, double z_s, int64_t n_b, const double *d_theta,
+                              const rt3d_bundle_opts *b, int slices, double *d_bout, double *d_rout, cudaStream_t st)
+{
+    const bool fp64 = ctx->opt.precision == RT3D_FP64;
+    const int nr = 1 + b->n_ring;
+    const int64_t n_rays = n_b * nr;
+    Scratch &s = ctx->scr;
+    CK(grow(s.state, s.state_rays, (size_t)(32 * n_rays)));
+    CK(grow(s.ints, s.ints_n, (size_t)(2 * n_rays + 2 * n_b)));
+    RayState rs = make_state(ctx, n_b, nr);
+    const int n_pl = (fs.df.replicated ? fs.df.n_rep : 1) * slices;
+    CK(grow(*(char **)&s.planes, s.planes_bytes, (size_t)n_pl * mp_plane_bytes()));
+    // particle splits: about five waves of blocks (128 bundles per block; 64 for FP64)
+    const int64_t blocks = (n_b + (fp64 ? 63 : 127)) / (fp64 ? 64 : 128);
+    const int64_t tiles = std::max<int64_t>(1, (fs.n + kTile - 1) / kTile);
+    const int splits = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, ((int64_t)ctx->n_sm * 5 * 4 + blocks - 1) / blocks));
+    CK(grow(*(char **)&s.partials, s.partials_bytes, mp_partials_bytes(b->n_ring, n_b, splits, fp64)));
+    TraceParams tp{};
+    tp.cosmo = ctx->cosmo;
+    tp.n_ring = b->n_ring;
+    tp.theta_r = b->theta_r;
+    tp.phase = b->phase;
+    tp.christoffel = ctx->opt.christoffel;
+    tp.n_steps = 1;
+    const bool umass = !fp64 && fs.df.uniform_mass;
+    CK(mp_run(ctx->cosmo, fs.df, z_s, slices, fs.x3_lo, fs.x3_hi, tp, d_theta, rs, s.planes, n_pl, s.partials, splits,
+              fp64, umass, s.misc, s.counters + 2, d_bout, d_rout, st));
+    ctx->stats = rt3d_stats{};
+    ctx->stats.launches = 4 + 2 * (int64_t)n_pl;
+    ctx->stats.force_launches = n_pl;
+    ctx->stats.splits = splits;
+    ctx->stats.variant = 7;
+    ctx->last_npart = (double)n_rays;  // interactions = rays x particles on the planes
+    ctx->stats_pending = true;
+    ctx->tev_used = 0;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_multiplane(rt3d_ctx *ctx, int field_id, double z_s, int64_t n_b, const double *theta,
+                               const rt3d_bundle_opts *b, int slices, rt3d_bundle_result *out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
+    int rc = check_mp_args(ctx, field_id, z_s, n_b, b, slices);
+    if (rc) return rc;
+    if (!theta || !out || !out->mu) return fail(ctx, RT3D_EINVAL, "null theta or result arrays");
+    for (int64_t i = 0; i < 2 * n_b; ++i)
+        if (!isfinite(theta[i])) return fail(ctx, RT3D_EINVAL, "non-finite theta");
+    CK(cudaSetDevice(ctx->device));
+    const int64_t n_rays = n_b * (1 + b->n_ring);
+    Scratch &s = ctx->scr;
+    CK(grow(s.theta, s.theta_n, (size_t)(2 * n_b)));
+    CK(grow(s.bout, s.bout_n, (size_t)(6 * n_b)));
+    const bool want_rays = out->ray_state != nullptr;
+    if (want_rays) CK(grow(s.rout, s.rout_n, (size_t)(8 * n_rays)));
+    cudaStream_t st = ctx->stream;
+    CK(cudaEventRecord(ctx->ev0, st));
+    CK(cudaMemcpyAsync(s.theta, theta, 2 * n_b * sizeof(double), cudaMemcpyHostToDevice, st));
+    rc = enqueue_multiplane(ctx, ctx->fields[field_id], z_s, n_b, s.theta, b, slices, s.bout,
+                            want_rays ? s.rout : nullptr, st);
+    if (rc) return rc;
+    std::vector<double> bo((size_t)(6 * n_b));
+    CK(cudaMemcpyAsync(bo.data(), s.bout, 6 * n_b * sizeof(double), cudaMemcpyDeviceToHost, st));
+    if (want_rays) CK(cudaMemcpyAsync(out->ray_state, s.rout, 8 * n_rays * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CK(cudaEventRecord(ctx->ev1, st));
+    CK(cudaStreamSynchronize(st));
+    float ms = 0.0f;
+    CK(cudaEventElapsedTime(&ms, ctx->ev0, ctx->ev1));
+    rc = finish_stats(ctx);
+    if (rc) return rc;
+    ctx->stats.device_ms = ms;
+    unpack_bundles(bo.data(), n_b, out);
+    if (out->ray_steps)
+        for (int64_t i = 0; i < n_rays; ++i) out->ray_steps[i] = 0;
+    return RT3D_OK;
+}
+
+extern "C" int rt3d_multiplane_device(rt3d_ctx *ctx, void *stream, int field_id, double z_s, int64_t n_b,
+                                      const double *d_theta, const rt3d_bundle_opts *b, int slices,
+                                      double *d_bundle_out, double *d_ray_out)
+{
+    if (!ctx) return RT3D_EINVAL;
+    ctx->trace.open = false;  // this call reuses the open trace's scratch
+    int rc = check_mp_args(ctx, field_id, z_s, n_b, b, slices);
+    if (rc) return rc;
+    if (!d_theta || !d_bundle_out) return fail(ctx, RT3D_EINVAL, "null device arrays");
+    CK(cudaSetDevice(ctx->device));
+    return enqueue_multiplane(ctx, ctx->fields[field_id], z_s, n_b, d_theta, b, slices, d_bundle_out, d_ray_out,
+                              (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

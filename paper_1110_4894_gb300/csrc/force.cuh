@@ -381,6 +381,21 @@ __global__ void __launch_bounds__(NT) k_force_packed(ForceArgs A)
                                                (float2 *)A.out, s_a, s_b, s_e);
 }
 
+// Potential sum of a ring ray to first order about its bundle's central ray:
+// with S0 = sum m / r and S = sum m d / r^3 (d = particle - ray), phi = -S0
+// and grad phi = -S (times the mass scale), so phi(r_k) = phi(r_c) + (r_k -
+// r_c) . grad phi(r_c) gives S0_k = S0_c - e_k . S_c for e_k = r_c - r_k.  The
+// potential enters the geodesic equation only in terms of order phi times
+// a-dot (App. A), where the neglected second-order term, e_k^T H e_k / 2 of
+// the particles nearest the ray, acts over a path of the order of their
+// distance: its effect on a ray's direction is below 1e-14 rad for the
+// softened fields here, against bundle differential deflections of 1e-8 rad
+// and more.  The gradient sums themselves stay exact per ray.
+__device__ __forceinline__ float ring_phi(float s0_c, const float e[3], float gx, float gy, float gz)
+{
+    return s0_c - fmaf(e[0], gx, fmaf(e[1], gy, e[2] * gz));
+}
+
 // Bundle-centric variant: one thread per bundle (central ray + NRING rays).
 // Each satellite's offset from a particle is formed from the central ray's,
 //   d_k = (p - r_c) + (r_c - r_k),
@@ -436,9 +451,9 @@ __device__ __forceinline__ void bundle_block_sum(const DevField &f, const double
         ez[p] = make_float2(v[0][2], v[1][2]);
     }
     float c_phi = 0.f, c_hx = 0.f, c_hy = 0.f, c_hz = 0.f, c_lx = 0.f, c_ly = 0.f, c_lz = 0.f;
-    float2 phi[PP], hx[PP], hy[PP], hz[PP], lx[PP], ly[PP], lz[PP];
+    float2 hx[PP], hy[PP], hz[PP], lx[PP], ly[PP], lz[PP];
 #pragma unroll
-    for (int p = 0; p < PP; ++p) phi[p] = hx[p] = hy[p] = hz[p] = lx[p] = ly[p] = lz[p] = make_float2(0.f, 0.f);
+    for (int p = 0; p < PP; ++p) hx[p] = hy[p] = hz[p] = lx[p] = ly[p] = lz[p] = make_float2(0.f, 0.f);
     const float dlt = (float)f.delta;
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
     for (int j = rmin; j <= rmax; ++j) {
@@ -511,15 +526,7 @@ __device__ __forceinline__ void bundle_block_sum(const DevField &f, const double
                         s2 = __ffma2_rn(qx, qx, s2);
                         const float2 w = make_float2(rsqrt_mufu(s2.x), rsqrt_mufu(s2.y));
                         const float2 w2 = __fmul2_rn(w, w);
-                        float2 m3;
-                        if (UMASS) {
-                            phi[p] = __fadd2_rn(phi[p], w);
-                            m3 = __fmul2_rn(w, w2);
-                        } else {
-                            const float2 mw = __fmul2_rn(make_float2(a.w, a.w), w);
-                            phi[p] = __fadd2_rn(phi[p], mw);
-                            m3 = __fmul2_rn(mw, w2);
-                        }
+                        const float2 m3 = UMASS ? __fmul2_rn(w, w2) : __fmul2_rn(__fmul2_rn(make_float2(a.w, a.w), w), w2);
                         cx[p] = __ffma2_rn(qx, m3, cx[p]);
                         cy[p] = __ffma2_rn(qy, m3, cy[p]);
                         cz[p] = __ffma2_rn(qz, m3, cz[p]);
@@ -543,12 +550,15 @@ __device__ __forceinline__ void bundle_block_sum(const DevField &f, const double
     out[(sn + 1) * n_rays + ic] = make_float2(c_hx, c_lx);
     out[(sn + 2) * n_rays + ic] = make_float2(c_hy, c_ly);
     out[(sn + 3) * n_rays + ic] = make_float2(c_hz, c_lz);
+    // ring potentials to first order about the central ray (ring_phi)
+    const float gcx = c_hx + c_lx, gcy = c_hy + c_ly, gcz = c_hz + c_lz;
 #pragma unroll
     for (int p = 0; p < PP; ++p)
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int64_t i = ic + 1 + 2 * p + h;
-            out[(sn + 0) * n_rays + i] = make_float2(h ? phi[p].y : phi[p].x, 0.f);
+            const float e[3] = {h ? ex[p].y : ex[p].x, h ? ey[p].y : ey[p].x, h ? ez[p].y : ez[p].x};
+            out[(sn + 0) * n_rays + i] = make_float2(ring_phi(c_phi, e, gcx, gcy, gcz), 0.f);
             out[(sn + 1) * n_rays + i] = h ? make_float2(hx[p].y, lx[p].y) : make_float2(hx[p].x, lx[p].x);
             out[(sn + 2) * n_rays + i] = h ? make_float2(hy[p].y, ly[p].y) : make_float2(hy[p].x, ly[p].x);
             out[(sn + 3) * n_rays + i] = h ? make_float2(hz[p].y, lz[p].y) : make_float2(hz[p].x, lz[p].x);
@@ -614,9 +624,7 @@ __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const doubl
     float2 *s_hi = s_hl, *s_lo = s_hl + NR * 3 * NT;
 #pragma unroll
     for (int q = 0; q < NR * 3; ++q) s_hi[q * NT + tid] = s_lo[q * NT + tid] = make_float2(0.f, 0.f);
-    float2 phi[NR];
-#pragma unroll
-    for (int g = 0; g < NR; ++g) phi[g] = make_float2(0.f, 0.f);
+    float2 phi = make_float2(0.f, 0.f);  // central rays; the ring's follow in the epilogue
     const float dlt = (float)f.delta;
     const float2 E2u = make_float2(f.eps2u, f.eps2u);
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
@@ -686,11 +694,11 @@ __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const doubl
                         const float2 w2 = __fmul2_rn(w, w);
                         float2 m3;
                         if (UMASS) {
-                            phi[g] = __fadd2_rn(phi[g], w);
+                            if (g == 0) phi = __fadd2_rn(phi, w);
                             m3 = __fmul2_rn(w, w2);
                         } else {
                             const float2 mw = __fmul2_rn(M2, w);
-                            phi[g] = __fadd2_rn(phi[g], mw);
+                            if (g == 0) phi = __fadd2_rn(phi, mw);
                             m3 = __fmul2_rn(mw, w2);
                         }
                         cx[g] = __ffma2_rn(qx, m3, cx[g]);
@@ -718,10 +726,23 @@ __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const doubl
     for (int h = 0; h < 2; ++h) {
         if (!valid[h]) continue;
         const int64_t ic = bb[h] * NR;
+        const float pc = h ? phi.y : phi.x;
+        float gc[3];
+#pragma unroll
+        for (int oo = 0; oo < 3; ++oo) {
+            const float2 hi = s_hi[oo * NT + tid], lo = s_lo[oo * NT + tid];
+            gc[oo] = h ? hi.y + lo.y : hi.x + lo.x;
+        }
 #pragma unroll
         for (int g = 0; g < NR; ++g) {
             const int64_t i = ic + g;
-            out[(sn + 0) * n_rays + i] = make_float2(h ? phi[g].y : phi[g].x, 0.f);
+            float pg = pc;
+            if (g > 0) {  // ring potentials to first order about the central ray (ring_phi)
+                const float e[3] = {h ? ex[g - 1].y : ex[g - 1].x, h ? ey[g - 1].y : ey[g - 1].x,
+                                    h ? ez[g - 1].y : ez[g - 1].x};
+                pg = ring_phi(pc, e, gc[0], gc[1], gc[2]);
+            }
+            out[(sn + 0) * n_rays + i] = make_float2(pg, 0.f);
 #pragma unroll
             for (int oo = 0; oo < 3; ++oo) {
                 const int q = (g * 3 + oo) * NT + tid;
@@ -814,9 +835,7 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     float2 *s_hi = s_hl, *s_lo = s_hl + NQ * NT;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) s_hi[q * NT + tid] = s_lo[q * NT + tid] = make_float2(0.f, 0.f);
-    float2 phi[NR];
-#pragma unroll
-    for (int g = 0; g < NR; ++g) phi[g] = make_float2(0.f, 0.f);
+    float2 phi = make_float2(0.f, 0.f);  // central rays; the ring's follow in the epilogue
     const float dlt = (float)f.delta;
     const float2 E2u = make_float2(f.eps2u, f.eps2u);
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
@@ -891,11 +910,11 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
                         const float2 u = __fmul2_rn(w, w);
                         float2 m3;
                         if (UMASS) {
-                            phi[g] = __fadd2_rn(phi[g], w);
+                            if (g == 0) phi = __fadd2_rn(phi, w);
                             m3 = __fmul2_rn(w, u);
                         } else {
                             const float2 mw = __fmul2_rn(M2, w);
-                            phi[g] = __fadd2_rn(phi[g], mw);
+                            if (g == 0) phi = __fadd2_rn(phi, mw);
                             m3 = __fmul2_rn(mw, u);
                         }
                         if (g > 0) cs[g - 1] = __fadd2_rn(cs[g - 1], m3);
@@ -934,8 +953,7 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     // of bundle h.
     constexpr int NSLOT = NR + 2 * NR * 3;
     float2 res[NSLOT];
-#pragma unroll
-    for (int g = 0; g < NR; ++g) res[g] = phi[g];
+    res[0] = phi;
 #pragma unroll
     for (int h = 0; h < 2; ++h)
 #pragma unroll
@@ -965,6 +983,20 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
                 res[NR + (h * NR + g) * 3 + oo] = make_float2(hi, lo);
             }
         }
+    // ring potentials to first order about the central ray (ring_phi), from
+    // the central gradient; e_k = r_c - r_k is half the stored 2 e_k
+#pragma unroll
+    for (int g = 1; g < NR; ++g) {
+        float v[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const float2 *gc = res + NR + (h * NR) * 3;
+            const float e[3] = {0.5f * (h ? fx[g - 1].y : fx[g - 1].x), 0.5f * (h ? fy[g - 1].y : fy[g - 1].x),
+                                0.5f * (h ? fz[g - 1].y : fz[g - 1].x)};
+            v[h] = ring_phi(h ? phi.y : phi.x, e, gc[0].x + gc[0].y, gc[1].x + gc[1].y, gc[2].x + gc[2].y);
+        }
+        res[g] = make_float2(v[0], v[1]);
+    }
     if (CL == 1) {
         const int64_t sn = (int64_t)split * 4;
 #pragma unroll

@@ -293,6 +293,8 @@ struct Scratch {
     size_t rout_n = 0;
     double *prism = nullptr;       // n_b * 13 bundle prism records
     size_t prism_n = 0;
+    char *planes = nullptr;        // lens-plane table of the multi-plane system
+    size_t planes_bytes = 0;
 };
 
 // streaming multiprocessors of the current device (queried once per device;
@@ -387,5 +389,13 @@ cudaError_t born_run(const Cosmo &c, const DevField &f, int64_t n_particles, dou
 
 int force_max_splits(const ForceShape &sh, int64_t n_particles);
 size_t partials_bytes(const ForceShape &sh, int64_t n_rays, bool fp64);
+
+// multiple lens-plane comparison system (multiplane.cu)
+size_t mp_plane_bytes();
+size_t mp_partials_bytes(int n_ring, int64_t n_b, int splits, bool fp64);
+cudaError_t mp_run(const Cosmo &c, const DevField &f, double z_s, int slices, double x3_lo, double x3_hi,
+                   const TraceParams &tp, const double *d_theta, RayState rs, void *d_planes, int n_pl, void *partials,
+                   int splits, bool fp64, bool umass, double *misc, unsigned long long *count, double *d_bout,
+                   double *d_rout, cudaStream_t st);
 
 }  // namespace rt3d
