@@ -316,8 +316,8 @@ int rt3d_trace_batch(rt3d_ctx *ctx, int n_cones, const rt3d_cone *cones,
  * into slabs along x3 -- each replica of a box into `slices` slabs of equal
  * thickness, the last one cut at the source plane x3 = chi(z_s); an isolated
  * field's x3 range into `slices` slabs -- and each slab is projected onto a
- * plane at its centre (Sec. 3.1: "projected onto a plane ... usually placed at
- * the centre of the box"; slices = 1 is that).  A ray travels straight from
+ * plane at its centre (Sec. 3.1 puts each box's plane at its centre as the
+ * rule; slices = 1 is that).  A ray travels straight from
  * plane to plane and is deflected only at them, by the matter of that plane:
  * the thin-lens angle of Eq. defangleB of each projected Plummer particle,
  *   alpha_hat(x) = 4 G/c^2 (1 + z_k) sum_p m_p (x - x_p) / (|x - x_p|^2 + eps^2)

@@ -8,7 +8,7 @@ Steps, in the paper's order:
 1. Cloud-in-cell assignment of the particle masses to the nodes
    x = lo + h (i1, i2, i3), i = 0..n-1 (Sec. 3.3, Hockney & Eastwood CIC);
    mass that falls on nodes outside the grid is dropped.  Optionally the mean
-   node mass is subtracted ("the mean matter density is then subtracted off").
+   node mass is subtracted (Sec. 3.3 removes the mean density).
 2. phi and grad phi on the nodes by a zero-padded FFT convolution (Eqs. psi,
    derivs with phi = a psi) of the node masses with the kernels
        K_phi(d) = -mu_G (|d|^2 + eps^2)^(-1/2),
@@ -146,10 +146,10 @@ class BoxGridField:
     along x3 into `cubes` cubes of side W; the particles of each cube (half-
     open in every axis, the others dropped) go on that cube's own n^3 grid
     with nodes on its faces (spacing W / (n - 1)), minus the cube's mean node
-    mass, and each cube's field is computed from its own mass only ("structure
-    within the box only").  A bundle uses the cube holding its central ray;
-    points up to one node spacing outside the cube's nodes (the bundle's other
-    rays near a face) take the end intervals' cubics."""
+    mass, and each cube's field is computed from its own mass only (Sec. 5.2:
+    each box contributes its own structure).  A bundle uses the cube holding
+    its central ray; points up to one node spacing outside the cube's nodes
+    (the bundle's other rays near a face) take the end intervals' cubics."""
 
     def __init__(self, pos, mass, soft, L, rot, shift, cubes, n, n_int=2, mean_subtract=True):
         from . import MassField, replica_world

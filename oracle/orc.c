@@ -324,7 +324,7 @@ static void prep_free(prep_field *pf)
  *   phi(r)      = - mu_G sum_p m_p (|r - x_p|^2 + eps_p^2)^(-1/2)
  *   grad phi(r) =   mu_G sum_p m_p (r - x_p) (|r - x_p|^2 + eps_p^2)^(-3/2)
  * For mean-subtracted boxes the field of the replica's uniform mean density
- * is removed (Sec. 3.3, "the mean matter density is then subtracted off"). */
+ * is removed (Sec. 3.3: the mean density is subtracted from the field). */
 static void field_eval(const orc_field *f, const prep_field *pf, int rep, const double *r,
                        double out[4], double *npairs)
 {

@@ -4,8 +4,8 @@
 //   1. cloud-in-cell assignment of the particle masses to n^3 nodes, summed in
 //      64-bit fixed point with integer atomics (order-independent, so the
 //      node masses are bit-reproducible);
-//   2. optional subtraction of the mean node mass ("the mean matter density
-//      is then subtracted off");
+//   2. optional subtraction of the mean node mass (Sec. 3.3 removes the mean
+//      density);
 //   3. phi and grad phi on the nodes: the zero-padded (2n)^3 FFT convolution
 //      of the node masses with the Plummer kernels (Eqs. psi, derivs with
 //      phi = a psi), by cuFFT (double precision, real-to-complex);
