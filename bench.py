@@ -162,11 +162,15 @@ def run_cones(args):
     return 0
 
 
-# App. B evaluation of one ray on the mixed path: 2 n_int = 4 node lines per
-# transverse axis, two nodes per x3 line, eight FP32 numbers per node
-GRID_BYTES_PER_RAY = 4 * 4 * 2 * 8 * 4
-GRID_ROOFLINE_NOTE = ("algorithmic bytes = the FP32 node records one ray's interpolation reads (1 KB); "
-                      "neighbouring rays share them, so most reads hit L1/L2")
+# App. B evaluation of one ray on the mixed path (n_int = 2), in FP32
+# operations: per field, 16 x3-line cubics from two nodes and their second
+# derivatives (8 fused multiply-adds each) and the x2 and x1 weight sums
+# (16 + 4 FMAs); the weight vectors (~50 operations) are shared by the four
+# fields.  2 FLOP per FMA.
+GRID_FLOPS_PER_RAY = 4 * 2 * (16 * 8 + 16 + 4) + 100
+GRID_ROOFLINE_NOTE = ("k_grid_eval32 gathers its node records mostly from L1/L2 and is bound by that latency, "
+                      "neither by HBM nor by the FP32 pipe (low frac); a trace's own bound on the grid path is "
+                      "the FP64 integrator stage")
 
 
 def run_grid(args):
@@ -242,13 +246,7 @@ def run_grid(args):
     mu64 = c64.trace(0, cfg["z_s"], cfg["theta"], **kw)["mu"]
     dmu64 = float(np.max(np.abs(mu_grid / mu64 - 1)))
     per_launch_s = eval_ms / 1e3 / max(1, eval_launches)
-    bytes_per_launch = nb * (1 + cfg["n_ring"]) * GRID_BYTES_PER_RAY
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs") or 6800.0
+    flops_per_launch = nb * (1 + cfg["n_ring"]) * GRID_FLOPS_PER_RAY
     out = {"metric": "ray bundles/s (grid path)", "value": nb * args.steps / dev_s, "unit": "bundles/s",
            "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dev_s / args.steps,
            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
@@ -256,8 +254,8 @@ def run_grid(args):
                       "bundles": nb, "rk4_steps": cfg["n_steps"], "l2": "256 MB buffer written between timed steps"},
            "grid_build_s": build_s,
            "field_evals_per_s": evals / dev_s,
-           "roofline": {"bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9, "peak": hbm,
-                        "unit": "GB/s", "frac": bytes_per_launch / per_launch_s / 1e9 / hbm, "traffic": None,
+           "roofline": {"bound": "alu", "achieved": flops_per_launch / per_launch_s / 1e12, "peak": FP32_PEAK / 1e12,
+                        "unit": "TFLOP/s", "frac": flops_per_launch / per_launch_s / FP32_PEAK, "traffic": None,
                         "kernel": "k_grid_eval32", "avg_launch_ms": per_launch_s * 1e3,
                         "note": GRID_ROOFLINE_NOTE},
            "grid_vs_direct_sum": {"median_abs_dmu_over_mu": float(np.median(dmu)),
@@ -332,13 +330,7 @@ def run_prism(args):
     mu64 = c64.trace(0, cfg["z_s"], cfg["theta"][:k], **kw)["mu"]
     dmu64 = float(np.max(np.abs(res[:k, 0] / mu64 - 1)))
     per_launch_s = eval_ms / 1e3 / max(1, eval_launches)
-    bytes_per_launch = nb * (1 + cfg["n_ring"]) * GRID_BYTES_PER_RAY
-    peaks = {}
-    try:
-        peaks = json.load(open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "MEASURED_PEAKS.json")))
-    except Exception:
-        pass
-    hbm = peaks.get("hbm_gbs") or 6800.0
+    flops_per_launch = nb * (1 + cfg["n_ring"]) * GRID_FLOPS_PER_RAY
     out = {"metric": "ray bundles/s (grid path, replicated box)", "value": nb * args.steps / dev_s,
            "unit": "bundles/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
@@ -350,8 +342,8 @@ def run_prism(args):
                       "l2": "30 GB of cube grids, larger than L2"},
            "grid_build_s": build_s,
            "field_evals_per_s": evals / dev_s,
-           "roofline": {"bound": "hbm", "achieved": bytes_per_launch / per_launch_s / 1e9, "peak": hbm,
-                        "unit": "GB/s", "frac": bytes_per_launch / per_launch_s / 1e9 / hbm, "traffic": None,
+           "roofline": {"bound": "alu", "achieved": flops_per_launch / per_launch_s / 1e12, "peak": FP32_PEAK / 1e12,
+                        "unit": "TFLOP/s", "frac": flops_per_launch / per_launch_s / FP32_PEAK, "traffic": None,
                         "kernel": "k_grid_eval32", "avg_launch_ms": per_launch_s * 1e3,
                         "note": GRID_ROOFLINE_NOTE},
            "mixed_vs_fp64_grid": {"bundles": k, "max_abs_dmu_over_mu": dmu64},
@@ -843,7 +835,7 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=1, variant=args.variant)
+    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=0 if args.no_tune else 1, variant=args.variant)
     ctx.set_cosmology(*cfg["cosmo"])
     load_box(ctx, 0, cfg)
     d_theta = torch.from_numpy(np.ascontiguousarray(theta)).to(dev)
@@ -1150,6 +1142,7 @@ def main():
     ap.add_argument("--ref-bundles", type=int, default=0, help="reference arm: bundles per step (0: one per core)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cones", action="store_true")
+    ap.add_argument("--no-tune", action="store_true", help="profiling: the default launch shape, no autotuning")
     ap.add_argument("--cone-warmup", type=int, default=2)
     ap.add_argument("--cone-runs", type=int, default=2)
     # auxiliary workloads

@@ -753,8 +753,9 @@ __device__ __forceinline__ void bundle2_block_sum(const DevField &f, const doubl
     }
 }
 
+// bounded for 512 resident threads per SM (128 registers, no spills)
 template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS>
-__global__ void __launch_bounds__(NT, 384 / NT) k_force_bundle2(ForceArgs A)
+__global__ void __launch_bounds__(NT, 512 / NT) k_force_bundle2(ForceArgs A)
 {
     if (A.gate && *A.gate == 0ull) return;
     __shared__ float4 s_a[kTile];
@@ -1056,8 +1057,8 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     cluster.sync();  // no block leaves while the others read its shared memory
 }
 
-// TPSM: resident threads per SM the register allocation is bounded for (384:
-// 168 registers, with some spilling; 256: no spills)
+// TPSM: resident threads per SM the register allocation is bounded for (512:
+// 128 registers with 16 bytes of spills)
 template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM, int CL>
 __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
 {

@@ -27,12 +27,15 @@ static cudaError_t go_one(const ForceArgs &A, dim3 grid, cudaStream_t st)
     return cudaLaunchKernelEx(&cfg, k_force_bundle2x<NT, 4, REPL, PEPS, UMASS, T, CL>, A);
 }
 
-// 64-thread blocks are bounded for 6 blocks per SM (168 registers), 128-thread
-// blocks for 2 (no spills): the tuner times both register regimes
+// Both block sizes are bounded for 512 resident threads per SM (128
+// registers, 16 bytes of spills): four warps per scheduler hide the FP32
+// pipe's dependency latencies better than the 168-register (384 threads) and
+// 170-register (256 threads) allocations, 1.5-4 % faster per launch on the
+// 2^24-particle box
 template <int NT, bool UMASS, int CL>
 static cudaError_t go_bundle2x(const ForceArgs &A, dim3 grid, cudaStream_t st)
 {
-    constexpr int T = NT == 64 ? 384 : 256;
+    constexpr int T = 512;
     const bool repl = A.f.replicated != 0, peps = A.f.eps2 != nullptr;
     if (repl && peps) return go_one<NT, UMASS, true, true, T, CL>(A, grid, st);
     if (repl) return go_one<NT, UMASS, true, false, T, CL>(A, grid, st);
