@@ -67,11 +67,11 @@ PEAK64_BASIS = "152 SM x 2 FP64 lanes x 2 x 2070 MHz (derived; nominal GB300 FP6
 HIST = dict(bins=200, mu_min=0.5, mu_max=5.0)
 KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "k_force_bundle", 4: "k_force_bundle2",
                 5: "k_force_bundle2x"}
-# dram__bytes_read.sum + dram__bytes_write.sum per pair-sum launch, from ncu
-# captures of the kernel named (summaries under profiles/), keyed by
-# (workload, kernel, threads per block); scaled from the captured case to
-# the full launch as those summaries state.  A shape not listed reports null.
-PROFILED_DRAM_BYTES = {}
+# dram__bytes_read.sum + dram__bytes_write.sum per pair-sum launch, from an ncu
+# capture of that very launch (one metric pass on the full-size headline
+# stage; profiles/dram_k_force_bundle2x_box2e24_full.md), keyed by (workload,
+# kernel, threads per block, splits).  A shape not listed reports null.
+PROFILED_DRAM_BYTES = {("c5", "k_force_bundle2x", 128, 2): 7818983424 + 442632704}
 C5_NAME = "box_2e24p_200mpch_zs1_1048576b_uniform1000_rk4stage"
 
 
@@ -472,21 +472,25 @@ def run_box(args):
 
 
 def run_multiplane(args):
-    """The comparison of Sec. 5.4 on the 2^21-particle box (z_s = 0.5): the
-    multiple lens-plane system (one plane per replica at its centre, Sec. 3.1)
-    on all 65,536 bundles, timed as the metric (one step = one multi-plane
-    trace of every bundle: plane table, deflection pair sums, updates,
-    reducer); then the 3D trace (1000 uniform RK4 steps) on the first
-    --mp-3d-bundles bundles of the same grid, and both methods' muPDF and
-    shear statistics on those bundles (<mu>_w, sigma_w, |gamma|)."""
+    """The comparison of Sec. 5.4 on the sampling region of Sec. 5.2: 256^3
+    particles in a 50/h Mpc box replicated 28 times to z_s = 0.5, 176^2
+    bundles inside the prism.  The multiple lens-plane system (one plane per
+    replica at its centre, direct-sum deflections of the projected particles,
+    Sec. 3.1) runs on every bundle and is the timed metric (one step = one
+    multi-plane trace of every bundle).  Beside it, on the same bundles: the
+    3D trace on the paper's own grid path (each replica's prism in 8 cubes of
+    128^3 nodes, n_int = 2, 1000 uniform RK4 steps), and on the first
+    --mp-3d-bundles bundles the 3D direct-sum trace at 1000 and 2000 steps and
+    the multi-plane system with 8 planes per replica.  Reported per method:
+    the muPDF's weighted mean and spread and the shear statistics."""
     import torch
 
     import inputs
     import paper_1110_4894_gb300 as P
-    cfg = inputs.config_c3(n_steps=1000)
+    cfg = inputs.config_prism(n_steps=1000)
     dev = torch.device("cuda", 0)
     nb = cfg["theta"].shape[0]
-    ctx = P.Context(0, precision=P.MIXED, autotune=1, time_kernels=1)
+    ctx = P.Context(0, precision=P.MIXED, autotune=1)
     ctx.set_cosmology(*cfg["cosmo"])
     ctx.load_particles(0, cfg["pos"], cfg["mass"], cfg["soft"], replicated=True, box_length=cfg["L"], rot=cfg["rot"],
                        shift=cfg["shift"], mean_subtract=True)
@@ -510,40 +514,53 @@ def run_multiplane(args):
             inter += ctx.stats()["interactions"]
     clocks = clk.summary()
     dev_s = sum(a.elapsed_time(b) for a, b in ev) / 1e3
-    mp_all = d_bout.view(nb, 6).cpu().numpy()
-    # one-to-one: the 3D trace and the lens planes on the same bundles
-    k = min(nb, args.mp_3d_bundles)
-    th = np.ascontiguousarray(cfg["theta"][:k])
-    t0 = time.perf_counter()
-    r3 = ctx.trace(0, cfg["z_s"], th, n_steps=cfg["n_steps"], schedule=0, **kw)
-    t3 = time.perf_counter() - t0
-    i3 = ctx.stats()["interactions"]
-    rm = ctx.multiplane(0, cfg["z_s"], th, slices=args.mp_slices, **kw)
+    res = d_bout.view(nb, 6).cpu().numpy()
+    mp = {"mu": res[:, 0], "gamma1": res[:, 2], "gamma2": res[:, 3], "flags": res[:, 5].astype(np.int32)}
 
-    def stats(r):
-        c, w, sc = ctx.histogram(r["mu"], r["flags"], **HIST)
-        gam = np.hypot(r["gamma1"], r["gamma2"])
-        wt = 1.0 / np.abs(r["mu"])
+    def stats(r, sel=slice(None)):
+        mu, fl = np.asarray(r["mu"])[sel], np.asarray(r["flags"])[sel]
+        c, w, sc = ctx.histogram(mu, fl, **HIST)
+        gam = np.hypot(np.asarray(r["gamma1"])[sel], np.asarray(r["gamma2"])[sel])
+        wt = 1.0 / np.abs(mu)
         return {"bundles": int(sc["n_used"]), "mean_w": sc["mean_w"], "sigma_w": sc["sigma_w"],
-                "mu_p5_p50_p95": [float(v) for v in np.percentile(r["mu"], [5, 50, 95])],
+                "mu_p5_p50_p95": [float(v) for v in np.percentile(mu, [5, 50, 95])],
                 "gamma_mean_w": float(np.sum(wt * gam) / np.sum(wt)),
                 "gamma_p50_p95": [float(v) for v in np.percentile(gam, [50, 95])]}
 
-    all_mp = {"mu": mp_all[:, 0], "gamma1": mp_all[:, 2], "gamma2": mp_all[:, 3],
-              "flags": mp_all[:, 5].astype(np.int32)}
+    # the 3D trace on the grid path: each replica's prism in 8 cubes of 128^3 nodes
+    cg = P.Context(0, precision=P.MIXED)
+    cg.set_cosmology(*cfg["cosmo"])
+    t0 = time.perf_counter()
+    cg.load_grid_box(0, cfg["pos"], cfg["mass"], cfg["soft"], cfg["L"], cfg["rot"], cfg["shift"], cfg["cubes"],
+                     cfg["grid_n"], n_int=2, mean_subtract=True)
+    build_s = time.perf_counter() - t0
+    g3 = cg.trace(0, cfg["z_s"], cfg["theta"], schedule=0, n_steps=cfg["n_steps"], **kw)
+    cg.close()
+    # the first k bundles: 3D direct sum at 1000 and 2000 steps, 8 planes per replica
+    k = min(nb, args.mp_3d_bundles)
+    th = np.ascontiguousarray(cfg["theta"][:k])
+    d3 = ctx.trace(0, cfg["z_s"], th, schedule=0, n_steps=1000, **kw)
+    d3b = ctx.trace(0, cfg["z_s"], th, schedule=0, n_steps=2000, **kw)
+    m8 = ctx.multiplane(0, cfg["z_s"], th, slices=8, **kw)
+    sub = slice(0, k)
     out = {"metric": "ray-particle interactions/s (multiple lens planes)", "value": inter / dev_s,
            "unit": "interactions/s", "n_gpus": 1, "steps": args.steps, "warmup": args.warmup,
            "ms_per_step": 1e3 * dev_s / args.steps, "higher_is_better": True, "scaling": "weak",
            "vs_baseline": None, "dtype": "f32", "data": "synthetic", "bundles_per_s": nb * args.steps / dev_s,
-           "config": {"workload": "box_2e21p_100mpch_zs0.5_65536b_planes%d" % args.mp_slices,
+           "config": {"workload": "prism_box_256cubed_50mpch_zs0.5_%db_planes%d" % (nb, args.mp_slices),
                       "particles": len(cfg["mass"]), "bundles": nb, "replicas": int(cfg["n_rep"]),
                       "planes_per_replica": args.mp_slices},
-           "multiplane_all_bundles": stats(all_mp),
-           "one_to_one": {"bundles": k, "rk4_steps_3d": cfg["n_steps"], "trace_3d_s": t3,
-                          "trace_3d_interactions_per_s": i3 / t3,
-                          "3d": stats(r3), "multiplane": stats(rm),
-                          "median_abs_mu_mp_over_mu_3d_minus_1": float(np.median(np.abs(rm["mu"] / r3["mu"] - 1))),
-                          "corr_mu_minus_1": float(np.corrcoef(rm["mu"] - 1, r3["mu"] - 1)[0, 1])},
+           "all_bundles": {"multiplane": stats(mp), "grid_3d_8x128": stats(g3), "grid_build_s": build_s,
+                           "median_abs_mu_mp_over_mu_grid_minus_1": float(np.median(np.abs(mp["mu"] / g3["mu"] - 1))),
+                           "corr_mu_minus_1_mp_grid": float(np.corrcoef(mp["mu"] - 1, g3["mu"] - 1)[0, 1])},
+           "first_bundles": {"bundles": k, "multiplane": stats(mp, sub), "multiplane_8_planes": stats(m8),
+                             "grid_3d_8x128": stats(g3, sub), "direct_3d_1000": stats(d3), "direct_3d_2000": stats(d3b),
+                             "median_abs_mu_direct_1000_over_2000_minus_1":
+                                 float(np.median(np.abs(d3["mu"] / d3b["mu"] - 1))),
+                             "median_abs_mu_mp_over_direct_2000_minus_1":
+                                 float(np.median(np.abs(mp["mu"][sub] / d3b["mu"] - 1))),
+                             "median_abs_mu_grid_over_direct_2000_minus_1":
+                                 float(np.median(np.abs(g3["mu"][sub] / d3b["mu"] - 1)))},
            "clocks": clocks}
     print(json.dumps(out))
     return 0
@@ -835,7 +852,8 @@ def run_ours(args):
             torch.distributed.barrier()
         torch.cuda.synchronize(dev)
 
-    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=0 if args.no_tune else 1, variant=args.variant)
+    ctx = P.Context(local, precision=P.MIXED, time_kernels=1, autotune=0 if args.no_tune else 1, variant=args.variant,
+                    threads_per_block=args.tpb, splits=args.splits)
     ctx.set_cosmology(*cfg["cosmo"])
     load_box(ctx, 0, cfg)
     d_theta = torch.from_numpy(np.ascontiguousarray(theta)).to(dev)
@@ -1130,7 +1148,7 @@ def main():
     ap.add_argument("--workload", default="c5", choices=["c5", "nfw", "cones", "grid", "born", "box3", "box5",
                                                           "prism", "multiplane"])
     ap.add_argument("--mp-slices", type=int, default=1, help="multiplane: planes per replica")
-    ap.add_argument("--mp-3d-bundles", type=int, default=4096, help="multiplane: bundles also traced in 3D")
+    ap.add_argument("--mp-3d-bundles", type=int, default=256, help="multiplane: bundles also traced in 3D")
     ap.add_argument("--table-steps", type=int, default=1000, help="RK4 steps of the headline trace's table")
     ap.add_argument("--box-particles", type=int, default=2 ** 24, help="checks only: a smaller headline box")
     ap.add_argument("--bundles", type=int, default=0, help="checks only: trace the first bundles of the grid")
@@ -1143,6 +1161,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-cones", action="store_true")
     ap.add_argument("--no-tune", action="store_true", help="profiling: the default launch shape, no autotuning")
+    ap.add_argument("--tpb", type=int, default=0, help="profiling: pair-sum threads per block (0: tuned)")
+    ap.add_argument("--splits", type=int, default=0, help="profiling: pair-sum particle splits (0: tuned)")
     ap.add_argument("--cone-warmup", type=int, default=2)
     ap.add_argument("--cone-runs", type=int, default=2)
     # auxiliary workloads
