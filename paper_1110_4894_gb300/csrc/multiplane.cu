@@ -15,10 +15,11 @@
 // x -> x + (chi_next - chi) theta between planes: the multi-plane lens
 // equation of Sec. 3.1 in a flat universe.
 //
-// Per plane: k_mp_deflect, the FP32 two-dimensional pair sum over the
-// particles of the plane's slab (bundle-centric: the ring rays' separations
-// expanded about the central ray's, compensated sums per chunk, partial sums
-// per particle split), then k_mp_update in FP64 (split reduction, mean
+// Per plane: k_mp_deflect2 (rings of 4 and 8, two bundles per thread in
+// f32x2) or k_mp_deflect (other rings), the FP32 two-dimensional pair sum over
+// the particles of the plane's slab (bundle-centric: the ring rays'
+// separations expanded about the central ray's, compensated sums per chunk,
+// partial sums per particle split), then k_mp_update in FP64 (split reduction, mean
 // subtraction, deflection, propagation to the next plane).  The RT3D_FP64
 // context runs k_mp_deflect64 (all FP64) instead.  The bundle reducer of the
 // 3D trace fits the lens-map Jacobian at the source plane.
@@ -202,7 +203,7 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
                     if (blockIdx.x == 0) atomicAdd(A.count, 1ull);
                     v.x = (float)(g[0] - ax) * dlt;
                     v.y = (float)(g[1] - ay) * dlt;
-                    v.z = UMASS ? 1.0f : __int_as_float(pr.w);
+                    v.z = __int_as_float(pr.w);
                     v.w = PEPS ? f.eps2[pi] : f.eps2u;
                 }
             }
@@ -220,7 +221,7 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
                 const float r2 = fmaf(dx, dx, fmaf(dy, dy, p.w));
                 float w;
                 asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(w) : "f"(r2));
-                w *= p.z;
+                if (!UMASS) w *= p.z;
                 cx = fmaf(dx, w, cx);
                 cy = fmaf(dy, w, cy);
 #pragma unroll
@@ -228,7 +229,7 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
                     const float s2 = r2 + fmaf(ex2[k], dx, fmaf(ey2[k], dy, ee[k]));
                     float wk;
                     asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(wk) : "f"(s2));
-                    wk *= p.z;
+                    if (!UMASS) wk *= p.z;
                     gs[k] += wk;
                     gx[k] = fmaf(dx, wk, gx[k]);
                     gy[k] = fmaf(dy, wk, gy[k]);
@@ -257,6 +258,153 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
     const int64_t sn = (int64_t)blockIdx.y * NQ;
 #pragma unroll
     for (int q = 0; q < NQ; ++q) out[(sn + q) * A.n_b + b] = s_hl[q * kMpNT + tid];
+}
+
+// The same sums with two bundles per thread (rings of 4 and 8): bundles A =
+// b0 + tid and B = b0 + NT + tid form f32x2 pairs ray by ray, so every FP32
+// operation is one f32x2 instruction.  Particles are staged negated and
+// duplicated, (-x, -x, -y, -y) and (m, m, eps^2, eps^2), so that d = r - p is
+// one f32x2 add; a uniform-mass field skips the mass product (the update
+// applies it).  Per particle and bundle pair: 6 + 6 NRING f32x2 operations and
+// 2 (1 + NRING) reciprocals.  Same outputs and layout as k_mp_deflect.
+constexpr int kMp2NT = 64;
+
+// (rings of 4 bounded for 8 blocks per SM, 128 registers; rings of 8, whose
+// accumulators need more, for 4)
+template <int NRING, bool REPL, bool PEPS, bool UMASS>
+__global__ void __launch_bounds__(kMp2NT, NRING <= 4 ? 8 : 4) k_mp_deflect2(MPArgs A)
+{
+    constexpr int NR = NRING + 1;
+    constexpr int NQ = 2 + 3 * NRING;
+    const MPPlane P = A.pl[A.q];
+    if (!P.active) return;
+    __shared__ float4 s_a[kTile];
+    __shared__ float4 s_b[kTile];
+    __shared__ float2 s_hl[2 * NQ * kMp2NT];  // (hi, lo) of output q for the pair (A, B)
+    const DevField &f = A.f;
+    const int tid = threadIdx.x;
+    const int64_t b0 = (int64_t)blockIdx.x * 2 * kMp2NT;
+    const int64_t bb[2] = {b0 + tid, b0 + kMp2NT + tid};
+    const bool valid[2] = {bb[0] < A.n_b, bb[1] < A.n_b};
+    const int64_t n = A.n_rays;
+    const double chi_s = A.misc[0];
+    double o[3];
+    frame_origin(f, REPL ? P.rep : 0, o);
+    const int64_t ia = b0 * NR;  // anchor: the block's first central ray
+    const long long ax = anchor_q(A.x[ia], o[0], f.inv_delta);
+    const long long ay = anchor_q(A.x[n + ia], o[1], f.inv_delta);
+    float rc[2][2], e2[2][NRING][3];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        rc[h][0] = rc[h][1] = 1e30f;  // far sentinel: contributions vanish
+#pragma unroll
+        for (int k = 0; k < NRING; ++k) e2[h][k][0] = e2[h][k][1] = e2[h][k][2] = 0.f;
+        if (valid[h]) {
+            const int64_t ic = bb[h] * NR;
+            rc[h][0] = (float)(((A.x[ic] - o[0]) * f.inv_delta - (double)ax) * f.delta);
+            rc[h][1] = (float)(((A.x[n + ic] - o[1]) * f.inv_delta - (double)ay) * f.delta);
+#pragma unroll
+            for (int k = 0; k < NRING; ++k) {
+                const float ex = (float)(A.x[ic + 1 + k] - A.x[ic]), ey = (float)(A.x[n + ic + 1 + k] - A.x[n + ic]);
+                e2[h][k][0] = 2.f * ex;
+                e2[h][k][1] = 2.f * ey;
+                e2[h][k][2] = fmaf(ex, ex, ey * ey);
+            }
+        }
+    }
+    const float2 RX = make_float2(rc[0][0], rc[1][0]), RY = make_float2(rc[0][1], rc[1][1]);
+    float2 EX2[NRING], EY2[NRING], EE[NRING];
+#pragma unroll
+    for (int k = 0; k < NRING; ++k) {
+        EX2[k] = make_float2(e2[0][k][0], e2[1][k][0]);
+        EY2[k] = make_float2(e2[0][k][1], e2[1][k][1]);
+        EE[k] = make_float2(e2[0][k][2], e2[1][k][2]);
+    }
+    float2 *s_hi = s_hl, *s_lo = s_hl + NQ * kMp2NT;
+#pragma unroll
+    for (int q = 0; q < NQ; ++q) s_hi[q * kMp2NT + tid] = s_lo[q * kMp2NT + tid] = make_float2(0.f, 0.f);
+    const int64_t p0 = (int64_t)blockIdx.y * A.per_split;
+    const int64_t p1 = min(f.n, p0 + A.per_split);
+    const float dlt = (float)f.delta;
+    for (int64_t t0 = p0; t0 < p1; t0 += kTile) {
+        __syncthreads();
+        for (int qq = tid; qq < kTile; qq += kMp2NT) {
+            const int64_t pi = t0 + qq;
+            float x = -1e18f, y = -1e18f, m = 0.f, e = 0.f;
+            if (pi < p1) {
+                const int4 pr = f.part[pi];
+                long long g[3] = {pr.x, pr.y, pr.z};
+                if (REPL) replica_q(f, P.rep, pr.x, pr.y, pr.z, g);
+                const double x3 = (double)g[2] * f.delta + o[2];
+                if (on_plane(P, REPL ? 1 : 0, A.slices, x3, chi_s)) {
+                    if (blockIdx.x == 0) atomicAdd(A.count, 1ull);
+                    x = -(float)(g[0] - ax) * dlt;
+                    y = -(float)(g[1] - ay) * dlt;
+                    m = __int_as_float(pr.w);
+                    e = PEPS ? f.eps2[pi] : f.eps2u;
+                }
+            }
+            s_a[qq] = make_float4(x, x, y, y);
+            s_b[qq] = make_float4(m, m, e, e);
+        }
+        __syncthreads();
+        float2 cx = make_float2(0.f, 0.f), cy = cx, gx[NRING], gy[NRING], gs[NRING];
+#pragma unroll
+        for (int k = 0; k < NRING; ++k) gx[k] = gy[k] = gs[k] = make_float2(0.f, 0.f);
+#pragma unroll 1
+        for (int jj = 0; jj < kTile; ++jj) {
+            const float4 a = s_a[jj];
+            const float4 b = s_b[jj];
+            const float2 DX = __fadd2_rn(RX, make_float2(a.x, a.y));
+            const float2 DY = __fadd2_rn(RY, make_float2(a.z, a.w));
+            const float2 R2 = __ffma2_rn(DX, DX, __ffma2_rn(DY, DY, make_float2(b.z, b.w)));
+            float2 w;
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(w.x) : "f"(R2.x));
+            asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(w.y) : "f"(R2.y));
+            if (!UMASS) w = __fmul2_rn(w, make_float2(b.x, b.y));
+            cx = __ffma2_rn(DX, w, cx);
+            cy = __ffma2_rn(DY, w, cy);
+#pragma unroll
+            for (int k = 0; k < NRING; ++k) {
+                const float2 s2 = __fadd2_rn(R2, __ffma2_rn(EX2[k], DX, __ffma2_rn(EY2[k], DY, EE[k])));
+                float2 wk;
+                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(wk.x) : "f"(s2.x));
+                asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(wk.y) : "f"(s2.y));
+                if (!UMASS) wk = __fmul2_rn(wk, make_float2(b.x, b.y));
+                gs[k] = __fadd2_rn(gs[k], wk);
+                gx[k] = __ffma2_rn(DX, wk, gx[k]);
+                gy[k] = __ffma2_rn(DY, wk, gy[k]);
+            }
+        }
+        // merge the tile into the (hi, lo) sums of both bundles
+        float2 v[NQ];
+        v[0] = cx;
+        v[1] = cy;
+#pragma unroll
+        for (int k = 0; k < NRING; ++k) {
+            v[2 + 3 * k] = gx[k];
+            v[3 + 3 * k] = gy[k];
+            v[4 + 3 * k] = gs[k];
+        }
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            float2 hi = s_hi[q * kMp2NT + tid], lo = s_lo[q * kMp2NT + tid];
+            two_sum2_into(hi, lo, v[q]);
+            s_hi[q * kMp2NT + tid] = hi;
+            s_lo[q * kMp2NT + tid] = lo;
+        }
+    }
+    float2 *out = (float2 *)A.out;
+    const int64_t sn = (int64_t)blockIdx.y * NQ;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        if (!valid[h]) continue;
+#pragma unroll
+        for (int q = 0; q < NQ; ++q) {
+            const float2 hi = s_hi[q * kMp2NT + tid], lo = s_lo[q * kMp2NT + tid];
+            out[(sn + q) * A.n_b + bb[h]] = h ? make_float2(hi.y, lo.y) : make_float2(hi.x, lo.x);
+        }
+    }
 }
 
 // the all-FP64 twin: plain FP64 sums, every ray on its own (outputs per ray:
@@ -426,8 +574,13 @@ cudaError_t go_deflect(const MPArgs &A, int S, bool fp64, cudaStream_t st)
         dim3 grid((unsigned)((A.n_b + kMpNT64 - 1) / kMpNT64), (unsigned)S);
         k_mp_deflect64<NRING, REPL, PEPS><<<grid, kMpNT64, 0, st>>>(A);
     } else {
-        dim3 grid((unsigned)((A.n_b + kMpNT - 1) / kMpNT), (unsigned)S);
-        k_mp_deflect<NRING, REPL, PEPS, UMASS><<<grid, kMpNT, 0, st>>>(A);
+        if constexpr (NRING == 4 || NRING == 8) {  // two bundles per thread, f32x2
+            dim3 grid((unsigned)((A.n_b + 2 * kMp2NT - 1) / (2 * kMp2NT)), (unsigned)S);
+            k_mp_deflect2<NRING, REPL, PEPS, UMASS><<<grid, kMp2NT, 0, st>>>(A);
+        } else {
+            dim3 grid((unsigned)((A.n_b + kMpNT - 1) / kMpNT), (unsigned)S);
+            k_mp_deflect<NRING, REPL, PEPS, UMASS><<<grid, kMpNT, 0, st>>>(A);
+        }
     }
     return cudaGetLastError();
 }
