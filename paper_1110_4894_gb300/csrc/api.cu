@@ -20,7 +20,8 @@ cudaError_t dispatch_fp64(const ForceArgs &A, const ForceShape &sh, cudaStream_t
 cudaError_t dispatch_packed(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 cudaError_t dispatch_bundle(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
 cudaError_t dispatch_bundle2(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
-cudaError_t dispatch_bundle2x(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st);
+cudaError_t dispatch_bundle2x(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st,
+                              int *occ = nullptr);
 struct BatchArgs;
 
 // rays covered by one block of the pair-sum kernel of shape sh
@@ -547,6 +548,53 @@ extern "C" int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const
     return RT3D_OK;
 }
 
+// resident blocks per SM of shape sh's pair-sum kernel: queried for the
+// two-bundle kernel (its launch bounds and shared memory set it), about five
+// blocks of 128 threads for the others
+static int resident_blocks(const DevField &f, const ForceShape &sh)
+{
+    if (sh.variant == 5) {
+        ForceArgs A{};
+        A.f = f;
+        A.n = rays_per_block(sh);
+        ForceShape q = sh;
+        q.splits = q.cl;
+        int occ = 0;
+        if (dispatch_bundle2x(A, q, q.umass != 0, nullptr, &occ) == cudaSuccess && occ > 0) return occ;
+    }
+    return std::max(1, 640 / sh.NT);
+}
+
+// Particle splits for a launch of nrb ray blocks: about `waves` waves of
+// resident blocks (wave = blocks the device holds at once), whole tiles per
+// split.  A last wave that is only part full leaves SMs idle at the end of the
+// launch, so up to twice that count the first split count whose blocks fill
+// their last wave to 99 % is taken (else the fullest).
+static int splits_for(int64_t nrb, int64_t wave, double waves, int tiles)
+{
+    auto balanced = [&](int64_t s) {
+        s = std::max<int64_t>(1, std::min<int64_t>(s, tiles));
+        const int64_t tps = (tiles + s - 1) / s;
+        return (int)((tiles + tps - 1) / tps);
+    };
+    auto fill = [&](int s) {
+        const int64_t b = nrb * s;
+        return (double)b / (double)(((b + wave - 1) / wave) * wave);
+    };
+    const int s0 = balanced((int64_t)std::ceil(waves * (double)wave / (double)nrb));
+    int best = s0;
+    double bf = fill(s0);
+    for (int s = s0 + 1; s <= std::min(2 * s0, tiles) && bf < 0.99; ++s) {
+        const int sb = balanced(s);
+        const double fb = fill(sb);
+        if (fb > bf + 1e-12) {
+            best = sb;
+            bf = fb;
+        }
+    }
+    return best;
+}
+
 // a clustered shape needs whole clusters along the splits; splits past the
 // particles are empty and add zeros
 static void round_to_clusters(ForceShape &sh)
@@ -587,20 +635,18 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
     }
     const int64_t per_block = rays_per_block(sh);
     const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
+    const int tiles = force_max_splits(sh, n_particles);
     int S;
     if (ctx->opt.splits > 0) {
-        S = ctx->opt.splits;
+        S = std::min(ctx->opt.splits, tiles);
+        // balance: whole tiles per split, then the number of splits actually used
+        const int64_t tps = (tiles + S - 1) / S;
+        S = (int)((tiles + tps - 1) / tps);
     } else {
-        // about five waves of resident blocks (SMs x ~5 blocks): many
-        // small blocks balance the SMs better than one exact wave
-        const int64_t target = (int64_t)ctx->n_sm * 5 * 5;
-        S = (int)std::max<int64_t>(1, (target + nrb - 1) / nrb);
+        // about five waves of resident blocks: many small blocks balance the
+        // SMs better than one exact wave
+        S = splits_for(nrb, (int64_t)ctx->n_sm * resident_blocks(f, sh), 5.0, tiles);
     }
-    const int tiles = force_max_splits(sh, n_particles);
-    S = std::min(S, tiles);
-    // balance: whole tiles per split, then the number of splits actually used
-    const int64_t tps = (tiles + S - 1) / S;
-    S = (int)((tiles + tps - 1) / tps);
     sh.splits = std::max(1, S);
     // the expanded two-bundle kernel can add groups of 4 splits in a cluster
     // (off unless asked for: measured slower on the NFW workload, see the tuner)
@@ -656,16 +702,13 @@ static int ilog2(int64_t v)
     return l;
 }
 
-static ForceShape with_splits(const rt3d_ctx *ctx, ForceShape sh, int64_t n_points, int64_t n_particles, int waves)
+static ForceShape with_splits(const rt3d_ctx *ctx, const DevField &f, ForceShape sh, int64_t n_points,
+                              int64_t n_particles, int waves)
 {
     const int64_t per_block = rays_per_block(sh);
     const int64_t nrb = std::max<int64_t>(1, (n_points + per_block - 1) / per_block);
-    const int64_t slots = (int64_t)ctx->n_sm * std::max(1, 640 / sh.NT);
-    int S = (int)std::max<int64_t>(1, (waves * slots + nrb - 1) / nrb);
-    const int tiles = force_max_splits(sh, n_particles);
-    S = std::min(S, tiles);
-    const int64_t tps = (tiles + S - 1) / S;
-    sh.splits = (int)std::max<int64_t>(1, (tiles + tps - 1) / tps);
+    const int64_t wave = (int64_t)ctx->n_sm * resident_blocks(f, sh);
+    sh.splits = splits_for(nrb, wave, (double)waves, force_max_splits(sh, n_particles));
     round_to_clusters(sh);
     return sh;
 }
@@ -682,7 +725,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
                                      ilog2(n), ilog2(std::max<int64_t>(1, fs.n)));
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end()) {
-        out = with_splits(ctx, it->second, n, fs.n, it->second.splits);  // splits slot holds the wave count
+        out = with_splits(ctx, fs.df, it->second, n, fs.n, it->second.splits);  // splits slot holds the wave count
         return RT3D_OK;
     }
     // Launches beyond 2^37 interactions (~50 ms) are timed on a proxy: the
@@ -712,7 +755,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     const bool bundles = base.variant >= 3;
     const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 9 : 3) : 4);
     for (int c = 0; c < nrn; ++c)
-        for (int w : {2, 3, 5, 8}) {
+        for (int w : {2, 3, 5, 8, 16}) {
             ForceShape s = base;
             // a requested bundle kernel (or cluster size) is tuned over its own shapes only
             if (bundles && ctx->opt.variant >= 3 && rnb[c][0] != base.variant) continue;
@@ -727,7 +770,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
                 s.R = p[0];
                 s.NT = p[1];
             }
-            s = with_splits(ctx, s, n_t, dft.n, w);
+            s = with_splits(ctx, dft, s, n_t, dft.n, w);
             bool dup = false;  // the same launch under another wave count
             for (const auto &c2 : cand)
                 dup |= c2.variant == s.variant && c2.R == s.R && c2.NT == s.NT && c2.cl == s.cl && c2.splits == s.splits;
@@ -767,7 +810,7 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     ForceShape keep = cand[bi];
     keep.splits = waves[bi];
     ctx->tuned[key] = keep;
-    out = n_t == n && dft.n == fs.df.n ? cand[bi] : with_splits(ctx, keep, n, fs.n, waves[bi]);
+    out = n_t == n && dft.n == fs.df.n ? cand[bi] : with_splits(ctx, fs.df, keep, n, fs.n, waves[bi]);
     return RT3D_OK;
 }
 

@@ -124,8 +124,8 @@ __device__ __forceinline__ void batch_item(const BatchCone &C, int4 item, int g,
     if constexpr (MODE == 5) {
         const int64_t b0 = (int64_t)item.y * 2 * NT;
 #define RT3D_XITEM(R_, E_, U_)                                                                                   \
-    bundle2x_block_sum<NT, 4, R_, E_, U_, 1>(C.f, px, py, pz, rep, C.rs.n_b, C.rs.n_rays, b0, p0, p1, item.z,      \
-                                             C.partials, s_a, s_b, (float *)s_e, s_hl)
+    bundle2x_block_sum<NT, 4, R_, E_, U_, 1, false>(C.f, px, py, pz, rep, C.rs.n_b, C.rs.n_rays, b0, p0, p1,      \
+                                                    item.z, C.partials, s_a, s_b, (float *)s_e, s_hl)
         switch (C.flags) {
         case 0: RT3D_XITEM(false, false, false); break;
         case 1: RT3D_XITEM(true, false, false); break;

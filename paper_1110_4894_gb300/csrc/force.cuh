@@ -780,10 +780,14 @@ __global__ void __launch_bounds__(NT, 512 / NT) k_force_bundle2(ForceArgs A)
 // ring ray adds a three-FMA correction (its own rounding is one add), and the
 // ring gradient splits into a sum along d_c plus e_k times a positive scalar
 // sum S_k, combined once per block.  Per particle and pair of bundles this is
-// 56 f32x2 operations for 10 interactions (the unexpanded kernel: 60).
+// 52 f32x2 operations for 10 interactions (the unexpanded kernel: 56).
 // (Taking 1/r^2 from MUFU rcp instead of rsqrt^2 saves 5 more but was
 // measured 26 % slower: the MUFU pipe then limits.)
-template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int CL>
+// AHEAD: read the next particle's records one iteration ahead, so that the
+// shared-memory latency overlaps the current particle's arithmetic (s_a and
+// s_b then hold kTile + 1 records).  It pays in the single-trace kernel;
+// the persistent batched kernel runs faster without it.
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int CL, bool AHEAD = true>
 __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const double *__restrict__ px,
                                                    const double *__restrict__ py, const double *__restrict__ pz,
                                                    const int *__restrict__ rep, int64_t n_b, int64_t n_rays,
@@ -886,10 +890,23 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
                 for (int g = 0; g < NR; ++g) cx[g] = cy[g] = cz[g] = make_float2(0.f, 0.f);
 #pragma unroll
                 for (int k = 0; k < NRING; ++k) cs[k] = make_float2(0.f, 0.f);
+                float4 a_nx, b_nx;  // read-ahead registers (AHEAD)
+                if constexpr (AHEAD) {
+                    a_nx = s_a[c0];
+                    b_nx = s_b[c0];
+                }
 #pragma unroll 1
                 for (int jj = c0; jj < c0 + kChunk2; ++jj) {
-                    const float4 a = s_a[jj];
-                    const float4 b = s_b[jj];
+                    float4 a, b;
+                    if constexpr (AHEAD) {
+                        a = a_nx;
+                        b = b_nx;
+                        a_nx = s_a[jj + 1];
+                        b_nx = s_b[jj + 1];
+                    } else {
+                        a = s_a[jj];
+                        b = s_b[jj];
+                    }
                     const float2 E2 = PEPS ? make_float2(s_e[jj], s_e[jj]) : E2u;
                     const float2 M2 = make_float2(b.z, b.w);
                     const float2 DX = __fadd2_rn(make_float2(a.x, a.y), NX);
@@ -1057,14 +1074,14 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     cluster.sync();  // no block leaves while the others read its shared memory
 }
 
-// TPSM: resident threads per SM the register allocation is bounded for (512:
-// 128 registers with 16 bytes of spills)
+// TPSM: resident threads per SM the register allocation is bounded for (384:
+// 168 registers, no spills)
 template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM, int CL>
 __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
 {
     if (A.gate && *A.gate == 0ull) return;
-    __shared__ float4 s_a[kTile];
-    __shared__ float4 s_b[kTile];
+    __shared__ float4 s_a[kTile + 1];  // + 1: the particle loop reads one record ahead
+    __shared__ float4 s_b[kTile + 1];
     __shared__ float s_e[PEPS ? kTile : 1];
     __shared__ float2 s_hl[2 * ((NRING + 1) * 3 + NRING) * NT];
     const int64_t n_b = A.n / (NRING + 1);
@@ -1098,7 +1115,7 @@ template <int R, int NT, bool REPL, bool PEPS>
 __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
 {
     if (A.gate && *A.gate == 0ull) return;
-    __shared__ double4 s_p[kTile64];
+    __shared__ double4_16a s_p[kTile64];
     __shared__ double s_e[PEPS ? kTile64 : 1];
     const DevField &f = A.f;
     const int tid = threadIdx.x;
@@ -1136,13 +1153,13 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
             __syncthreads();
             for (int q = tid; q < kTile64; q += NT) {
                 const int64_t pi = t0 + q;
-                double4 v = make_double4(1e100, 1e100, 1e100, 0.0);
+                double4_16a v = make_double4_16a(1e100, 1e100, 1e100, 0.0);
                 double e2 = 0.0;
                 if (pi < p1) {
                     const int4 pr = f.part[pi];
                     long long qq[3] = {pr.x, pr.y, pr.z};
                     if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
-                    v = make_double4((double)(qq[0] - ax) * f.delta, (double)(qq[1] - ay) * f.delta,
+                    v = make_double4_16a((double)(qq[0] - ax) * f.delta, (double)(qq[1] - ay) * f.delta,
                                      (double)(qq[2] - az) * f.delta, f.m64[pi]);
                     if (PEPS) e2 = f.eps2_64[pi];
                 }
@@ -1152,7 +1169,7 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
             __syncthreads();
 #pragma unroll 4
             for (int jj = 0; jj < kTile64; ++jj) {
-                const double4 p = s_p[jj];
+                const double4_16a p = s_p[jj];
                 const double e2 = PEPS ? s_e[jj] : f.eps2u64;
 #pragma unroll
                 for (int k = 0; k < R; ++k) {

@@ -40,11 +40,64 @@ struct MPPlane {
     double chi, zp1, thick, lo, hi, next_chi;
     double a, b, d;  // the plane's replica / field spans [a, b); slab = floor((x3 - a) / d)
     int active, rep, slice, pad;
+    long long qlo, qhi;  // grid z-coordinates (plane's frame) on the plane: [qlo, qhi]
 };
 
+// slab rule of a particle at world x3 against plane p, split in two
+// predicates that are monotone in x3: below (x3 before the slab, or before
+// the replica or the observer) and above (past the slab, the replica or the
+// source).  A particle is on the plane when it is neither.
+__device__ __forceinline__ double slab_index(const MPPlane &p, int slices, double x3)
+{
+    if (!(p.d > 0.0)) return 0.0;
+    return fmin(floor((x3 - p.a) / p.d), (double)(slices - 1));
+}
+__device__ __forceinline__ bool slab_below(const MPPlane &p, int replicated, int slices, double x3)
+{
+    return x3 < 0.0 || (replicated && x3 < p.a) || slab_index(p, slices, x3) < (double)p.slice;
+}
+__device__ __forceinline__ bool slab_above(const MPPlane &p, int replicated, int slices, double x3, double chi_s)
+{
+    return x3 >= chi_s || (replicated && x3 >= p.b) || slab_index(p, slices, x3) > (double)p.slice;
+}
+
+// world x3 of grid z-coordinate gz in a frame whose origin has z = o2
+__device__ __forceinline__ double grid_x3(long long gz, double delta, double o2) { return (double)gz * delta + o2; }
+
+// The grid z-coordinates whose particles lie on plane p form one interval:
+// x3 and the slab index never decrease as gz grows.  Both ends are found by
+// bisection over the 32-bit coordinate range with the slab rule itself, so
+// the pair sums test two integers per staged particle and select exactly the
+// particles the rule selects.
+__device__ void plane_q_range(MPPlane &p, int replicated, int slices, double chi_s, double delta, double o2)
+{
+    constexpr long long G0 = -2147483648LL, G1 = 2147483647LL;
+    long long lo = G1 + 1, hi = G0 - 1;  // empty
+    if (!slab_below(p, replicated, slices, grid_x3(G1, delta, o2))) {
+        long long l = G0 - 1, h = G1;  // below(l) taken as true, below(h) false
+        while (h - l > 1) {
+            const long long m = l + (h - l) / 2;
+            if (slab_below(p, replicated, slices, grid_x3(m, delta, o2))) l = m;
+            else h = m;
+        }
+        lo = h;
+    }
+    if (!slab_above(p, replicated, slices, grid_x3(G0, delta, o2), chi_s)) {
+        long long l = G0, h = G1 + 1;  // above(l) false, above(h) taken as true
+        while (h - l > 1) {
+            const long long m = l + (h - l) / 2;
+            if (slab_above(p, replicated, slices, grid_x3(m, delta, o2), chi_s)) h = m;
+            else l = m;
+        }
+        hi = l;
+    }
+    p.qlo = lo;
+    p.qhi = hi;
+}
+
 // the plane table: chi_s in misc[0], the first plane's distance in misc[1]
-__global__ void k_mp_table(Cosmo c, double z_s, int replicated, double L, int slices, double a_iso, double b_iso,
-                           int n_pl, MPPlane *pl, double *misc)
+__global__ void k_mp_table(Cosmo c, DevField f, double z_s, int slices, double a_iso, double b_iso, int n_pl,
+                           MPPlane *pl, double *misc)
 {
     __shared__ double s_chi;
     if (threadIdx.x == 0) {
@@ -53,6 +106,8 @@ __global__ void k_mp_table(Cosmo c, double z_s, int replicated, double L, int sl
     }
     __syncthreads();
     const double chi_s = s_chi;
+    const int replicated = f.replicated;
+    const double L = f.L;
     for (int q = threadIdx.x; q < n_pl; q += blockDim.x) {
         const int j = q / slices, s = q % slices;
         double a, b;
@@ -83,6 +138,9 @@ __global__ void k_mp_table(Cosmo c, double z_s, int replicated, double L, int sl
         // an isolated field deflects nothing, so it may stay in the table
         p.active = (replicated || d > 0.0) ? (hi > lo) : (s == 0 && a >= 0.0 && a < chi_s);
         p.next_chi = chi_s;
+        double o[3];
+        frame_origin(f, replicated ? j : 0, o);
+        plane_q_range(p, replicated, slices, chi_s, f.delta, o[2]);
         pl[q] = p;
     }
     __syncthreads();
@@ -113,17 +171,6 @@ __global__ void k_mp_init(TraceParams tp, const double *__restrict__ theta, RayS
     rs.y[1 * n + i] = chi1 * ty;
     rs.y[2 * n + i] = tx;
     rs.y[3 * n + i] = ty;
-}
-
-// slab membership of a particle at world x3 on plane p (the same rule and
-// arithmetic as the plane table's slabs)
-__device__ __forceinline__ bool on_plane(const MPPlane &p, int replicated, int slices, double x3, double chi_s)
-{
-    if (x3 < 0.0 || x3 >= chi_s) return false;
-    if (replicated && (x3 < p.a || x3 >= p.b)) return false;
-    int s = p.d > 0.0 ? (int)floor((x3 - p.a) / p.d) : 0;
-    if (s >= slices) s = slices - 1;
-    return s == p.slice;
 }
 
 struct MPArgs {
@@ -159,7 +206,7 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
     const int64_t b0 = (int64_t)blockIdx.x * kMpNT, b = b0 + tid;
     const bool valid = b < A.n_b;
     const int64_t n = A.n_rays;
-    const double chi_s = A.misc[0];
+    unsigned n_on = 0;  // staged particles on the plane (block column 0 counts)
     double o[3];
     frame_origin(f, REPL ? P.rep : 0, o);
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
@@ -198,9 +245,8 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
                 const int4 pr = f.part[pi];
                 long long g[3] = {pr.x, pr.y, pr.z};
                 if (REPL) replica_q(f, P.rep, pr.x, pr.y, pr.z, g);
-                const double x3 = (double)g[2] * f.delta + o[2];
-                if (on_plane(P, REPL ? 1 : 0, A.slices, x3, chi_s)) {
-                    if (blockIdx.x == 0) atomicAdd(A.count, 1ull);
+                if (g[2] >= P.qlo && g[2] <= P.qhi) {
+                    ++n_on;
                     v.x = (float)(g[0] - ax) * dlt;
                     v.y = (float)(g[1] - ay) * dlt;
                     v.z = __int_as_float(pr.w);
@@ -253,6 +299,7 @@ __global__ void __launch_bounds__(kMpNT) k_mp_deflect(MPArgs A)
             }
         }
     }
+    if (blockIdx.x == 0 && n_on) atomicAdd(A.count, (unsigned long long)n_on);
     if (!valid) return;
     float2 *out = (float2 *)A.out;
     const int64_t sn = (int64_t)blockIdx.y * NQ;
@@ -278,8 +325,8 @@ __global__ void __launch_bounds__(kMp2NT, NRING <= 4 ? 8 : 4) k_mp_deflect2(MPAr
     constexpr int NQ = 2 + 3 * NRING;
     const MPPlane P = A.pl[A.q];
     if (!P.active) return;
-    __shared__ float4 s_a[kTile];
-    __shared__ float4 s_b[kTile];
+    __shared__ float4 s_a[kTile + 1];  // + 1: the particle loop reads one record ahead
+    __shared__ float4 s_b[kTile + 1];
     __shared__ float2 s_hl[2 * NQ * kMp2NT];  // (hi, lo) of output q for the pair (A, B)
     const DevField &f = A.f;
     const int tid = threadIdx.x;
@@ -287,7 +334,7 @@ __global__ void __launch_bounds__(kMp2NT, NRING <= 4 ? 8 : 4) k_mp_deflect2(MPAr
     const int64_t bb[2] = {b0 + tid, b0 + kMp2NT + tid};
     const bool valid[2] = {bb[0] < A.n_b, bb[1] < A.n_b};
     const int64_t n = A.n_rays;
-    const double chi_s = A.misc[0];
+    unsigned n_on = 0;  // staged particles on the plane (block column 0 counts)
     double o[3];
     frame_origin(f, REPL ? P.rep : 0, o);
     const int64_t ia = b0 * NR;  // anchor: the block's first central ray
@@ -335,9 +382,8 @@ __global__ void __launch_bounds__(kMp2NT, NRING <= 4 ? 8 : 4) k_mp_deflect2(MPAr
                 const int4 pr = f.part[pi];
                 long long g[3] = {pr.x, pr.y, pr.z};
                 if (REPL) replica_q(f, P.rep, pr.x, pr.y, pr.z, g);
-                const double x3 = (double)g[2] * f.delta + o[2];
-                if (on_plane(P, REPL ? 1 : 0, A.slices, x3, chi_s)) {
-                    if (blockIdx.x == 0) atomicAdd(A.count, 1ull);
+                if (g[2] >= P.qlo && g[2] <= P.qhi) {
+                    ++n_on;
                     x = -(float)(g[0] - ax) * dlt;
                     y = -(float)(g[1] - ay) * dlt;
                     m = __int_as_float(pr.w);
@@ -351,10 +397,16 @@ __global__ void __launch_bounds__(kMp2NT, NRING <= 4 ? 8 : 4) k_mp_deflect2(MPAr
         float2 cx = make_float2(0.f, 0.f), cy = cx, gx[NRING], gy[NRING], gs[NRING];
 #pragma unroll
         for (int k = 0; k < NRING; ++k) gx[k] = gy[k] = gs[k] = make_float2(0.f, 0.f);
+        // the next particle's records are read one iteration ahead (s_a and s_b
+        // hold kTile + 1 records), so the shared-memory latency overlaps the
+        // current particle's arithmetic
+        float4 a_nx = s_a[0], b_nx = s_b[0];
 #pragma unroll 1
         for (int jj = 0; jj < kTile; ++jj) {
-            const float4 a = s_a[jj];
-            const float4 b = s_b[jj];
+            const float4 a = a_nx;
+            const float4 b = b_nx;
+            a_nx = s_a[jj + 1];
+            b_nx = s_b[jj + 1];
             const float2 DX = __fadd2_rn(RX, make_float2(a.x, a.y));
             const float2 DY = __fadd2_rn(RY, make_float2(a.z, a.w));
             const float2 R2 = __ffma2_rn(DX, DX, __ffma2_rn(DY, DY, make_float2(b.z, b.w)));
@@ -394,6 +446,7 @@ __global__ void __launch_bounds__(kMp2NT, NRING <= 4 ? 8 : 4) k_mp_deflect2(MPAr
             s_lo[q * kMp2NT + tid] = lo;
         }
     }
+    if (blockIdx.x == 0 && n_on) atomicAdd(A.count, (unsigned long long)n_on);
     float2 *out = (float2 *)A.out;
     const int64_t sn = (int64_t)blockIdx.y * NQ;
 #pragma unroll
@@ -415,13 +468,13 @@ __global__ void __launch_bounds__(kMpNT64) k_mp_deflect64(MPArgs A)
     constexpr int NR = NRING + 1;
     const MPPlane P = A.pl[A.q];
     if (!P.active) return;
-    __shared__ double4 s_p[kTile64];
+    __shared__ double4_16a s_p[kTile64];
     const DevField &f = A.f;
     const int tid = threadIdx.x;
     const int64_t b = (int64_t)blockIdx.x * kMpNT64 + tid;
     const bool valid = b < A.n_b;
     const int64_t n = A.n_rays;
-    const double chi_s = A.misc[0];
+    unsigned n_on = 0;  // staged particles on the plane (block column 0 counts)
     double o[3];
     frame_origin(f, REPL ? P.rep : 0, o);
     double rx[NR], ry[NR], sx[NR], sy[NR];
@@ -437,15 +490,14 @@ __global__ void __launch_bounds__(kMpNT64) k_mp_deflect64(MPArgs A)
         __syncthreads();
         for (int qq = tid; qq < kTile64; qq += kMpNT64) {
             const int64_t pi = t0 + qq;
-            double4 v = make_double4(1e100, 1e100, 0.0, 0.0);
+            double4_16a v = make_double4_16a(1e100, 1e100, 0.0, 0.0);
             if (pi < p1) {
                 const int4 pr = f.part[pi];
                 long long g[3] = {pr.x, pr.y, pr.z};
                 if (REPL) replica_q(f, P.rep, pr.x, pr.y, pr.z, g);
-                const double x3 = (double)g[2] * f.delta + o[2];
-                if (on_plane(P, REPL ? 1 : 0, A.slices, x3, chi_s)) {
-                    if (blockIdx.x == 0) atomicAdd(A.count, 1ull);
-                    v = make_double4((double)g[0] * f.delta, (double)g[1] * f.delta, f.m64[pi],
+                if (g[2] >= P.qlo && g[2] <= P.qhi) {
+                    ++n_on;
+                    v = make_double4_16a((double)g[0] * f.delta, (double)g[1] * f.delta, f.m64[pi],
                                      PEPS ? f.eps2_64[pi] : f.eps2u64);
                 }
             }
@@ -454,7 +506,7 @@ __global__ void __launch_bounds__(kMpNT64) k_mp_deflect64(MPArgs A)
         __syncthreads();
 #pragma unroll 2
         for (int jj = 0; jj < kTile64; ++jj) {
-            const double4 p = s_p[jj];
+            const double4_16a p = s_p[jj];
 #pragma unroll
             for (int k = 0; k < NR; ++k) {
                 const double dx = rx[k] - p.x, dy = ry[k] - p.y;
@@ -464,6 +516,7 @@ __global__ void __launch_bounds__(kMpNT64) k_mp_deflect64(MPArgs A)
             }
         }
     }
+    if (blockIdx.x == 0 && n_on) atomicAdd(A.count, (unsigned long long)n_on);
     if (!valid) return;
     double *out = (double *)A.out;
     const int64_t sn = (int64_t)blockIdx.y * 2;
@@ -631,7 +684,7 @@ cudaError_t mp_run(const Cosmo &c, const DevField &f, double z_s, int slices, do
                    double *d_rout, cudaStream_t st)
 {
     MPPlane *pl = (MPPlane *)d_planes;
-    k_mp_table<<<1, 256, 0, st>>>(c, z_s, f.replicated, f.L, slices, x3_lo, x3_hi, n_pl, pl, misc);
+    k_mp_table<<<1, 256, 0, st>>>(c, f, z_s, slices, x3_lo, x3_hi, n_pl, pl, misc);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     const unsigned rb = (unsigned)((rs.n_rays + 255) / 256);
