@@ -71,7 +71,7 @@ KERNEL_NAMES = {0: "k_force_packed", 1: "k_force_mixed", 2: "k_force_fp64", 3: "
 # capture of that very launch (one metric pass on the full-size headline
 # stage; profiles/dram_k_force_bundle2x_box2e24_full.md), keyed by (workload,
 # kernel, threads per block, splits).  A shape not listed reports null.
-PROFILED_DRAM_BYTES = {("c5", "k_force_bundle2x", 128, 2): 7818983424 + 442632704}
+PROFILED_DRAM_BYTES = {("c5", "k_force_bundle2x", 128, 1): 7763856384 + 261923584}
 C5_NAME = "box_2e24p_200mpch_zs1_1048576b_uniform1000_rk4stage"
 
 
