@@ -75,10 +75,11 @@ typedef struct {
     double watchdog_s;     /* limit for the persistent kernel's grid-barrier waits; 0 = 120 s */
     int time_kernels;      /* 1: bracket every pair-sum launch with CUDA events (stats.force_ms) */
     int variant;           /* pair-sum kernel: 0 = automatic (bundle-centric FP32x2 for traces:
-                              5 for rings of 4, 3 otherwise; with autotune, the fastest of 3, 4, 5),
-                              1 = scalar FP32, 2 = packed FP32x2 per ray, 3 = one bundle per thread,
-                              4 = two bundles per thread (rings of 4), 5 = as 4 with the ring
-                              separations expanded about the central ray.  rt3d_trace_batch:
+                              5 for rings of 4 and 8, 3 otherwise; with autotune, the fastest of
+                              3, 4, 5), 1 = scalar FP32, 2 = packed FP32x2 per ray, 3 = one bundle
+                              per thread, 4 = two bundles per thread (rings of 4), 5 = two bundles
+                              per thread with the ring separations expanded about the central ray
+                              (rings of 4 and 8; rings of 8 in blocks of 64).  rt3d_trace_batch:
                               3 = bundle-centric items, 5 = expanded two-bundle items (64
                               threads; the default for rings of 4), 0 with autotune = the faster */
     int cluster;           /* variant 5: 4 = thread-block clusters of 4 splits add their partials in

@@ -619,14 +619,19 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
         sh.R = 2;
         sh.NT = 128;
     } else if ((ctx->opt.variant == 0 || ctx->opt.variant >= 3) && (group == 5 || group == 9)) {
-        // bundle-centric: two bundles per thread for rings of 4 (variant 5,
-        // the expanded separations, or 4), one per thread otherwise (3)
-        sh.variant = group == 5 ? (ctx->opt.variant == 3 || ctx->opt.variant == 4 ? ctx->opt.variant : 5) : 3;
+        // bundle-centric: two bundles per thread with the expanded separations
+        // (variant 5, rings of 4 and 8), without them (4, rings of 4), or one
+        // bundle per thread (3)
+        if (group == 5)
+            sh.variant = ctx->opt.variant == 3 || ctx->opt.variant == 4 ? ctx->opt.variant : 5;
+        else
+            sh.variant = ctx->opt.variant == 3 || ctx->opt.variant == 4 ? 3 : 5;
         sh.umass = f.uniform_mass ? 1 : 0;
         sh.R = group;
         const bool two = sh.variant == 4 || sh.variant == 5;
         sh.NT = ctx->opt.threads_per_block > 0 ? ctx->opt.threads_per_block : (two ? 64 : 128);
         if (two && sh.NT > 128) sh.NT = 128;
+        if (sh.variant == 5 && group == 9) sh.NT = 64;  // the ring-of-8 kernel's only block size
     } else {
         sh.variant = ctx->opt.variant == 1 ? 1 : 0;
         sh.umass = (sh.variant == 0 && f.uniform_mass) ? 1 : 0;
@@ -749,11 +754,12 @@ static int tuned_shape(rt3d_ctx *ctx, const FieldSlot &fs, const double *px, con
     const int rn[][2] = {{4, 128}, {4, 256}, {4, 64}, {8, 64}};
     const int rn64[][2] = {{2, 128}, {1, 128}};
     // bundle shapes: {variant, rays per bundle, threads per block, cluster size}
-    const int rnb[][4] = {{3, group, 128, 1}, {3, group, 64, 1}, {3, group, 256, 1}, {4, group, 64, 1},
-                          {4, group, 128, 1}, {5, group, 64, 1}, {5, group, 128, 1}, {5, group, 64, 4},
-                          {5, group, 128, 4}};
+    const int rnb4[][4] = {{3, 5, 128, 1}, {3, 5, 64, 1}, {3, 5, 256, 1}, {4, 5, 64, 1}, {4, 5, 128, 1},
+                           {5, 5, 64, 1}, {5, 5, 128, 1}, {5, 5, 64, 4}, {5, 5, 128, 4}};
+    const int rnb8[][4] = {{3, 9, 128, 1}, {3, 9, 64, 1}, {3, 9, 256, 1}, {5, 9, 64, 1}};
+    const int(*rnb)[4] = group == 5 ? rnb4 : rnb8;
     const bool bundles = base.variant >= 3;
-    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 9 : 3) : 4);
+    const int nrn = base.variant == 2 ? 2 : (bundles ? (group == 5 ? 9 : 4) : 4);
     for (int c = 0; c < nrn; ++c)
         for (int w : {2, 3, 5, 8, 16}) {
             ForceShape s = base;

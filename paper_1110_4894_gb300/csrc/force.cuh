@@ -1074,9 +1074,9 @@ __device__ __forceinline__ void bundle2x_block_sum(const DevField &f, const doub
     cluster.sync();  // no block leaves while the others read its shared memory
 }
 
-// TPSM: resident threads per SM the register allocation is bounded for (384:
-// 168 registers, no spills)
-template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM, int CL>
+// TPSM: resident threads per SM the register allocation is bounded for;
+// AHEAD: the particle loop's read-ahead (bundle2x_block_sum)
+template <int NT, int NRING, bool REPL, bool PEPS, bool UMASS, int TPSM, int CL, bool AHEAD = true>
 __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
 {
     if (A.gate && *A.gate == 0ull) return;
@@ -1089,7 +1089,7 @@ __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
     const int split = blockIdx.y;
     const int64_t p0 = (int64_t)split * A.per_split;
     const int64_t p1 = min(A.f.n, p0 + A.per_split);
-    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS, CL>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
+    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS, CL, AHEAD>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
                                                      (float2 *)A.out, s_a, s_b, s_e, s_hl);
 }
 

@@ -1,16 +1,16 @@
 // force_bundle2x.cu -- launch dispatch of the two-bundles-per-thread pair sum
-// with ring separations expanded about the central ray.
+// with ring separations expanded about the central ray (rings of 4 and 8).
 #include "force.cuh"
 
 namespace rt3d {
 
-template <int NT, bool UMASS, bool REPL, bool PEPS, int T, int CL>
+template <int NT, int NRING, bool UMASS, bool REPL, bool PEPS, int T, int CL, bool AHEAD>
 static cudaError_t go_one(const ForceArgs &A, dim3 grid, cudaStream_t st, int *occ)
 {
-    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k_force_bundle2x<NT, 4, REPL, PEPS, UMASS, T, CL>,
-                                                                  NT, 0);
+    const auto kern = k_force_bundle2x<NT, NRING, REPL, PEPS, UMASS, T, CL, AHEAD>;
+    if (occ) return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, kern, NT, 0);
     if (CL == 1) {
-        k_force_bundle2x<NT, 4, REPL, PEPS, UMASS, T, 1><<<grid, NT, 0, st>>>(A);
+        kern<<<grid, NT, 0, st>>>(A);
         return cudaGetLastError();
     }
     // thread-block clusters of CL consecutive splits of one bundle block
@@ -26,10 +26,20 @@ static cudaError_t go_one(const ForceArgs &A, dim3 grid, cudaStream_t st, int *o
     attr[0].val.clusterDim.z = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    return cudaLaunchKernelEx(&cfg, k_force_bundle2x<NT, 4, REPL, PEPS, UMASS, T, CL>, A);
+    return cudaLaunchKernelEx(&cfg, kern, A);
 }
 
-// Both block sizes are bounded for 384 resident threads per SM (168
+template <int NT, int NRING, bool UMASS, int T, int CL, bool AHEAD>
+static cudaError_t go_fields(const ForceArgs &A, dim3 grid, cudaStream_t st, int *occ)
+{
+    const bool repl = A.f.replicated != 0, peps = A.f.eps2 != nullptr;
+    if (repl && peps) return go_one<NT, NRING, UMASS, true, true, T, CL, AHEAD>(A, grid, st, occ);
+    if (repl) return go_one<NT, NRING, UMASS, true, false, T, CL, AHEAD>(A, grid, st, occ);
+    if (peps) return go_one<NT, NRING, UMASS, false, true, T, CL, AHEAD>(A, grid, st, occ);
+    return go_one<NT, NRING, UMASS, false, false, T, CL, AHEAD>(A, grid, st, occ);
+}
+
+// Rings of 4, both block sizes: bounded for 384 resident threads per SM (168
 // registers, no spills).  With the particle records read one iteration ahead,
 // three warps per scheduler keep the FP32 pipe busier than four at 128
 // registers, where the read-ahead spills (on the 2^24-particle box, 128-thread
@@ -38,22 +48,32 @@ static cudaError_t go_one(const ForceArgs &A, dim3 grid, cudaStream_t st, int *o
 template <int NT, bool UMASS, int CL>
 static cudaError_t go_bundle2x(const ForceArgs &A, dim3 grid, cudaStream_t st, int *occ)
 {
-    constexpr int T = 384;
-    const bool repl = A.f.replicated != 0, peps = A.f.eps2 != nullptr;
-    if (repl && peps) return go_one<NT, UMASS, true, true, T, CL>(A, grid, st, occ);
-    if (repl) return go_one<NT, UMASS, true, false, T, CL>(A, grid, st, occ);
-    if (peps) return go_one<NT, UMASS, false, true, T, CL>(A, grid, st, occ);
-    return go_one<NT, UMASS, false, false, T, CL>(A, grid, st, occ);
+    return go_fields<NT, 4, UMASS, 384, CL, true>(A, grid, st, occ);
 }
 
-// rings of 4: grid.x counts blocks of 2 NT bundles, grid.y the splits (a
-// multiple of sh.cl).  With occ set nothing is launched: *occ receives the
-// kernel's resident blocks per SM.
+// Rings of 8 (the paper's bundle of 8 rays around the central one): 64
+// threads, no clusters; the 35 compensated sums and 16 ring offsets per
+// bundle pair need about twice the registers of a ring of 4
+constexpr int kRing8Threads = 256;  // resident threads per SM the registers are bounded for
+constexpr bool kRing8Ahead = true;
+template <bool UMASS>
+static cudaError_t go_bundle2x8(const ForceArgs &A, dim3 grid, cudaStream_t st, int *occ)
+{
+    return go_fields<64, 8, UMASS, kRing8Threads, 1, kRing8Ahead>(A, grid, st, occ);
+}
+
+// rings of 4 (R = 5) or 8 (R = 9): grid.x counts blocks of 2 NT bundles,
+// grid.y the splits (a multiple of sh.cl).  With occ set nothing is launched:
+// *occ receives the kernel's resident blocks per SM.
 cudaError_t dispatch_bundle2x(const ForceArgs &A, const ForceShape &sh, bool umass, cudaStream_t st, int *occ)
 {
-    const int64_t n_b = A.n / 5;
+    if ((sh.R != 5 && sh.R != 9) || sh.splits % sh.cl != 0) return cudaErrorInvalidConfiguration;
+    const int64_t n_b = A.n / sh.R;
     const dim3 grid((unsigned)((n_b + 2 * sh.NT - 1) / (2 * sh.NT)), (unsigned)sh.splits);
-    if (sh.R != 5 || sh.splits % sh.cl != 0) return cudaErrorInvalidConfiguration;
+    if (sh.R == 9) {
+        if (sh.NT != 64 || sh.cl != 1) return cudaErrorInvalidConfiguration;
+        return umass ? go_bundle2x8<true>(A, grid, st, occ) : go_bundle2x8<false>(A, grid, st, occ);
+    }
     switch ((sh.NT * 2 + (umass ? 1 : 0)) * 8 + sh.cl) {
     case 128 * 8 + 1: return go_bundle2x<64, false, 1>(A, grid, st, occ);
     case 129 * 8 + 1: return go_bundle2x<64, true, 1>(A, grid, st, occ);

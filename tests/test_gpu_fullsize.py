@@ -51,6 +51,15 @@ def test_nfw_full_size_ring_of_eight_sampled(cosmo):
     assert np.array_equal(g["flags"][idx], o.flags)
     assert rel_mu(g["mu"][idx], o.mu).max() < 1e-4
     assert rel_alpha(g["rays"][idx], o).max() < 1e-5
+    # the two-bundle kernel with expanded separations on the same bundles
+    c5 = P.Context(0, precision=P.MIXED, autotune=0, variant=5)
+    c5.set_cosmology(*cfg["cosmo"])
+    gpu_load(c5, 0, cfg)
+    g5 = c5.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    assert c5.stats()["variant"] == 5
+    assert np.array_equal(g5["flags"][idx], o.flags)
+    assert rel_mu(g5["mu"][idx], o.mu).max() < 1e-4
+    assert rel_alpha(g5["rays"][idx], o).max() < 1e-5
     c64 = P.Context(0, precision=P.FP64)
     c64.set_cosmology(*cfg["cosmo"])
     gpu_load(c64, 0, cfg)

@@ -160,6 +160,26 @@ def test_c2_small_nfw(P, cosmo, precision, n_ring):
     assert st["interactions"] > 0
 
 
+@pytest.mark.parametrize("variant", [3, 5])
+@pytest.mark.parametrize("n_side", [4, 12])
+def test_ring_of_eight_kernels(P, cosmo, variant, n_side):
+    # the paper's 8-ray bundle through each pair-sum kernel that serves it:
+    # one bundle per thread (3) and two per thread with the expanded
+    # separations (5, blocks of 128 bundles: 16 bundles fill part of one
+    # block, 144 one and part of a second)
+    cfg = _c2_small(n_particles=6000, n_side=n_side, n_steps=120)
+    cfg["n_ring"] = 8
+    cfg["phase"] = 0.3
+    ctx = ctx_for(P, P.MIXED, variant=variant)
+    gpu_load(ctx, 0, cfg)
+    g = ctx.trace(0, cfg["z_s"], cfg["theta"], want_rays=True, **trace_kw(cfg))
+    assert ctx.stats()["variant"] == variant
+    o = run_oracle(cfg, cfg["theta"], cosmo)
+    assert np.array_equal(g["flags"], o.flags)
+    assert rel_mu(g["mu"], o.mu).max() < MU_GATE
+    assert rel_alpha(g["rays"], o).max() < ALPHA_GATE
+
+
 @pytest.mark.parametrize("precision", PRECISIONS)
 def test_box_replicas_mean_subtracted(P, cosmo, precision):
     b = _small_box()
