@@ -52,10 +52,13 @@ static cudaError_t go_bundle2x(const ForceArgs &A, dim3 grid, cudaStream_t st, i
 }
 
 // Rings of 8 (the paper's bundle of 8 rays around the central one): 64
-// threads, no clusters; the 35 compensated sums and 16 ring offsets per
-// bundle pair need about twice the registers of a ring of 4
-constexpr int kRing8Threads = 256;  // resident threads per SM the registers are bounded for
-constexpr bool kRing8Ahead = true;
+// threads, no clusters; the 35 compensated sums and 32 ring-offset registers
+// per bundle pair need about twice the registers of a ring of 4, so the
+// bound is 256 resident threads (255 registers; at 320 or 384 the allocation
+// falls to 168 and spills).  Without the read-ahead: 0.732 of the FP32 peak
+// against 0.723 with it on 65,536 bundles of the 2^24-particle box.
+constexpr int kRing8Threads = 256;
+constexpr bool kRing8Ahead = false;
 template <bool UMASS>
 static cudaError_t go_bundle2x8(const ForceArgs &A, dim3 grid, cudaStream_t st, int *occ)
 {
