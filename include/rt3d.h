@@ -82,9 +82,9 @@ typedef struct {
                               (rings of 4 and 8; rings of 8 in blocks of 64).  rt3d_trace_batch:
                               3 = bundle-centric items, 5 = expanded two-bundle items (64
                               threads; the default for rings of 4), 0 with autotune = the faster */
-    int cluster;           /* variant 5: 4 = thread-block clusters of 4 splits add their partials in
-                              distributed shared memory, 1 = no clusters, 0 = automatic (none unless
-                              the autotuner finds clusters faster) */
+    int cluster;           /* variant 5, rings of 4: 4 = thread-block clusters of 4 splits add their
+                              partials in distributed shared memory, 1 = no clusters, 0 = automatic
+                              (none unless the autotuner finds clusters faster) */
 } rt3d_options;
 
 /* Mass distribution layout.

@@ -655,7 +655,7 @@ static ForceShape choose_shape(rt3d_ctx *ctx, const DevField &f, int64_t n_point
     sh.splits = std::max(1, S);
     // the expanded two-bundle kernel can add groups of 4 splits in a cluster
     // (off unless asked for: measured slower on the NFW workload, see the tuner)
-    sh.cl = (sh.variant == 5 && ctx->opt.cluster == 4) ? 4 : 1;
+    sh.cl = (sh.variant == 5 && group == 5 && ctx->opt.cluster == 4) ? 4 : 1;
     round_to_clusters(sh);
     return sh;
 }
