@@ -1089,8 +1089,8 @@ __global__ void __launch_bounds__(NT, TPSM / NT) k_force_bundle2x(ForceArgs A)
     const int split = blockIdx.y;
     const int64_t p0 = (int64_t)split * A.per_split;
     const int64_t p1 = min(A.f.n, p0 + A.per_split);
-    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS, CL, AHEAD>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1, split,
-                                                     (float2 *)A.out, s_a, s_b, s_e, s_hl);
+    bundle2x_block_sum<NT, NRING, REPL, PEPS, UMASS, CL, AHEAD>(A.f, A.px, A.py, A.pz, A.rep, n_b, A.n, b0, p0, p1,
+                                                            split, (float2 *)A.out, s_a, s_b, s_e, s_hl);
 }
 
 // ForceArgs for the bundle kernel: n = rays, group = rays per bundle; rep is
@@ -1160,7 +1160,7 @@ __global__ void __launch_bounds__(NT) k_force_fp64(ForceArgs A)
                     long long qq[3] = {pr.x, pr.y, pr.z};
                     if (REPL) replica_q(f, j, pr.x, pr.y, pr.z, qq);
                     v = make_double4_16a((double)(qq[0] - ax) * f.delta, (double)(qq[1] - ay) * f.delta,
-                                     (double)(qq[2] - az) * f.delta, f.m64[pi]);
+                                         (double)(qq[2] - az) * f.delta, f.m64[pi]);
                     if (PEPS) e2 = f.eps2_64[pi];
                 }
                 s_p[q] = v;

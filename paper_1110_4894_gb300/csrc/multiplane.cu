@@ -498,7 +498,7 @@ __global__ void __launch_bounds__(kMpNT64) k_mp_deflect64(MPArgs A)
                 if (g[2] >= P.qlo && g[2] <= P.qhi) {
                     ++n_on;
                     v = make_double4_16a((double)g[0] * f.delta, (double)g[1] * f.delta, f.m64[pi],
-                                     PEPS ? f.eps2_64[pi] : f.eps2u64);
+                                         PEPS ? f.eps2_64[pi] : f.eps2u64);
                 }
             }
             s_p[qq] = v;
