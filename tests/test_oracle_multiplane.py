@@ -7,6 +7,8 @@ Eqs. defangleB, lenseqn, defangle):
 - one plane with a point mass is the thin lens of App. C exactly (deflection
   theta_E^2/theta, mu = (1 - x^-4)^-1, |gamma| = x^-2, two-image total);
 - one plane with a Plummer particle is the Plummer sphere's thin lens;
+- two point masses on two planes follow the textbook multi-plane lens
+  equation in angles and angular-diameter distances;
 - an extended weak lens cut into more and more planes agrees with the 3D
   trace to second order in the field;
 - the plane bookkeeping of a replicated box: slabs at their centres, the last
@@ -173,6 +175,56 @@ def test_thin_planes_approach_the_3d_trace(cosmo):
     assert dev[0] < 1e-2 and dal[0] < 2e-3
     assert dev[2] < dev[1] < dev[0] and dal[2] < dal[1] < dal[0]
     assert dev[2] < 3e-4 and dal[2] < 1e-4
+
+
+def test_two_planes_match_the_angular_lens_equation(cosmo):
+    # two point masses on two planes against the multi-plane lens equation in
+    # its textbook angular form (Sec. 3.1, Eq. lenseqn): physical impact
+    # parameters xi_i = D_i theta_i - p_i / (1 + z_i), deflections
+    # 4 G M xi / |xi|^2, theta_2 = theta - (D_12 / D_2) alpha_1 and
+    # beta = theta - sum_i (D_is / D_s) alpha_i, with the flat universe's
+    # angular-diameter distances D_ij = (chi_j - chi_i) / (1 + z_j).  The
+    # oracle works in comoving positions and slopes instead; a wrong distance
+    # ratio, (1 + z) factor or plane order fails here.
+    from scipy import optimize
+    z_a, z_b, z_s = 0.2, 0.35, 0.6
+    chi_a, chi_b, chi_s = cosmo.chi(z_a), cosmo.chi(z_b), cosmo.chi(z_s)
+    M = np.array([2e13, 1e13])
+    p = np.array([[0.0, 0.0], [0.05, -0.03]])
+    pos = np.array([[p[0, 0], p[0, 1], chi_a], [p[1, 0], p[1, 1], chi_b]])
+    # two slabs of the particles' x3 range, each projected onto its centre
+    d = 0.5 * (chi_b - chi_a)
+    chi_pl = np.array([chi_a + 0.5 * d, chi_a + 1.5 * d])
+    z_pl = np.array([optimize.brentq(lambda z: cosmo.chi(z) - c, 0.0, 1.0, xtol=1e-15) for c in chi_pl])
+    thE = A.theta_einstein(cosmo, M[0], z_a, z_s)
+    th = np.array([[1.7, 0.4], [-1.1, 1.9], [2.6, -2.2], [0.3, -3.1], [4.0, 1.0]]) * thE
+    r = oracle.multiplane(cosmo, oracle.MassField(pos, M, 0.0), z_s, th, n_ring=8, theta_r=1e-3 * thE, slices=2)
+    assert np.allclose(r.planes[:, 0], chi_pl, rtol=1e-13) and np.array_equal(r.planes[:, 2], [1, 1])
+
+    D = chi_pl / (1 + z_pl)
+    D_s = chi_s / (1 + z_s)
+    D_12 = (chi_pl[1] - chi_pl[0]) / (1 + z_pl[1])
+    D_is = (chi_s - chi_pl) / (1 + z_s)
+    G = oracle.mu_G()
+
+    def deflection(i, t):
+        xi = D[i] * t - p[i] / (1 + z_pl[i])
+        return 4.0 * G * M[i] * xi / np.sum(xi * xi, axis=-1, keepdims=True)
+
+    def beta(t):
+        a1 = deflection(0, t)
+        a2 = deflection(1, t - (D_12 / D[1]) * a1)
+        return t - (D_is[0] / D_s) * a1 - (D_is[1] / D_s) * a2
+
+    rays = r.ray_theta()
+    want = beta(rays)
+    assert np.max(np.linalg.norm(r.beta() - want, axis=-1) / np.linalg.norm(rays - want, axis=-1)) < 1e-12
+    # the bundle's magnification against the Jacobian of the angular map
+    h = 1e-6 * thE
+    for b in range(th.shape[0]):
+        jac = np.stack([(beta(th[b] + h * e) - beta(th[b] - h * e)) / (2 * h) for e in np.eye(2)], 1)
+        mu = 1.0 / np.linalg.det(jac)
+        assert abs(r.mu[b] / mu - 1) < 1e-6, (b, r.mu[b], mu)  # the bundle's finite size: ~1e-9
 
 
 def test_box_planes_bookkeeping(cosmo):
