@@ -183,9 +183,14 @@ int rt3d_set_cosmology(rt3d_ctx *ctx, double omega_m, double omega_l, double h);
  * Copy a particle set to the device as field field_id (0..RT3D_MAX_FIELDS-1,
  * replacing any previous one).  pos: n*3, mass: n (> 0), soft: n Plummer
  * softening lengths if soft_per_particle, else soft[0] for all (>= 0).
- * Positions are stored as integers on a grid of 2^-e Mpc (the finest that
- * holds the field), so coordinates that are multiples of 2^-22 Mpc are kept
- * exactly.  vol may be NULL (isolated field). */
+ * Positions are stored as integers on a grid of 2^-e Mpc, the finest that
+ * holds the field: 2^30 grid units for the largest distance of an isolated
+ * field's particles from its centre, 2^31 for a replicated box's length.
+ * Coordinates that are multiples of 2^-e Mpc are kept exactly; others are
+ * rounded to the nearest multiple (at most 2^-(e+1) Mpc away).  Multiples of
+ * 2^-22 Mpc are exact when that distance is at most 256 Mpc (box length at
+ * most 512 Mpc); a wider field has e <= 21.  vol may be NULL (isolated
+ * field). */
 int rt3d_load_particles(rt3d_ctx *ctx, int field_id, int64_t n, const double *pos,
                         const double *mass, const double *soft, int soft_per_particle,
                         const rt3d_volume *vol);
