@@ -638,16 +638,22 @@ def relaunch_command(argv, gpus, port):
 
 def c5_config(args):
     """the headline box (2^24 particles unless --box-particles asks for a
-    smaller box with the same generator, for checks)"""
+    smaller box with the same generator, for checks; rings of 4 unless
+    --n-ring asks for another bundle, e.g. the paper's ring of 8)"""
     import inputs
     if args.box_particles == 2 ** 24:
-        return inputs.config_c5(n_steps=args.table_steps)
-    n_halos = max(1, int(round(24000 * args.box_particles / 2 ** 24)))
-    return inputs.config_c5(N=args.box_particles, n_halos=n_halos, n_steps=args.table_steps)
+        cfg = inputs.config_c5(n_steps=args.table_steps)
+    else:
+        n_halos = max(1, int(round(24000 * args.box_particles / 2 ** 24)))
+        cfg = inputs.config_c5(N=args.box_particles, n_halos=n_halos, n_steps=args.table_steps)
+    if args.n_ring:
+        cfg["n_ring"] = args.n_ring
+    return cfg
 
 
 def c5_name(args):
-    return C5_NAME if args.box_particles == 2 ** 24 else C5_NAME.replace("2e24p", "%dp" % args.box_particles)
+    name = C5_NAME if args.box_particles == 2 ** 24 else C5_NAME.replace("2e24p", "%dp" % args.box_particles)
+    return name + ("_ring%d" % args.n_ring if args.n_ring and args.n_ring != 4 else "")
 
 
 def load_box(ctx, fid, cfg):
@@ -1152,6 +1158,7 @@ def main():
     ap.add_argument("--table-steps", type=int, default=1000, help="RK4 steps of the headline trace's table")
     ap.add_argument("--box-particles", type=int, default=2 ** 24, help="checks only: a smaller headline box")
     ap.add_argument("--bundles", type=int, default=0, help="checks only: trace the first bundles of the grid")
+    ap.add_argument("--n-ring", type=int, default=0, help="checks only: rays on the bundle's ring (0: the workload's 4)")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--e2e-bundles", type=int, default=16384)
     ap.add_argument("--e2e-table", type=int, default=2)
